@@ -1,0 +1,100 @@
+"""Small test-side helpers: state functions used to CHECK invariants, the
+transpose index, the dependency-closure submesh used for sampled parity at
+full size, and an SSPRK(3,3) stage loop that exposes every stage's trace."""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2106_02159_gb300 import meshes as M
+
+
+def internal_energy(U):
+    dim = U.shape[0] - 2
+    return U[dim + 1] - 0.5 * (U[1:dim + 1] ** 2).sum(0) / U[0]
+
+
+def phi(U, gamma=1.4):
+    return internal_energy(U) * U[0] ** (-gamma)
+
+
+def flux_dot_n(U, n, gamma=1.4):
+    """f(U) n for states U [S, m] and vectors n [dim, m]."""
+    dim = U.shape[0] - 2
+    rho = U[0]
+    v = U[1:dim + 1] / rho
+    p = (gamma - 1.0) * internal_energy(U)
+    vn = (v * n).sum(0)
+    out = np.empty_like(U)
+    out[0] = rho * vn
+    for a in range(dim):
+        out[1 + a] = U[1 + a] * vn + p * n[a]
+    out[dim + 1] = (U[dim + 1] + p) * vn
+    return out
+
+
+def transpose_index(mesh):
+    rows = mesh.row_of_entry()
+    key = rows * mesh.n + mesh.col.astype(np.int64)
+    tkey = mesh.col.astype(np.int64) * mesh.n + rows
+    return np.searchsorted(key, tkey)
+
+
+def ssprk3_with_traces(orc, U, dt=0.0):
+    """One SSPRK(3,3) step of the oracle, stage by stage, returning the traces
+    of the three forward-Euler stages together with their inputs."""
+    out = []
+    w, tau, tr = orc.forward_euler(U, dt, trace=True)
+    out.append((U, w, tr))
+    w = orc.apply_bc(w)
+    v, _, tr = orc.forward_euler(w, tau, trace=True)
+    out.append((w, v, tr))
+    v = orc.apply_bc(v)
+    w2 = U + 0.25 * (v - U)
+    v, _, tr = orc.forward_euler(w2, tau, trace=True)
+    out.append((w2, v, tr))
+    v = orc.apply_bc(v)
+    return U + (2.0 / 3.0) * (v - U), tau, out
+
+
+def all_slip(mesh):
+    """The same mesh with every boundary node treated as a slip node whose
+    normal is the full boundary normal n_i (closed domain)."""
+    import dataclasses
+    return dataclasses.replace(mesh, bnd_kind=np.full(mesh.n_bnd, M.BC_SLIP, dtype=np.int32),
+                               bnd_normal=mesh.bnd_normal_full.copy())
+
+
+def submesh(mesh, seeds, radius, bnd_state=None):
+    """Rows within graph distance ``radius`` of ``seeds``, renumbered. Rows
+    farther than ``radius - k`` from the seeds are incomplete, so a quantity
+    that depends on k rings of neighbours is exact only on the seeds when
+    radius > k. Returns (submesh, old ids of the new nodes, new ids of the
+    seeds, bnd_state restricted)."""
+    seeds = np.unique(np.asarray(seeds))
+    keep = np.zeros(mesh.n, dtype=bool)
+    keep[seeds] = True
+    front = seeds
+    for _ in range(radius):
+        nb = np.concatenate([mesh.col[mesh.row_ptr[i]:mesh.row_ptr[i + 1]] for i in front]) if front.size else front
+        nb = np.unique(nb)
+        front = nb[~keep[nb]]
+        keep[front] = True
+    old = np.nonzero(keep)[0]
+    new_of_old = np.full(mesh.n, -1, dtype=np.int64)
+    new_of_old[old] = np.arange(old.size)
+    rows = mesh.row_of_entry()
+    sel = keep[rows] & keep[mesh.col]
+    r2 = new_of_old[rows[sel]]
+    c2 = new_of_old[mesh.col[sel]].astype(np.int32)
+    row_ptr = np.zeros(old.size + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(np.bincount(r2, minlength=old.size))
+    bsel = keep[mesh.bnd_node]
+    import dataclasses
+    sm = dataclasses.replace(
+        mesh, name=mesh.name + "-sub", coords=mesh.coords[old], row_ptr=row_ptr, col=c2,
+        cij=np.ascontiguousarray(mesh.cij[:, sel]), mij=mesh.mij[sel], mi=mesh.mi[old],
+        bnd_node=new_of_old[mesh.bnd_node[bsel]].astype(np.int32), bnd_kind=mesh.bnd_kind[bsel],
+        bnd_normal=np.ascontiguousarray(mesh.bnd_normal[:, bsel]), bnd_mass_full=mesh.bnd_mass_full[bsel],
+        bnd_normal_full=np.ascontiguousarray(mesh.bnd_normal_full[:, bsel]))
+    bs = None if bnd_state is None else np.ascontiguousarray(bnd_state[:, bsel])
+    return sm, old, new_of_old[seeds], bs

@@ -1,0 +1,207 @@
+"""Planted mistakes: each test compiles a copy of the oracle with one plausible
+error (a wrong sign, a dropped factor, a transposed operand, a skipped step)
+and checks that at least one pin rejects it. The mistakes are planted in a
+temporary copy on the CPU; the oracle itself is never modified. CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_02159_gb300 import meshes as M
+from paper_2106_02159_gb300 import workloads as W
+
+from . import helpers as H
+from . import riemann_exact as RE
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "euler_oracle.c")
+
+
+def _mutant(tmp_path, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, old
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new, 1))
+    return oracle.load(oracle.build(force=True, src=str(path), out=str(tmp_path / "libmutant.so")))
+
+
+# --- detectors: each returns True when the pin holds ------------------------
+
+def _safe(fn):
+    def wrapped(lib):
+        try:
+            return fn(lib)
+        except oracle.OracleError:
+            return False  # the oracle itself refused (e.g. a non-admissible state)
+    wrapped.__name__ = fn.__name__
+    return wrapped
+
+
+def _graded(lib):
+    mesh, U0, bs = W.cylinder_problem(8)
+    orc = oracle.Oracle(mesh, bnd_state=bs, lib=lib)
+    U, _ = orc.run(orc.apply_bc(U0), 6)
+    return mesh, orc, U
+
+
+@_safe
+def pin_low_order_flux_form(lib):
+    mesh, orc, U = _graded(lib)
+    _, tau, tr = orc.forward_euler(U, trace=True)
+    rows = mesh.row_of_entry()
+    from .test_oracle_pins import _flux_matrix
+    f = _flux_matrix(U)
+    fc = np.einsum("sdk,dk->sk", f[:, :, mesh.col], mesh.cij)
+    FL = -fc + tr["dij"] * (U[:, mesh.col] - U[:, rows])
+    rhs = np.stack([np.bincount(rows, weights=FL[s], minlength=mesh.n) for s in range(4)])
+    return bool(np.abs(U + tau * rhs / mesh.mi - tr["UL"]).max() <= 1e-12 * np.abs(U).max())
+
+
+@_safe
+def pin_compact_high_order_form(lib):
+    mesh, orc, U = _graded(lib)
+    _, tau, tr = orc.forward_euler(U, trace=True)
+    rows = mesh.row_of_entry()
+    FH = tr["FH"]
+    BF = FH + np.stack([np.bincount(rows, weights=-(mesh.mij / mesh.mi[mesh.col]) * FH[s, mesh.col],
+                                     minlength=mesh.n) for s in range(4)])
+    UH = U + tau * (FH + BF) / mesh.mi
+    lam = 1.0 / (np.diff(mesh.row_ptr) - 1)
+    sumP = np.stack([np.bincount(rows, weights=lam[rows] * tr["P"][s], minlength=mesh.n) for s in range(4)])
+    return bool(np.abs(tr["UL"] + sumP - UH).max() <= 1e-12 * np.abs(U).max())
+
+
+@_safe
+def pin_lambda_bound(lib):
+    rng = np.random.default_rng(1)
+    m = 20000
+    rho = np.exp(rng.uniform(-3, 3, (2, m)))
+    p = np.exp(rng.uniform(-3, 3, (2, m)))
+    u = rng.uniform(-3, 3, (2, m))
+    ul = W.conserved(rho[0], [u[0], 0 * u[0]], p[0]).T.copy()
+    ur = W.conserved(rho[1], [u[1], 0 * u[1]], p[1]).T.copy()
+    n = np.tile([1.0, 0.0], (m, 1))
+    lam = oracle.lambda_max_batch(ul, ur, n, lib=lib)
+    ex, _ = RE.max_wave_speed(rho[0], u[0], p[0], rho[1], u[1], p[1])
+    return bool(np.all(lam >= ex * (1 - 1e-10)))
+
+
+@_safe
+def pin_periodic_conservation(lib):
+    w = W.vortex_workload(24)
+    orc = oracle.Oracle(w.mesh, lib=lib)
+    U, _ = orc.run(w.U0, 2)
+    d = np.abs((w.mesh.mi * U).sum(1) - (w.mesh.mi * w.U0).sum(1))
+    return bool(np.all(d <= 1e-13 * (w.mesh.mi * np.abs(w.U0)).sum(1)))
+
+
+@_safe
+def pin_cfl_closed_form(lib):
+    mesh = M.periodic_p1_square(8)
+    U = W.uniform_state(mesh, 1.0, (0.0, 0.0), 1.0)
+    rows = mesh.row_of_entry()
+    T = H.transpose_index(mesh)
+    norms = np.linalg.norm(mesh.cij, axis=0)
+    upper = np.where(mesh.col > rows, norms, norms[T])
+    off = rows != mesh.col
+    dii = math.sqrt(1.4) * np.bincount(rows[off], weights=upper[off], minlength=mesh.n)
+    expect = 0.5 * np.min(mesh.mi / (2.0 * dii))
+    return math.isclose(oracle.Oracle(mesh, cfl=0.5, lib=lib).cfl_dt(U), expect, rel_tol=1e-13)
+
+
+@_safe
+def pin_sod_error(lib):
+    mesh = W.riemann_strip(100)
+    orc = oracle.Oracle(mesh, lib=lib)
+    data = W.RIEMANN_CASES["sod"]
+    try:
+        U, t, _ = orc.run_to(W.riemann_initial(mesh, "sod"), data[-1])
+    except oracle.OracleError:
+        return False
+    rho, _, _ = RE.sample(mesh.coords[:, 0], t, *data[:6])
+    e = (mesh.mi * np.abs(U[0] - rho)).sum() / (mesh.mi * rho).sum()
+    return bool(np.isfinite(e) and e < 0.025)
+
+
+@_safe
+def pin_indicator_small_in_smooth_flow(lib):
+    mesh = M.periodic_p1_square(64)
+    _, _, tr = oracle.Oracle(mesh, lib=lib).forward_euler(W.isentropic_vortex(mesh), trace=True)
+    core = np.hypot(*mesh.coords.T) < 3.0
+    return bool(tr["alpha"][core].max() < 0.5 and tr["alpha"][core].mean() < 0.05)
+
+
+@_safe
+def pin_slip_conservation(lib):
+    mesh = H.all_slip(M.cylinder_channel_q1(8))
+    x, y = mesh.coords.T
+    bump = np.exp(-40 * ((x - 2.0) ** 2 + (y - 0.5) ** 2))
+    U = W.conserved(1.0 + 0.5 * bump, [0.2 + 0 * x, 0.1 + 0 * x], 1.0 + 2.0 * bump)
+    orc = oracle.Oracle(mesh, lib=lib)
+    U = orc.apply_bc(U)
+    m0 = (mesh.mi * U).sum(1)
+    for _ in range(3):
+        U, _, _ = orc.ssprk3_step(U)
+    m = (mesh.mi * U).sum(1)
+    return bool(abs(m[0] - m0[0]) <= 1e-13 * abs(m0[0]) and abs(m[3] - m0[3]) <= 1e-13 * abs(m0[3]))
+
+
+@_safe
+def pin_stage_symmetries(lib):
+    w = W.vortex_workload(16)
+    orc = oracle.Oracle(w.mesh, lib=lib)
+    _, _, tr = orc.forward_euler(w.U0, trace=True)
+    T = H.transpose_index(w.mesh)
+    off = w.mesh.row_of_entry() != w.mesh.col
+    return bool(np.array_equal(tr["dij"][off], tr["dij"][T][off]))
+
+
+@_safe
+def pin_vortex_second_order(lib):
+    errs = []
+    for nv in (32, 64):
+        mesh = M.periodic_p1_square(nv)
+        orc = oracle.Oracle(mesh, bound_relaxation=True, lib=lib)
+        U, t, _ = orc.run_to(W.isentropic_vortex(mesh), 1.0)
+        ex = W.isentropic_vortex(mesh, t=t)
+        errs.append((mesh.mi * np.abs(U[0] - ex[0])).sum() / (mesh.mi * ex[0]).sum())
+    return math.log2(errs[0] / errs[1]) >= 1.8
+
+
+MUTATIONS = {
+    "bar_state_sign": ("ubar[s] = dL > 0.0 ? 0.5 * (ui[s] + uj[s]) - dfc[s] / (2.0 * dL) : ui[s];",
+                       "ubar[s] = dL > 0.0 ? 0.5 * (ui[s] + uj[s]) + dfc[s] / (2.0 * dL) : ui[s];",
+                       pin_low_order_flux_form),
+    "lambda_shock_factor": ("double k = (gamma + 1.0) / (2.0 * gamma);", "double k = (gamma - 1.0) / (2.0 * gamma);",
+                            pin_lambda_bound),
+    "lambda_right_velocity_not_divided": ("  un_r /= rho_r;\n", "\n", pin_lambda_bound),
+    "b_ij_b_ji_transposed": ("double val = bij * c->FH[s * n + j] - bji * c->FH[s * n + i]",
+                             "double val = bji * c->FH[s * n + j] - bij * c->FH[s * n + i]",
+                             pin_compact_high_order_form),
+    "limiter_not_symmetrised": ("c->lij[k] = fmin(c->lraw[k], c->lraw[c->transpose[k]]);",
+                                "c->lij[k] = c->lraw[k];", pin_periodic_conservation),
+    "cfl_missing_factor_two": ("double t = -p->cfl * p->mi[i] / (2.0 * c->dij[kdiag]);",
+                               "double t = -p->cfl * p->mi[i] / (c->dij[kdiag]);", pin_cfl_closed_form),
+    "indicator_commutator_sign": ("N += a - b;", "N += a + b;", pin_indicator_small_in_smooth_flow),
+    "slip_projection_sign": ("U[(1 + d) * n + i] -= mn * p->bnd_normal[(int64_t)d * p->n_bnd + b];",
+                             "U[(1 + d) * n + i] += mn * p->bnd_normal[(int64_t)d * p->n_bnd + b];",
+                             pin_slip_conservation),
+    "transpose_fill_skipped": ("if (j < i) c->dij[k] = c->dij[c->transpose[k]];",
+                               "if (j < i) c->dij[k] = 1.0;", pin_stage_symmetries),
+    "ssp_stage_weight": ("w[q] = u0[q] + 0.25 * (v[q] - u0[q]);", "w[q] = u0[q] + 0.5 * (v[q] - u0[q]);",
+                         pin_vortex_second_order),
+}
+
+
+@pytest.fixture(scope="module")
+def real_lib():
+    return oracle.load()
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pin_rejects_planted_mistake(name, tmp_path, real_lib):
+    old, new, pin = MUTATIONS[name]
+    assert pin(real_lib), f"pin {pin.__name__} must hold for the oracle itself"
+    mlib = _mutant(tmp_path, old, new)
+    assert not pin(mlib), f"planted mistake {name!r} was not caught by {pin.__name__}"

@@ -1,0 +1,519 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks a property that a plausible mistake in the oracle (a dropped
+term, a wrong sign or index, a transposed operand) breaks: exact wave-speed
+bounds from an exact Riemann solver, the invariants of Sec. 3 and Sec. 4
+(conservation, Lemma 3.1's boundary balance, Lemma 4.5, positivity, the local
+bounds, the symmetries of Sec. 3.3), closed forms of special cases, and
+convergence to exact solutions. CPU only.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_02159_gb300 import meshes as M
+from paper_2106_02159_gb300 import workloads as W
+
+from . import helpers as H
+from . import riemann_exact as RE
+
+GAMMA = 1.4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads():
+    oracle.set_threads(0)
+
+
+# ---------------------------------------------------------------------------
+# the exact Riemann solver used as a pin is itself checked first
+# ---------------------------------------------------------------------------
+
+def test_exact_riemann_solver_satisfies_jump_conditions():
+    """Rankine-Hugoniot across shocks, isentropy + Riemann invariant across
+    rarefactions, and equal u*, p* on both sides of the contact."""
+    g = GAMMA
+    for case in W.RIEMANN_CASES.values():
+        rl, ul, pl, rr, ur, pr, t = case
+        x = np.linspace(0.0, 1.0, 20001)
+        rho, u, p = RE.sample(x, t, rl, ul, pl, rr, ur, pr, g)
+        E = p / (g - 1) + 0.5 * rho * u * u
+        # locate jumps
+        jumps = np.nonzero(np.abs(np.diff(rho)) > 1e-3 * rho.max())[0]
+        for j in jumps:
+            a, b = j, j + 1
+            # only isolated discontinuities (shocks / contact); rarefaction fans change gradually
+            if (np.abs(np.diff(rho[max(0, a - 3):a + 1])).max() > 1e-9 or
+                    np.abs(np.diff(rho[b:b + 4])).max() > 1e-9):
+                continue
+            s = None
+            if abs(rho[b] - rho[a]) > 0:
+                s = (rho[b] * u[b] - rho[a] * u[a]) / (rho[b] - rho[a])
+            Fm = lambda r_, u_, p_: r_ * u_ * u_ + p_  # noqa: E731
+            Fe = lambda r_, u_, p_, e_: u_ * (e_ + p_)  # noqa: E731
+            assert math.isclose(Fm(rho[b], u[b], p[b]) - Fm(rho[a], u[a], p[a]),
+                                s * (rho[b] * u[b] - rho[a] * u[a]), rel_tol=1e-9, abs_tol=1e-9)
+            assert math.isclose(Fe(rho[b], u[b], p[b], E[b]) - Fe(rho[a], u[a], p[a], E[a]),
+                                s * (E[b] - E[a]), rel_tol=1e-9, abs_tol=1e-9)
+        # inside rarefaction fans: isentropic and the Riemann invariant u +/- 2a/(g-1) is constant
+        ps, us = (float(v) for v in RE.star_pressure(rl, ul, pl, rr, ur, pr, g))
+        sx = (x - 0.5) / t
+        a = np.sqrt(g * p / rho)
+        if ps < pl:
+            al, als = math.sqrt(g * pl / rl), math.sqrt(g * pl / rl) * (ps / pl) ** ((g - 1) / (2 * g))
+            fan = (sx > ul - al + 1e-6) & (sx < us - als - 1e-6)
+            assert fan.sum() > 10
+            assert np.allclose(p[fan] / rho[fan] ** g, pl / rl ** g, rtol=1e-12)
+            assert np.allclose(u[fan] + 2 * a[fan] / (g - 1), ul + 2 * al / (g - 1), rtol=1e-12)
+        if ps < pr:
+            ar, ars = math.sqrt(g * pr / rr), math.sqrt(g * pr / rr) * (ps / pr) ** ((g - 1) / (2 * g))
+            fan = (sx < ur + ar - 1e-6) & (sx > us + ars + 1e-6)
+            assert fan.sum() > 10
+            assert np.allclose(p[fan] / rho[fan] ** g, pr / rr ** g, rtol=1e-12)
+            assert np.allclose(u[fan] - 2 * a[fan] / (g - 1), ur - 2 * ar / (g - 1), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.1: lambda_max is a guaranteed upper bound
+# ---------------------------------------------------------------------------
+
+def _random_pairs(rng, m):
+    rho = np.exp(rng.uniform(np.log(1e-3), np.log(1e3), (2, m)))
+    p = np.exp(rng.uniform(np.log(1e-3), np.log(1e3), (2, m)))
+    un = rng.uniform(-10.0, 10.0, (2, m))
+    ut = rng.uniform(-10.0, 10.0, (2, m))
+    theta = rng.uniform(0, 2 * np.pi, m)
+    n = np.stack([np.cos(theta), np.sin(theta)], 1)
+    t = np.stack([-np.sin(theta), np.cos(theta)], 1)
+    states = []
+    for s in range(2):
+        v = un[s][:, None] * n + ut[s][:, None] * t
+        states.append(W.conserved(rho[s], [v[:, 0], v[:, 1]], p[s], GAMMA).T.copy())
+    return states[0], states[1], n, (rho, un, p)
+
+
+def test_lambda_max_bounds_exact_max_wave_speed():
+    """On 10^6 seeded random pairs: lambda_max >= exact max wave speed, with
+    equality when both waves are rarefactions (p_tr is then exact)."""
+    rng = np.random.default_rng(2106)
+    ul, ur, n, (rho, un, p) = _random_pairs(rng, 1_000_000)
+    lam = oracle.lambda_max_batch(ul, ur, n, GAMMA)
+    exact, pstar = RE.max_wave_speed(rho[0], un[0], p[0], rho[1], un[1], p[1], GAMMA)
+    # the oracle sees conserved states: eps = E - |m|^2/(2 rho) loses digits by
+    # cancellation when the kinetic energy dominates; allow that much roundoff
+    ke = 0.5 * ((ul[:, 1:3] ** 2).sum(1) / ul[:, 0] + (ur[:, 1:3] ** 2).sum(1) / ur[:, 0])
+    cond = 1.0 + ke / (p.min(0) / (GAMMA - 1.0))
+    assert np.all(lam >= exact * (1 - 4e-16 * cond - 1e-14))
+    two_raref = pstar < np.minimum(p[0], p[1]) * (1 - 1e-9)
+    assert two_raref.sum() > 1000
+    assert np.allclose(lam[two_raref], exact[two_raref], rtol=1e-9, atol=0)
+
+
+def test_lambda_max_special_cases():
+    """At rest: lambda = sound speed. Mirror symmetry: swapping the states and
+    reversing n gives the same bound. Galilean shift along n shifts the waves."""
+    U = W.conserved(1.0, [0.0, 0.0], 1.0)
+    assert math.isclose(oracle.lambda_max(U, U, [1.0, 0.0]), math.sqrt(GAMMA), rel_tol=1e-15)
+    rng = np.random.default_rng(7)
+    ul, ur, n, _ = _random_pairs(rng, 2000)
+    a = oracle.lambda_max_batch(ul, ur, n)
+    b = oracle.lambda_max_batch(ur, ul, -n)
+    assert np.allclose(a, b, rtol=1e-13)
+    # strong collision: two shocks; p_tr over-estimates p*, so the bound is safe but loose
+    UL = W.conserved(1.0, [5.0, 0.0], 1.0)
+    UR = W.conserved(1.0, [-5.0, 0.0], 1.0)
+    lam = oracle.lambda_max(UL, UR, [1.0, 0.0])
+    exact, _ = RE.max_wave_speed(1.0, 5.0, 1.0, 1.0, -5.0, 1.0)
+    assert lam >= exact[()] > math.sqrt(GAMMA)
+    # Galilean invariance along n: shifting both normal velocities by w shifts both
+    # outer wave speeds by w; with w large both waves move right, so lambda = lambda_3 + w
+    for w_ in (20.0, 50.0):
+        U1 = W.conserved(1.0, [0.3 + w_, 0.0], 1.0)
+        U2 = W.conserved(0.5, [-0.2 + w_, 0.0], 0.4)
+        V1 = W.conserved(1.0, [0.3 + 2 * w_, 0.0], 1.0)
+        V2 = W.conserved(0.5, [-0.2 + 2 * w_, 0.0], 0.4)
+        assert math.isclose(oracle.lambda_max(V1, V2, [1.0, 0.0]) - oracle.lambda_max(U1, U2, [1.0, 0.0]), w_,
+                            rel_tol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.2: entropy and its gradient
+# ---------------------------------------------------------------------------
+
+def test_entropy_gradient_matches_finite_differences():
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        rho = math.exp(rng.uniform(-2, 2))
+        v = rng.uniform(-3, 3, 2)
+        p = math.exp(rng.uniform(-2, 2))
+        U = W.conserved(rho, [v[0], v[1]], p)
+        g = oracle.entropy_gradient(U)
+        for s in range(4):
+            h = 1e-6 * max(1.0, abs(U[s]))
+            Up, Um = U.copy(), U.copy()
+            Up[s] += h
+            Um[s] -= h
+            fd = (oracle.entropy_eta(Up) - oracle.entropy_eta(Um)) / (2 * h)
+            assert math.isclose(g[s], fd, rel_tol=1e-6, abs_tol=1e-8)
+
+
+def test_entropy_is_minus_rho_s():
+    U = W.conserved(2.0, [0.3, -0.1], 3.0)
+    s = math.log(3.0 / 0.4 / 2.0 ** GAMMA * 1.0) / 0.4  # eps = p/(gamma-1), Phi = eps rho^-gamma
+    assert math.isclose(oracle.entropy_eta(U), -2.0 * s, rel_tol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.3: the line search
+# ---------------------------------------------------------------------------
+
+def _psi(U, P, l, phi_min):
+    u = U + l * P
+    if u[0] <= 0:
+        return -np.inf
+    return H.internal_energy(u[:, None])[0] - phi_min * u[0] ** GAMMA
+
+
+def test_line_search_returns_feasible_near_maximal_limiter():
+    """l in [0,1] satisfies the three bounds, and no l' > l + tol does
+    (checked against bisection on the exact constraint)."""
+    rng = np.random.default_rng(5)
+    n_active = 0
+    gaps = []
+    for _ in range(4000):
+        rho = math.exp(rng.uniform(-1, 1))
+        U = W.conserved(rho, list(rng.uniform(-1, 1, 2)), math.exp(rng.uniform(-1, 1)))
+        P = rng.normal(size=4) * np.array([0.3, 0.5, 0.5, 1.0]) * rng.choice([0.1, 1.0, 3.0])
+        phi_u = H.phi(U[:, None])[0]
+        rmin, rmax = rho * rng.uniform(0.5, 1.0), rho * rng.uniform(1.0, 1.5)
+        pmin = phi_u * rng.uniform(0.3, 1.0)
+        l = oracle.line_search(U, P, rmin, rmax, pmin)
+        assert 0.0 <= l <= 1.0
+        u = U + l * P
+        assert rmin * (1 - 1e-13) <= u[0] <= rmax * (1 + 1e-13)
+        assert _psi(U, P, l, pmin) >= -1e-13 * abs(H.internal_energy(u[:, None])[0])
+
+        def feasible(x):
+            w = U + x * P
+            return (w[0] >= rmin and w[0] <= rmax and w[0] > 0 and _psi(U, P, x, pmin) >= 0)
+        # largest feasible l by bisection (constraints are convex in l)
+        lo, hi = 0.0, 1.0
+        if feasible(1.0):
+            lo = 1.0
+        else:
+            for _ in range(80):
+                mid = 0.5 * (lo + hi)
+                if feasible(mid):
+                    lo = mid
+                else:
+                    hi = mid
+        assert l <= lo + 1e-12
+        # six fixed secant/Newton iterations: a very close lower estimate (Sec. 3.3)
+        assert l >= lo * (1 - 1e-4) - 1e-12
+        gaps.append((lo - l) / max(lo, 1e-12))
+        if lo < 1.0 and _psi(U, P, 1.0, pmin) < 0:
+            n_active += 1
+    assert n_active > 200
+    assert np.median(gaps) < 1e-12 and np.mean(np.array(gaps) < 1e-6) > 0.9
+
+
+# ---------------------------------------------------------------------------
+# stage-level invariants
+# ---------------------------------------------------------------------------
+
+def test_uniform_states_are_exact_fixed_points():
+    """Uniform states with compatible boundary data are preserved bitwise."""
+    cases = []
+    p1 = M.periodic_p1_square(12)
+    cases.append((p1, W.uniform_state(p1, 1.3, (0.7, -0.4), 2.0), None))
+    q1 = M.structured_q1(10, 7, periodic_x=True, periodic_y=True)
+    cases.append((q1, W.uniform_state(q1, 0.9, (-1.1, 0.3), 0.5), None))
+    ch = M.structured_q1(12, 6, 0.0, 2.0, 0.0, 1.0, kinds=(M.BC_DIRICHLET, M.BC_DO_NOTHING, M.BC_SLIP, M.BC_SLIP))
+    Uc = W.uniform_state(ch, 1.4, (3.0, 0.0), 1.0)
+    cases.append((ch, Uc, Uc[:, ch.bnd_node].copy()))
+    cyl = M.cylinder_channel_q1(8)
+    Ur = W.uniform_state(cyl, 1.0, (0.0, 0.0), 1.0)
+    cases.append((cyl, Ur, Ur[:, cyl.bnd_node].copy()))
+    for mesh, U, bs in cases:
+        orc = oracle.Oracle(mesh, bnd_state=bs)
+        U1, _, _ = orc.forward_euler(U)
+        assert np.array_equal(U1, U), mesh.name
+        U20, _ = orc.run(U, 20)
+        assert np.array_equal(U20, U), mesh.name
+
+
+def test_periodic_conservation_every_stage():
+    """sum_i m_i U_i is conserved by every stage on a periodic mesh (Sec. 3.3,
+    eq. mass_conservation_by_limiting with sum_j c_ij = 0 and no boundary)."""
+    w = W.vortex_workload(32)
+    orc = oracle.Oracle(w.mesh)
+    U = w.U0
+    total0 = (w.mesh.mi * U).sum(1)
+    scale = (w.mesh.mi * np.abs(U)).sum(1)
+    for _ in range(5):
+        U, _, stages = H.ssprk3_with_traces(orc, U)
+        for Uin, Uout, tr in stages:
+            d = np.abs((w.mesh.mi * Uout).sum(1) - (w.mesh.mi * Uin).sum(1))
+            assert np.all(d <= 1e-14 * scale)
+        assert np.all(np.abs((w.mesh.mi * U).sum(1) - total0) <= 1e-13 * scale)
+
+
+def test_boundary_balance_lemma_3_1():
+    """Lemma 3.1 (ii): sum m U^{n+1} + tau sum_bnd m^bnd f(U^n) n = sum m U^n,
+    for one forward-Euler step after limiting, before post-processing."""
+    mesh, U0, bs = W.cylinder_problem(10)
+    orc = oracle.Oracle(mesh, bnd_state=bs)
+    U, _ = orc.run(orc.apply_bc(U0), 15)  # a non-trivial admissible state
+    U1, tau, _ = orc.forward_euler(U)
+    lhs = (mesh.mi * U1).sum(1) + tau * (mesh.bnd_mass_full * H.flux_dot_n(
+        U[:, mesh.bnd_node], mesh.bnd_normal_full)).sum(1)
+    rhs = (mesh.mi * U).sum(1)
+    scale = (mesh.mi * np.abs(U)).sum(1)
+    assert np.all(np.abs(lhs - rhs) <= 1e-13 * scale)
+
+
+def test_slip_closed_domain_conserves_mass_and_energy_lemma_4_5():
+    mesh = H.all_slip(M.cylinder_channel_q1(10))
+    x, y = mesh.coords.T
+    bump = np.exp(-40 * ((x - 2.0) ** 2 + (y - 0.5) ** 2))
+    U = W.conserved(1.0 + 0.5 * bump, [0 * x, 0 * x], 1.0 + 2.0 * bump)
+    orc = oracle.Oracle(mesh)
+    m0 = (mesh.mi * U).sum(1)
+    scale = (mesh.mi * np.abs(U)).sum(1)
+    for _ in range(10):
+        U, _, _ = orc.ssprk3_step(U)
+        m = (mesh.mi * U).sum(1)
+        assert abs(m[0] - m0[0]) <= 1e-13 * scale[0]
+        assert abs(m[3] - m0[3]) <= 1e-13 * scale[3]
+    assert orc.count_not_admissible(U) == 0
+
+
+def _check_stage(mesh, Uin, Uout, tr, tau, passes=2, slack=1e-12, cfl=0.5):
+    """Positivity, local bounds, symmetries and IDP of U^L for one stage."""
+    T = H.transpose_index(mesh)
+    rows = mesh.row_of_entry()
+    off = rows != mesh.col
+    UL = tr["UL"]
+    b = tr["bounds"]
+    # low-order update is admissible and inside its own bounds (Sec. 3.1, c_cfl <= 1)
+    assert np.all(UL[0] > 0) and np.all(H.internal_energy(UL) > 0)
+    assert np.all(UL[0] >= b[0] * (1 - slack)) and np.all(UL[0] <= b[1] * (1 + slack))
+    assert np.all(H.phi(UL) >= b[2] * (1 - slack))
+    # limited states after every pass (Sec. 3.3)
+    for q in range(passes):
+        Uq = tr["Upass"][q]
+        assert np.all(Uq[0] > 0) and np.all(H.internal_energy(Uq) > 0)
+        assert np.all(Uq[0] >= b[0] * (1 - slack)) and np.all(Uq[0] <= b[1] * (1 + slack))
+        assert np.all(H.phi(Uq) >= b[2] * (1 - slack))
+        l = tr["lij"][q]
+        assert np.array_equal(l, l[T]) and np.all((l >= 0) & (l <= 1))
+    assert np.array_equal(Uout, tr["Upass"][passes - 1])
+    # d_ij symmetric, d_ii = -sum_{j != i} d_ij
+    d = tr["dij"]
+    assert np.array_equal(d[off], d[T][off])
+    assert np.all(d[off] > 0)
+    diag = np.bincount(rows[off], weights=d[off], minlength=mesh.n)
+    assert np.allclose(d[~off], -diag, rtol=1e-14)
+    # tau is fixed at the first stage (Sec. 3.1); every stage stays within the
+    # invariant-domain limit c_cfl = 1, i.e. tau <= tau_bound / c_cfl
+    assert tau <= tr["tau_bound"] / cfl * (1 + 1e-12)
+    # m_i lambda_i P_ij = - m_j lambda_j P_ji (Sec. 3.3)
+    card = np.diff(mesh.row_ptr)
+    lam = 1.0 / (card - 1)
+    mP = mesh.mi[rows] * lam[rows] * tr["P"]
+    scale = np.abs(mP).max() + 1e-300
+    assert np.abs(mP[:, off] + mP[:, T][:, off]).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("relax", [False, True])
+def test_positivity_bounds_symmetry_vortex(relax):
+    w = W.vortex_workload(32)
+    orc = oracle.Oracle(w.mesh, bound_relaxation=relax)
+    U = w.U0
+    for _ in range(4):
+        U, tau, stages = H.ssprk3_with_traces(orc, U)
+        assert tau == stages[0][2]["tau_bound"]
+        for Uin, Uout, tr in stages:
+            _check_stage(w.mesh, Uin, Uout, tr, tau)
+
+
+def test_positivity_bounds_symmetry_cylinder_and_strong_shock():
+    mesh, U0, bs = W.cylinder_problem(12)
+    orc = oracle.Oracle(mesh, bnd_state=bs)
+    U = orc.apply_bc(U0)
+    for step in range(12):
+        U, tau, stages = H.ssprk3_with_traces(orc, U)
+        if step % 3 == 2:
+            for Uin, Uout, tr in stages:
+                _check_stage(mesh, Uin, Uout, tr, tau)
+    assert orc.count_not_admissible(U) == 0
+    strip = W.riemann_strip(60)
+    orc = oracle.Oracle(strip)
+    U = W.riemann_initial(strip, (1.0, 0.0, 1000.0, 1.0, 0.0, 0.01, 0.0))
+    for _ in range(10):
+        U, tau, stages = H.ssprk3_with_traces(orc, U)
+        for Uin, Uout, tr in stages:
+            _check_stage(strip, Uin, Uout, tr, tau)
+
+
+def _flux_matrix(U, gamma=GAMMA):
+    """f(U) as [S, dim, n] (Sec. 2.1), for checks only."""
+    dim = U.shape[0] - 2
+    v = U[1:dim + 1] / U[0]
+    p = (gamma - 1.0) * H.internal_energy(U)
+    f = np.empty((dim + 2, dim, U.shape[1]))
+    f[0] = U[1:dim + 1]
+    for a in range(dim):
+        for b in range(dim):
+            f[1 + a, b] = v[b] * U[1 + a] + (p if a == b else 0.0)
+    f[dim + 1] = v * (U[dim + 1] + p)
+    return f
+
+
+def _graded_state():
+    mesh, U0, bs = W.cylinder_problem(10)
+    orc = oracle.Oracle(mesh, bnd_state=bs)
+    U, _ = orc.run(orc.apply_bc(U0), 12)
+    return mesh, orc, U
+
+
+def test_low_order_update_matches_flux_form():
+    """eq. loworder: m_i (U^L_i - U_i) = tau sum_j (-f(U_j) c_ij + d_ij (U_j - U_i)),
+    evaluated directly, equals the bar-state form eq. loworder_bis."""
+    mesh, orc, U = _graded_state()
+    _, tau, tr = orc.forward_euler(U, trace=True)
+    rows = mesh.row_of_entry()
+    f = _flux_matrix(U)
+    fc = np.einsum("sdk,dk->sk", f[:, :, mesh.col], mesh.cij)
+    FL = -fc + tr["dij"] * (U[:, mesh.col] - U[:, rows])
+    rhs = np.stack([np.bincount(rows, weights=FL[s], minlength=mesh.n) for s in range(4)])
+    UL = U + tau * rhs / mesh.mi
+    scale = np.abs(U).max(1, keepdims=True)
+    assert np.abs(UL - tr["UL"]).max() <= 1e-12 * scale.max()
+
+
+def test_unlimited_update_matches_compact_high_order_form():
+    """eq. highorderCompact: M_L (U^H - U) = tau (I + B) F^H with b_ij = delta_ij - m_ij/m_j,
+    evaluated with matrices, equals U^L + sum_{j != i} lambda_i P_ij (eqs. highorder,
+    LambdaArrangement with every limiter = 1). The mesh has non-uniform m_i."""
+    mesh, orc, U = _graded_state()
+    _, tau, tr = orc.forward_euler(U, trace=True)
+    rows = mesh.row_of_entry()
+    FH = tr["FH"]
+    BF = np.stack([np.bincount(rows, weights=-(mesh.mij / mesh.mi[mesh.col]) * FH[s, mesh.col],
+                               minlength=mesh.n) for s in range(4)])
+    BF += FH  # the delta_ij part of b_ij
+    UH = U + tau * (FH + BF) / mesh.mi
+    card = np.diff(mesh.row_ptr)
+    lam = 1.0 / (card - 1)
+    sumP = np.stack([np.bincount(rows, weights=lam[rows] * tr["P"][s], minlength=mesh.n) for s in range(4)])
+    scale = np.abs(U).max()
+    assert np.abs(tr["UL"] + sumP - UH).max() <= 1e-12 * scale
+    assert np.ptp(mesh.mi) > 0.5 * mesh.mi.max()  # a graded mesh: b_ij != b_ji
+
+
+def test_cfl_step_closed_form_at_rest():
+    """For a uniform state at rest every lambda_max equals the sound speed a,
+    so d_ij = a |c_ij| and tau = c_cfl min_i m_i / (2 a sum_{j != i} |c_ij|) (eq. dtCfl)."""
+    for mesh in (M.periodic_p1_square(10), M.structured_q1(9, 6, periodic_x=True, periodic_y=True)):
+        U = W.uniform_state(mesh, 1.0, (0.0, 0.0), 1.0)
+        a = math.sqrt(GAMMA)
+        rows = mesh.row_of_entry()
+        norms = np.linalg.norm(mesh.cij, axis=0)
+        T = H.transpose_index(mesh)
+        # value of the (min(i,j), max(i,j)) entry
+        upper = np.where(mesh.col > rows, norms, norms[T])
+        off = rows != mesh.col
+        dii = a * np.bincount(rows[off], weights=upper[off], minlength=mesh.n)
+        expect = 0.5 * np.min(mesh.mi / (2.0 * dii))
+        orc = oracle.Oracle(mesh, cfl=0.5)
+        assert math.isclose(orc.cfl_dt(U), expect, rel_tol=1e-13)
+
+
+def test_indicator_properties():
+    """alpha in [0,1]; alpha = 0 for uniform states; alpha = O(h) in the smooth
+    vortex; nonzero only where the solution varies."""
+    means = []
+    for nv in (32, 64, 128):
+        mesh = M.periodic_p1_square(nv)
+        _, _, tr = oracle.Oracle(mesh).forward_euler(W.isentropic_vortex(mesh), trace=True)
+        a = tr["alpha"]
+        assert np.all((a >= 0) & (a <= 1))
+        core = np.hypot(*mesh.coords.T) < 3.0
+        means.append(a[core].mean())
+        assert a[core].max() < 0.5
+    assert means[0] / means[1] > 1.6 and means[1] / means[2] > 1.6
+    mesh = M.periodic_p1_square(16)
+    _, _, tr = oracle.Oracle(mesh).forward_euler(W.uniform_state(mesh, 1.0, (1.0, 2.0), 1.0), trace=True)
+    assert np.all(tr["alpha"] == 0.0)
+    # Sod: alpha vanishes in the uniform regions and peaks inside the wave fan
+    strip = W.riemann_strip(100)
+    U = W.riemann_initial(strip, "sod")
+    orc = oracle.Oracle(strip)
+    U, t = orc.run(U, 30)
+    _, _, tr = orc.forward_euler(U, trace=True)
+    x = strip.coords[:, 0]
+    rl, ul, pl, rr, ur, pr, _ = W.RIEMANN_CASES["sod"]
+    head = 0.5 + (ul - math.sqrt(GAMMA * pl / rl)) * t
+    shock = 0.5 + RE.max_wave_speed(rl, ul, pl, rr, ur, pr)[0][()] * t
+    outside = (x < head - 0.05) | (x > shock + 0.05)  # numerical smearing: a few cells
+    assert np.all(tr["alpha"][outside] < 1e-3)
+    assert np.all(tr["alpha"][x < 0.3] < 1e-12)  # exactly uniform there
+    assert tr["alpha"][~outside].max() > 0.02
+
+
+# ---------------------------------------------------------------------------
+# convergence to exact solutions
+# ---------------------------------------------------------------------------
+
+def _riemann_errors(case, sizes=(100, 200, 400), relax=False):
+    errs = []
+    for nx in sizes:
+        mesh = W.riemann_strip(nx)
+        orc = oracle.Oracle(mesh, bound_relaxation=relax)
+        data = W.RIEMANN_CASES[case]
+        U, t, _ = orc.run_to(W.riemann_initial(mesh, case), data[-1])
+        rho, _, _ = RE.sample(mesh.coords[:, 0], t, *data[:6])
+        errs.append((mesh.mi * np.abs(U[0] - rho)).sum() / (mesh.mi * rho).sum())
+        assert orc.count_not_admissible(U) == 0
+    return np.array(errs)
+
+
+@pytest.mark.parametrize("case", sorted(W.RIEMANN_CASES))
+def test_riemann_problems_converge_to_exact_solution(case):
+    """L1 density error on a quasi-1D strip decreases at a rate >= 0.6 (the
+    rate of contacts and shocks is between 1/2 and 1 for this scheme)."""
+    e = _riemann_errors(case)
+    rates = np.log2(e[:-1] / e[1:])
+    assert np.all(rates >= 0.6), (e, rates)
+    assert e[-1] < {"sod": 0.01, "lax": 0.02, "strong_shock": 0.05, "double_rarefaction": 0.01}[case]
+
+
+def _vortex_errors(relax, sizes=(32, 64, 128), t_final=2.0):
+    errs = []
+    for nv in sizes:
+        mesh = M.periodic_p1_square(nv)
+        orc = oracle.Oracle(mesh, bound_relaxation=relax)
+        U, t, _ = orc.run_to(W.isentropic_vortex(mesh), t_final)
+        ex = W.isentropic_vortex(mesh, t=t)
+        errs.append((mesh.mi * np.abs(U[0] - ex[0])).sum() / (mesh.mi * ex[0]).sum())
+    return np.array(errs)
+
+
+def test_vortex_second_order_with_relaxed_bounds():
+    """Second-order convergence on the isentropic vortex (the abstract's claim)
+    once the local bounds are relaxed by O(h^1.5) at smooth extrema."""
+    e = _vortex_errors(True)
+    rates = np.log2(e[:-1] / e[1:])
+    assert np.all(rates >= 1.8), (e, rates)
+
+
+def test_vortex_converges_with_strict_bounds():
+    """With the paper's strict bounds, clipping at the smooth density minimum
+    limits the rate, but the error still decreases."""
+    e = _vortex_errors(False)
+    rates = np.log2(e[:-1] / e[1:])
+    assert np.all(rates >= 0.5), (e, rates)
+    assert e[-1] < 1.5e-3
