@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the hyperbolic (Euler) step: DOF-updates per second per RK stage.
+
+Workload (default): Mach-3 flow past a cylinder, Q1 quadrilaterals, channel
+[0,4]x[0,1] minus the disc r = 0.25 at (0.6, 0.5), ~4.0M vertices, inflow
+rho = 1.4, u = (3, 0), p = 1, slip walls, do-nothing outflow, SSPRK(3,3) at
+CFL 0.5, FP64, strict local bounds. One "step" is one SSPRK(3,3) step = three
+forward-Euler stages (all kernels of the hot path).
+
+value   : vertices x 3 stages x steps x ranks / max-over-ranks device time of
+          the timed steps (CUDA events on the solver's stream, inputs resident).
+e2e     : the same metric through the C ABI with host buffers: every step
+          copies the state from pinned host memory in (eh_set_state) and back
+          out (eh_get_state), inside the timed region.
+roofline: the kernel with the largest share of the step time (CUDA events
+          around each kernel on the solver's stream), its algorithmic bytes per
+          launch over its mean duration, against the measured HBM copy rate.
+cpu_baseline : the FP64 oracle on the host cores, on a window of the same mesh.
+
+--impl reference runs the oracle (the CPU reference of this repository) for
+the same workload and metric. Multi-GPU (torchrun): independent replicas, one
+per GPU, no collective on the data path (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/s per RK stage"
+UNIT = "DOF-updates/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("cylinder", "vortex"), default="cylinder")
+    ap.add_argument("--vertices", type=int, default=4_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+            td.init_process_group(backend="nccl" if self._cuda() else "gloo")
+            self.pg = td
+
+    @staticmethod
+    def _cuda():
+        import torch
+        return torch.cuda.is_available()
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if self.pg is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda" if self._cuda() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows if len(r) >= 9 for q in range(4)
+                          if r[5 + q].strip().lower() in ("active", "1")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_workload(args):
+    from paper_2106_02159_gb300 import meshes, workloads
+    if args.workload == "vortex":
+        w = workloads.vortex_workload(64)
+        desc = "2D isentropic vortex, P1 64x64-vertex periodic mesh of [-5,5]^2, CFL 0.5, FP64"
+    else:
+        m = meshes.cylinder_m_for_vertices(args.vertices)
+        mesh, U0, bs = workloads.cylinder_problem(m)
+        w = workloads.Workload(f"cylinder-q1-m{m}", mesh, U0, bs, 2000)
+        desc = ("2D Mach-3 cylinder channel, Q1, ring-graded O-grid + Cartesian blocks, "
+                f"{mesh.n} vertices, CFL 0.5, FP64, strict local bounds")
+    return w, desc
+
+
+def algorithmic_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
+    """Bytes each kernel must move at least once per launch (every array it
+    reads or writes, each element once; neighbour gathers counted once).
+    S = dim + 2 state components, SP = padded stride, REC = node record."""
+    S = dim + 2
+    SP = 4 if dim == 2 else 6
+    rec = 8 * (2 * dim + 9)            # node record fields written by prep
+    per = {
+        "prep": (8 * S + rec, 0),
+        "visc": (8 + rec + 8 + 1, 4 + 8 * dim + 8 + 8 * S + 8 + 4 / 2),
+        "low": (8 + 8 * (S + 1) + 8 * 3 + 8 * SP * 2 + 8 * 4, 4 + 8 + 8 * S),
+        "lim1": (8 + 8 * S + 8 * SP * 2 + 8 + 8 * 4 + 8 + 8 * SP, 4 + 8 * 3 + 8 * SP + 8),
+        "pass": (8 + 8 * SP * 2 + 8 * 4, 4 + 4 + 8 + 8 * SP * 2 + 8),
+        "final": (8 + 8 * SP + 8 * S * 2 + 4, 4 + 4 + 8 + 8 * SP),
+        "tau": (0, 0),
+    }[kernel]
+    return per[0] * n + per[1] * nnz
+
+
+def peaks():
+    try:
+        d = json.load(open(MEASURED_PEAKS))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on a window of the same mesh
+# ---------------------------------------------------------------------------
+
+def window_sample(mesh, U0, bs, x0=0.35, x1=0.85):
+    """Rows with x in [x0, x1] (the cylinder and its bow shock) and the
+    entries among them; the cut rows keep fewer neighbours (a timing sample)."""
+    import dataclasses
+    keep = (mesh.coords[:, 0] >= x0) & (mesh.coords[:, 0] <= x1)
+    old = np.nonzero(keep)[0]
+    new_of_old = np.full(mesh.n, -1, dtype=np.int64)
+    new_of_old[old] = np.arange(old.size)
+    rows = mesh.row_of_entry()
+    sel = keep[rows] & keep[mesh.col]
+    r2 = new_of_old[rows[sel]]
+    row_ptr = np.zeros(old.size + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(np.bincount(r2, minlength=old.size))
+    bsel = keep[mesh.bnd_node]
+    sm = dataclasses.replace(mesh, name=mesh.name + "-window", coords=mesh.coords[old], row_ptr=row_ptr,
+                             col=new_of_old[mesh.col[sel]].astype(np.int32),
+                             cij=np.ascontiguousarray(mesh.cij[:, sel]), mij=mesh.mij[sel], mi=mesh.mi[old],
+                             bnd_node=new_of_old[mesh.bnd_node[bsel]].astype(np.int32),
+                             bnd_kind=mesh.bnd_kind[bsel], bnd_normal=np.ascontiguousarray(mesh.bnd_normal[:, bsel]),
+                             bnd_mass_full=mesh.bnd_mass_full[bsel],
+                             bnd_normal_full=np.ascontiguousarray(mesh.bnd_normal_full[:, bsel]))
+    return sm, np.ascontiguousarray(U0[:, old]), None if bs is None else np.ascontiguousarray(bs[:, bsel])
+
+
+class OracleSample:
+    """The oracle as it stands, on a sample of the workload (a window of the
+    same mesh for large meshes, the full mesh otherwise)."""
+
+    def __init__(self, w):
+        import oracle
+        self.threads = oracle.set_threads(0)
+        if w.mesh.n > 200_000:
+            mesh, U0, bs = window_sample(w.mesh, w.U0, w.bnd_state)
+            self.sample = f"rows with x in [0.35, 0.85] of the same mesh ({mesh.n} vertices)"
+        else:
+            mesh, U0, bs = w.mesh, w.U0, w.bnd_state
+            self.sample = f"the full mesh ({mesh.n} vertices)"
+        self.n = mesh.n
+        self.orc = oracle.Oracle(mesh, cfl=w.cfl, bnd_state=bs)
+        self.U = self.orc.apply_bc(U0)
+
+    def step(self):
+        self.U, _, _ = self.orc.ssprk3_step(self.U)
+
+
+def cpu_baseline(w, seconds: float):
+    """Times the oracle: SSPRK(3,3) steps on the sample for ~``seconds``."""
+    smp = OracleSample(w)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        smp.step()
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    value = smp.n * 3 * steps / el
+    return {"value": value, "unit": UNIT, "cores": smp.threads, "kind": "oracle",
+            "sample": f"{steps} SSPRK(3,3) steps on {smp.sample}, FP64 C oracle, {smp.threads} OpenMP threads, "
+                      f"{el:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args, dist):
+    """The oracle as the reference arm: each step is one SSPRK(3,3) step on
+    the sample; rank 0 only."""
+    if dist.rank != 0:
+        return
+    w, desc = make_workload(args)
+    smp = OracleSample(w)
+    for _ in range(args.warmup):
+        smp.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        smp.step()
+    el = time.perf_counter() - t0
+    value = smp.n * 3 * args.steps / el
+    cb = {"value": value, "unit": UNIT, "cores": smp.threads, "kind": "oracle",
+          "sample": f"{args.steps} SSPRK(3,3) steps on {smp.sample}, FP64 C oracle, {smp.threads} OpenMP threads"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "vertices": w.mesh.n, "nnz": w.mesh.nnz},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, dist):
+    import torch
+    from paper_2106_02159_gb300 import binding
+    torch.cuda.set_device(dist.local_rank)
+    binding.build()
+    w, desc = make_workload(args)
+    mesh = w.mesh
+    S = mesh.dim + 2
+    stream = torch.cuda.Stream()
+    solver = binding.Solver(dim=mesh.dim, cfl=w.cfl, gamma=w.gamma, device=dist.local_rank,
+                            stream=stream.cuda_stream)
+    solver.upload_mesh(mesh, w.bnd_state)
+    solver.set_state(w.U0)
+    solver.apply_boundary_conditions()
+    solver.run(args.warmup)
+    solver.synchronize()
+
+    # ---- device-timed steps ----
+    clocks = Clocks(dist.local_rank)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.run(args.steps)
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    solver.synchronize()
+    diag = solver.diagnostics()
+    dist.barrier()
+    ms = dist.max(ms)
+    per_step_ms = ms / args.steps
+    value = mesh.n * 3 * args.steps * dist.world / (ms * 1e-3)
+
+    # ---- per-kernel event timing (same kernels, eager launches) ----
+    solver.profile(True)
+    solver.run(args.profile_steps)
+    prof = solver.profile_read()
+    solver.profile(False)
+    total = sum(v[0] for v in prof.values())
+    shares = {k: v[0] / total for k, v in prof.items() if v[1]}
+    top = max(shares, key=shares.get)
+    top_ms = prof[top][0] / prof[top][1]
+    hbm, hbm_src = peaks()
+    bytes_top = algorithmic_bytes(top, mesh.n, mesh.nnz, mesh.dim)
+    achieved = bytes_top / (top_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"k_{top}", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": hbm_src,
+                "algorithmic_bytes_per_launch": bytes_top, "mean_launch_ms": top_ms,
+                "kernel_shares": {k: round(v, 4) for k, v in sorted(shares.items(), key=lambda t: -t[1])}}
+
+    # ---- end to end through the C ABI with host buffers ----
+    host_in = torch.empty((S, mesh.n), dtype=torch.float64, pin_memory=True).numpy()
+    host_out = torch.empty((S, mesh.n), dtype=torch.float64, pin_memory=True).numpy()
+    solver.get_state(host_in)
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        solver.set_state(host_in)
+        solver.step(sync=False)
+        solver.get_state(host_out)
+        host_in, host_out = host_out, host_in
+    e2e_s = dist.max(time.perf_counter() - t0)
+    e2e_value = mesh.n * 3 * args.e2e_steps * dist.world / e2e_s
+
+    cb = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w, args.cpu_seconds)
+    if dist.rank == 0:
+        launches = solver.launches_per_step()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "vertices": mesh.n, "nnz": mesh.nnz, "rk_stages_per_step": 3,
+                       "limiter_passes": 2, "parallelism": f"replicas x{dist.world}",
+                       "l2": "inputs larger than L2 (edge arrays ~{:.1f} GB per stage)".format(
+                           mesh.nnz * 150 / 1e9),
+                       "invariant_violations": diag["not_admissible"],
+                       "cfl_violations": diag["cfl_violations"]},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * S * mesh.n,
+                    "d2h_bytes_per_step": 8 * S * mesh.n},
+            "gpu_launches": launches * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cb,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * euler_hyp.h -- C ABI of the GB300 (sm_103a) hyperbolic Euler solver.
+ *
+ * The library advances the compressible Euler equations (the hyperbolic
+ * operator S_H of Guermond, Kronbichler, Maier, Popov & Tomas,
+ * arXiv:2106.02159) on continuous P1/Q1 finite elements: one forward-Euler
+ * step is Algorithm 1 of the paper's Appendix B (graph viscosity, low-order
+ * update, local bounds, high-order fluxes, convex limiting with two
+ * symmetrised passes), followed by the boundary post-processing of Sec. 4,
+ * inside the SSPRK(3,3) time loop of Sec. 4.1 (eq. SPPRK33).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an eh_status and never aborts the process. On
+ *    failure eh_last_error() describes the cause.
+ *  - State vectors are component-major: U[s * n + i], s = 0 density,
+ *    1..dim momentum, dim+1 total energy (S = dim + 2 components).
+ *  - Host arrays passed to eh_upload_mesh are copied; the caller keeps
+ *    ownership. Device pointers (is_device_ptr = 1) are only read or written
+ *    during the call, on the context's stream.
+ *  - All device memory is owned by the context and freed by eh_destroy.
+ *  - Work is queued on the context's stream; eh_step/eh_run do not
+ *    synchronise unless a host result is requested.
+ */
+#ifndef EULER_HYP_H
+#define EULER_HYP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eh_ctx eh_ctx;
+
+typedef enum {
+  EH_OK = 0,
+  EH_ERR_INVALID_ARG = 1,     /* a NULL pointer, a size or a parameter out of range */
+  EH_ERR_OOM = 2,             /* device memory allocation failed */
+  EH_ERR_BAD_MESH = 3,        /* CSR not sorted / no diagonal / pattern not symmetric / bad boundary list */
+  EH_ERR_NOT_ADMISSIBLE = 4,  /* a state with rho <= 0 or internal energy <= 0 (Sec. 2.1, set A) */
+  EH_ERR_CFL = 5,             /* a prescribed dt above the invariant-domain limit (Sec. 3.1, c_cfl <= 1) */
+  EH_ERR_CUDA = 6,            /* a CUDA runtime error */
+  EH_ERR_STATE = 7            /* called out of order (e.g. eh_step before a mesh and a state) */
+} eh_status;
+
+/* Boundary kinds (Sec. 4): slip (eq. slip_bc), supersonic inflow = Dirichlet
+ * state (eq. Supersonic_inflow), supersonic outflow = do nothing
+ * (eq. Supersonic_outflow). */
+enum { EH_BC_SLIP = 1, EH_BC_DIRICHLET = 2, EH_BC_DO_NOTHING = 3 };
+
+/* Arithmetic of the step. FP64: everything in IEEE double. MIXED: c_ij,
+ * lambda_max, d_ij and the high-order fluxes in FP32; state, bounds, limiter
+ * and dt in FP64. */
+enum { EH_PRECISION_FP64 = 0, EH_PRECISION_MIXED = 1 };
+
+typedef struct {
+  int dim;              /* 2 or 3 */
+  double gamma;         /* ratio of specific heats, 1 < gamma <= 5/3 (lambda_max is a bound there) */
+  double cfl;           /* c_cfl of eq. dtCfl, 0 < cfl <= 1 */
+  int limiter_passes;   /* limiting passes of Sec. 3.3, >= 1 (the paper uses 2) */
+  int bound_relaxation; /* 0: strict local bounds (the paper's text); 1: bounds scaled by
+                           (1 -/+ r_i), r_i = (m_i / sum_j m_j)^(1.5/dim) */
+  int precision;        /* EH_PRECISION_* */
+  int device;           /* CUDA device ordinal */
+  void *stream;         /* cudaStream_t to run on, or NULL for a stream owned by the context */
+} eh_config;
+
+typedef struct {
+  double t;                   /* simulated time advanced by eh_step/eh_run */
+  int64_t steps;              /* SSPRK(3,3) steps taken */
+  double last_dt;             /* dt of the last step */
+  double last_stage_bound[3]; /* c_cfl min_i m_i / (2 |d_ii|) of the last step's three stages */
+  int64_t cfl_violations;     /* stages 2-3 whose dt exceeded min_i m_i/(2|d_ii|) (c_cfl = 1) */
+  int64_t not_admissible;     /* non-admissible nodes found after a step (0 unless an error) */
+} eh_diagnostics;
+
+/* Fills *cfg with the defaults: dim 2, gamma 1.4, cfl 0.5, 2 limiter passes,
+ * strict bounds, FP64, device 0, own stream. */
+void eh_config_default(eh_config *cfg);
+
+/* Creates a context on cfg->device. Returns EH_ERR_INVALID_ARG for an
+ * out-of-range parameter. *out receives the context (NULL on error). */
+eh_status eh_create(const eh_config *cfg, eh_ctx **out);
+
+/* Uploads a mesh (Sec. 2.2). Host pointers, copied.
+ *   n, nnz        : nodes and CSR entries (diagonal included), nnz < 2^31
+ *   row_ptr[n+1]  : int64 CSR offsets; col[nnz] int32 columns, sorted and
+ *                   unique within a row, diagonal present, pattern symmetric
+ *   cij[dim][nnz] : c_ij = int phi_i grad phi_j (component-major)
+ *   mij[nnz]      : consistent mass m_ij; mi[n]: lumped mass m_i > 0
+ *   n_bnd, bnd_node[n_bnd], bnd_kind[n_bnd] (EH_BC_*): every node on the
+ *                   boundary, once (nodes not listed are interior)
+ *   bnd_normal[dim][n_bnd] : unit slip normal n^s_i of eq. def_ns_nio (read for slip nodes)
+ *   bnd_state[S][n_bnd]    : Dirichlet states (read for Dirichlet nodes; may be
+ *                            NULL if there are none)
+ * The library builds the transpose index itself. Errors: EH_ERR_BAD_MESH for
+ * an invalid pattern or boundary list, EH_ERR_OOM. A second call replaces the
+ * mesh and invalidates the state. */
+eh_status eh_upload_mesh(eh_ctx *ctx, int32_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                         const double *cij, const double *mij, const double *mi, int32_t n_bnd,
+                         const int32_t *bnd_node, const int32_t *bnd_kind, const double *bnd_normal,
+                         const double *bnd_state);
+
+/* Sets the state U[S][n] (host or device pointer). Returns
+ * EH_ERR_NOT_ADMISSIBLE (state left unset) if some node has rho <= 0 or
+ * internal energy <= 0. Synchronises the stream. */
+eh_status eh_set_state(eh_ctx *ctx, const double *U, int is_device_ptr);
+
+/* Copies the state into U_out[S][n] (host or device pointer). Synchronises
+ * and reports a pending device-side error (EH_ERR_CFL, EH_ERR_NOT_ADMISSIBLE). */
+eh_status eh_get_state(eh_ctx *ctx, double *U_out, int is_device_ptr);
+
+/* Applies the boundary post-processing of Sec. 4 to the current state (use
+ * once on initial data that does not satisfy the boundary conditions). */
+eh_status eh_apply_boundary_conditions(eh_ctx *ctx);
+
+/* CFL time step tau = c_cfl min_i m_i / (2 |d_ii|) of the current state
+ * (Sec. 3.1, eq. dtCfl). Synchronises. */
+eh_status eh_cfl_dt(eh_ctx *ctx, double *dt);
+
+/* One forward-Euler stage (Algorithm 1) plus boundary post-processing applied
+ * to the current state: U <- BC(FE(U)). tau > 0: that step; tau <= 0: the
+ * stage's CFL step. tau_used may be NULL (then no synchronisation). */
+eh_status eh_stage(eh_ctx *ctx, double tau, double *tau_used);
+
+/* One SSPRK(3,3) step. dt > 0: that step (EH_ERR_CFL if it exceeds the
+ * invariant-domain limit of the first stage; the state is then unchanged);
+ * dt <= 0: the CFL step of the first stage, reused by stages 2 and 3.
+ * dt_used may be NULL (then no synchronisation). */
+eh_status eh_step(eh_ctx *ctx, double dt, double *dt_used);
+
+/* nsteps SSPRK(3,3) steps with the same dt rule as eh_step, replayed from a
+ * CUDA graph, without synchronising. */
+eh_status eh_run(eh_ctx *ctx, int32_t nsteps, double dt);
+
+/* Waits for queued work and reports a pending device-side error. */
+eh_status eh_synchronize(eh_ctx *ctx);
+
+/* Diagnostics of the last steps (synchronises). */
+eh_status eh_get_diagnostics(eh_ctx *ctx, eh_diagnostics *out);
+
+/* Intermediate arrays of the last forward-Euler stage, for checking against
+ * a reference (synchronises). 'what' selects one of EH_TRACE_*; host_out must
+ * hold 'count' doubles, which must equal the array's size:
+ *   D_IJ [nnz] graph viscosity d^L_ij (diagonal included)
+ *   ALPHA [n] indicator alpha_i
+ *   U_LOW [S][n] low-order update U^L
+ *   F_HIGH [S][n] high-order fluxes F^H_i
+ *   BOUNDS [3][n] rho_min, rho_max, Phi_min
+ *   L_PASS1 [nnz] symmetrised limiter of the first pass (1 on the diagonal)
+ *   U_PASS1 [S][n] state after the first limiting pass
+ *   TAU [1] the stage's tau; TAU_BOUND [1] its own CFL bound */
+enum {
+  EH_TRACE_D_IJ = 0, EH_TRACE_ALPHA = 1, EH_TRACE_U_LOW = 2, EH_TRACE_F_HIGH = 3, EH_TRACE_BOUNDS = 4,
+  EH_TRACE_L_PASS1 = 5, EH_TRACE_U_PASS1 = 6, EH_TRACE_TAU = 7, EH_TRACE_TAU_BOUND = 8
+};
+eh_status eh_trace(eh_ctx *ctx, int what, double *host_out, int64_t count);
+
+/* Per-kernel timing with CUDA events on the context's stream, for profiling.
+ * While enabled, eh_step/eh_stage/eh_run launch eagerly (no graph) and record
+ * an event pair around every kernel. eh_profile_read returns, for one kernel
+ * kind (EH_KERNEL_*), the summed duration in milliseconds and the number of
+ * launches since profiling was enabled (synchronises). */
+enum {
+  EH_KERNEL_PREP = 0, EH_KERNEL_VISC = 1, EH_KERNEL_LOW = 2, EH_KERNEL_TAU = 3, EH_KERNEL_LIM1 = 4,
+  EH_KERNEL_PASS = 5, EH_KERNEL_FINAL = 6, EH_KERNEL_COUNT = 7
+};
+eh_status eh_profile_enable(eh_ctx *ctx, int enable);
+eh_status eh_profile_read(eh_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
+
+/* Number of kernel launches one eh_step issues (for accounting). */
+int32_t eh_launches_per_step(const eh_ctx *ctx);
+
+/* Text of the last error of this context (never NULL). */
+const char *eh_last_error(const eh_ctx *ctx);
+
+/* Name of a status code (never NULL). */
+const char *eh_status_string(eh_status st);
+
+/* Frees every resource of the context; NULL is a no-op. */
+void eh_destroy(eh_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EULER_HYP_H */

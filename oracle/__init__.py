@@ -26,11 +26,32 @@ BC_SLIP, BC_DIRICHLET, BC_DO_NOTHING = 1, 2, 3
 _lib = None
 
 
-def build(force: bool = False, src: str | None = None, out: str | None = None, extra=()) -> str:
-    """Compile the oracle (or, for mutation tests, another copy of its source)."""
+_FMA_LIB_PATH = os.path.join(_BUILD, "libeuler_oracle_fma.so")
+
+
+def fma_flags():
+    """Flags of the contracted build: a*b+c fused wherever the compiler likes
+    (the rounding a GPU compiler applies by default)."""
+    import platform
+    flags = ["-ffp-contract=fast"]
+    if platform.machine() in ("x86_64", "AMD64"):
+        flags.insert(0, "-mfma")
+    return flags
+
+
+def build(force: bool = False, src: str | None = None, out: str | None = None, extra=(), variant: str = "ieee") -> str:
+    """Compile the oracle (or, for mutation tests, another copy of its source).
+
+    variant "ieee": no contraction (the reference build). variant "fma": the
+    same source with fused multiply-adds, used only to measure how much the
+    method's result moves under a different valid rounding."""
     src = src or _SRC
+    if variant == "fma" and out is None:
+        out = _FMA_LIB_PATH
+        extra = tuple(extra) + tuple(fma_flags())
     out = out or _LIB_PATH
-    if not force and out == _LIB_PATH and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+    if (not force and out in (_LIB_PATH, _FMA_LIB_PATH) and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(src)):
         return out
     os.makedirs(os.path.dirname(out), exist_ok=True)
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-fopenmp",
@@ -91,6 +112,17 @@ def _bind(lib):
     lib.oracle_run_to.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, ctypes.c_int, dp,
                                   ctypes.POINTER(ctypes.c_int)]
     return lib
+
+
+_fma_lib = None
+
+
+def load_fma():
+    """The contracted build of the same oracle source (see build())."""
+    global _fma_lib
+    if _fma_lib is None:
+        _fma_lib = _bind(ctypes.CDLL(build(variant="fma")))
+    return _fma_lib
 
 
 def load(path: str | None = None):

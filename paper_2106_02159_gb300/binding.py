@@ -1,0 +1,250 @@
+"""ctypes binding of the C ABI in ``include/euler_hyp.h``.
+
+Argument marshalling only: every step of the hyperbolic solver runs in the
+CUDA library ``libeuler_hyp.so`` built from ``csrc/`` for sm_103a. There is
+no CPU fallback: if the library is missing or no GPU is present, the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+CSRC = os.path.join(_HERE, "csrc")
+BUILD_DIR = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(BUILD_DIR, "libeuler_hyp.so")
+SOURCES = ("kernels.cu", "capi.cu")
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-shared"]
+
+EH_OK, EH_ERR_INVALID_ARG, EH_ERR_OOM, EH_ERR_BAD_MESH = 0, 1, 2, 3
+EH_ERR_NOT_ADMISSIBLE, EH_ERR_CFL, EH_ERR_CUDA, EH_ERR_STATE = 4, 5, 6, 7
+EH_BC_SLIP, EH_BC_DIRICHLET, EH_BC_DO_NOTHING = 1, 2, 3
+EH_PRECISION_FP64, EH_PRECISION_MIXED = 0, 1
+(EH_TRACE_D_IJ, EH_TRACE_ALPHA, EH_TRACE_U_LOW, EH_TRACE_F_HIGH, EH_TRACE_BOUNDS, EH_TRACE_L_PASS1,
+ EH_TRACE_U_PASS1, EH_TRACE_TAU, EH_TRACE_TAU_BOUND) = range(9)
+
+# every symbol the header declares
+EXPORTS = ("eh_config_default", "eh_create", "eh_upload_mesh", "eh_set_state", "eh_get_state",
+           "eh_apply_boundary_conditions", "eh_cfl_dt", "eh_stage", "eh_step", "eh_run", "eh_synchronize",
+           "eh_get_diagnostics", "eh_trace", "eh_profile_enable", "eh_profile_read", "eh_launches_per_step",
+           "eh_last_error", "eh_status_string", "eh_destroy")
+KERNEL_NAMES = ("prep", "visc", "low", "tau", "lim1", "pass", "final")
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libeuler_hyp.so for sm_103a (nvcc; no GPU needed)."""
+    srcs = [os.path.join(CSRC, s) for s in SOURCES]
+    deps = srcs + [os.path.join(CSRC, "kernels.cuh"), os.path.join(_ROOT, "include", "euler_hyp.h")]
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(d) for d in deps):
+        return LIB_PATH
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    tmp = LIB_PATH + ".tmp"
+    cmd = ["nvcc", *NVCC_FLAGS, "-o", tmp, *srcs]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("limiter_passes", ctypes.c_int), ("bound_relaxation", ctypes.c_int), ("precision", ctypes.c_int),
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Diagnostics(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_int64), ("last_dt", ctypes.c_double),
+                ("last_stage_bound", ctypes.c_double * 3), ("cfl_violations", ctypes.c_int64),
+                ("not_admissible", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the library (built in-tree). Raises OSError if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: run paper_2106_02159_gb300.binding.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(path)
+    vp, dp, i32, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int64
+    lib.eh_config_default.argtypes = [ctypes.POINTER(Config)]
+    lib.eh_config_default.restype = None
+    lib.eh_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+    lib.eh_upload_mesh.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
+    lib.eh_set_state.argtypes = [vp, vp, ctypes.c_int]
+    lib.eh_get_state.argtypes = [vp, vp, ctypes.c_int]
+    lib.eh_apply_boundary_conditions.argtypes = [vp]
+    lib.eh_cfl_dt.argtypes = [vp, dp]
+    lib.eh_stage.argtypes = [vp, ctypes.c_double, dp]
+    lib.eh_step.argtypes = [vp, ctypes.c_double, dp]
+    lib.eh_run.argtypes = [vp, i32, ctypes.c_double]
+    lib.eh_synchronize.argtypes = [vp]
+    lib.eh_get_diagnostics.argtypes = [vp, ctypes.POINTER(Diagnostics)]
+    lib.eh_trace.argtypes = [vp, ctypes.c_int, dp, i64]
+    lib.eh_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.eh_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(i64)]
+    lib.eh_launches_per_step.argtypes = [vp]
+    lib.eh_launches_per_step.restype = i32
+    lib.eh_last_error.argtypes = [vp]
+    lib.eh_last_error.restype = ctypes.c_char_p
+    lib.eh_status_string.argtypes = [ctypes.c_int]
+    lib.eh_status_string.restype = ctypes.c_char_p
+    lib.eh_destroy.argtypes = [vp]
+    lib.eh_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("eh_config_default", "eh_destroy", "eh_launches_per_step", "eh_last_error",
+                        "eh_status_string"):
+            getattr(lib, name).restype = ctypes.c_int
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+class EulerError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Solver:
+    """One context of the C library (eh_create ... eh_destroy)."""
+
+    def __init__(self, dim=2, gamma=1.4, cfl=0.5, limiter_passes=2, bound_relaxation=False, device=0, stream=None,
+                 precision=EH_PRECISION_FP64, lib=None):
+        self.lib = lib or load()
+        cfg = Config()
+        self.lib.eh_config_default(ctypes.byref(cfg))
+        cfg.dim, cfg.gamma, cfg.cfl, cfg.limiter_passes = dim, gamma, cfl, limiter_passes
+        cfg.bound_relaxation, cfg.precision, cfg.device = int(bool(bound_relaxation)), precision, device
+        cfg.stream = stream
+        self.cfg = cfg
+        self.dim, self.S = dim, dim + 2
+        ctx = ctypes.c_void_p()
+        st = self.lib.eh_create(ctypes.byref(cfg), ctypes.byref(ctx))
+        if st != EH_OK:
+            raise EulerError(st, f"eh_create failed: {self.lib.eh_status_string(st).decode()}")
+        self.ctx = ctx
+        self.n = self.nnz = 0
+
+    def _check(self, st, what):
+        if st != EH_OK:
+            raise EulerError(st, f"{what}: {self.lib.eh_last_error(self.ctx).decode()}")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.eh_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+    def upload_mesh(self, mesh, bnd_state=None):
+        self._mesh_keep = k = dict(
+            row_ptr=_arr(mesh.row_ptr, np.int64), col=_arr(mesh.col, np.int32), cij=_arr(mesh.cij, np.float64),
+            mij=_arr(mesh.mij, np.float64), mi=_arr(mesh.mi, np.float64), bnd_node=_arr(mesh.bnd_node, np.int32),
+            bnd_kind=_arr(mesh.bnd_kind, np.int32), bnd_normal=_arr(mesh.bnd_normal, np.float64),
+            bnd_state=None if bnd_state is None else _arr(bnd_state, np.float64))
+        st = self.lib.eh_upload_mesh(self.ctx, mesh.n, mesh.nnz, _p(k["row_ptr"]), _p(k["col"]), _p(k["cij"]),
+                                     _p(k["mij"]), _p(k["mi"]), mesh.n_bnd, _p(k["bnd_node"]), _p(k["bnd_kind"]),
+                                     _p(k["bnd_normal"]), _p(k["bnd_state"]))
+        self._check(st, "eh_upload_mesh")
+        self.n, self.nnz = mesh.n, mesh.nnz
+        del self._mesh_keep
+
+    def set_state(self, U):
+        """U: numpy [S, n] (host) or a CUDA tensor of that shape (device)."""
+        if hasattr(U, "is_cuda") and U.is_cuda:
+            assert U.is_contiguous() and tuple(U.shape) == (self.S, self.n)
+            self._check(self.lib.eh_set_state(self.ctx, ctypes.c_void_p(U.data_ptr()), 1), "eh_set_state")
+        else:
+            U = _arr(U, np.float64)
+            assert U.shape == (self.S, self.n), U.shape
+            self._check(self.lib.eh_set_state(self.ctx, _p(U), 0), "eh_set_state")
+
+    def get_state(self, out=None):
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            self._check(self.lib.eh_get_state(self.ctx, ctypes.c_void_p(out.data_ptr()), 1), "eh_get_state")
+            return out
+        U = np.empty((self.S, self.n)) if out is None else out
+        self._check(self.lib.eh_get_state(self.ctx, _p(U), 0), "eh_get_state")
+        return U
+
+    def apply_boundary_conditions(self):
+        self._check(self.lib.eh_apply_boundary_conditions(self.ctx), "eh_apply_boundary_conditions")
+
+    def cfl_dt(self) -> float:
+        dt = ctypes.c_double(0.0)
+        self._check(self.lib.eh_cfl_dt(self.ctx, ctypes.byref(dt)), "eh_cfl_dt")
+        return dt.value
+
+    def stage(self, tau=0.0, sync=True):
+        used = ctypes.c_double(0.0)
+        self._check(self.lib.eh_stage(self.ctx, float(tau), ctypes.byref(used) if sync else None), "eh_stage")
+        return used.value if sync else None
+
+    def step(self, dt=0.0, sync=True):
+        used = ctypes.c_double(0.0)
+        self._check(self.lib.eh_step(self.ctx, float(dt), ctypes.byref(used) if sync else None), "eh_step")
+        return used.value if sync else None
+
+    def run(self, nsteps, dt=0.0):
+        self._check(self.lib.eh_run(self.ctx, int(nsteps), float(dt)), "eh_run")
+
+    def synchronize(self):
+        self._check(self.lib.eh_synchronize(self.ctx), "eh_synchronize")
+
+    def diagnostics(self) -> dict:
+        d = Diagnostics()
+        self._check(self.lib.eh_get_diagnostics(self.ctx, ctypes.byref(d)), "eh_get_diagnostics")
+        return dict(t=d.t, steps=d.steps, last_dt=d.last_dt, last_stage_bound=list(d.last_stage_bound),
+                    cfl_violations=d.cfl_violations, not_admissible=d.not_admissible)
+
+    def trace(self, what):
+        sizes = {EH_TRACE_D_IJ: self.nnz, EH_TRACE_ALPHA: self.n, EH_TRACE_U_LOW: self.S * self.n,
+                 EH_TRACE_F_HIGH: self.S * self.n, EH_TRACE_BOUNDS: 3 * self.n, EH_TRACE_L_PASS1: self.nnz,
+                 EH_TRACE_U_PASS1: self.S * self.n, EH_TRACE_TAU: 1, EH_TRACE_TAU_BOUND: 1}
+        count = sizes[what]
+        out = np.empty(count)
+        self._check(self.lib.eh_trace(self.ctx, what, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), count),
+                    "eh_trace")
+        if what in (EH_TRACE_U_LOW, EH_TRACE_F_HIGH, EH_TRACE_U_PASS1):
+            return out.reshape(self.S, self.n)
+        if what == EH_TRACE_BOUNDS:
+            return out.reshape(3, self.n)
+        if what in (EH_TRACE_TAU, EH_TRACE_TAU_BOUND):
+            return float(out[0])
+        return out
+
+    def profile(self, enable: bool):
+        self._check(self.lib.eh_profile_enable(self.ctx, int(bool(enable))), "eh_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since profiling was enabled."""
+        out = {}
+        for k, name in enumerate(KERNEL_NAMES):
+            ms, cnt = ctypes.c_double(0.0), ctypes.c_int64(0)
+            self._check(self.lib.eh_profile_read(self.ctx, k, ctypes.byref(ms), ctypes.byref(cnt)), "eh_profile_read")
+            out[name] = (ms.value, cnt.value)
+        return out
+
+    def launches_per_step(self) -> int:
+        return int(self.lib.eh_launches_per_step(self.ctx))

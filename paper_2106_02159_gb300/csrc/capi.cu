@@ -1,0 +1,702 @@
+// capi.cu -- host side of the C ABI declared in include/euler_hyp.h: mesh
+// validation and preprocessing, device memory, the SSPRK(3,3) stage schedule
+// (Sec. 4.1, eq. SPPRK33), CUDA-graph replay and error reporting.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/euler_hyp.h"
+#include "kernels.cuh"
+
+using namespace eh;
+
+struct eh_ctx {
+  eh_config cfg{};
+  Params prm{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  // mesh
+  bool have_mesh = false, have_state = false;
+  int n = 0;
+  int64_t nnz = 0;
+  int n_bnd = 0;
+  std::vector<void *> allocs;  // every device allocation
+  MeshView mv{};
+  Work wk{};
+  // state [S][n], stage state, trace buffers
+  double *U = nullptr, *W = nullptr;
+  double *trace_lsym = nullptr, *trace_upass = nullptr, *trace_pre = nullptr;
+  DevStatus *st = nullptr;
+  DevStatus *st_host = nullptr;  // pinned
+  // host bookkeeping
+  double t = 0.0;
+  int64_t steps = 0;
+  double last_dt = 0.0;
+  bool last_stage_traced = false;
+  // graph cache for eh_run
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+  // optional per-kernel event timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_marks;  // kernel, (start, stop) event indices
+  double prof_ms[EH_KERNEL_COUNT] = {0};
+  int64_t prof_count[EH_KERNEL_COUNT] = {0};
+};
+
+namespace {
+
+const char *kStatusNames[] = {"EH_OK",         "EH_ERR_INVALID_ARG", "EH_ERR_OOM",  "EH_ERR_BAD_MESH",
+                              "EH_ERR_NOT_ADMISSIBLE", "EH_ERR_CFL",  "EH_ERR_CUDA", "EH_ERR_STATE"};
+
+eh_status fail(eh_ctx *c, eh_status st, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return st;
+}
+
+#define CUDA_TRY(c, expr)                                                                                     \
+  do {                                                                                                        \
+    cudaError_t e_ = (expr);                                                                                  \
+    if (e_ != cudaSuccess) {                                                                                  \
+      eh_status s_ = e_ == cudaErrorMemoryAllocation ? EH_ERR_OOM : EH_ERR_CUDA;                              \
+      return fail(c, s_, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__);       \
+    }                                                                                                         \
+  } while (0)
+
+template <typename T> eh_status dalloc(eh_ctx *c, T **p, size_t count) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? EH_ERR_OOM : EH_ERR_CUDA, "cudaMalloc of %zu bytes: %s",
+                count * sizeof(T), cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  *p = (T *)q;
+  return EH_OK;
+}
+
+void free_mesh(eh_ctx *c) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  for (void *q : c->allocs) cudaFree(q);
+  c->allocs.clear();
+  c->mv = MeshView{};
+  c->wk = Work{};
+  c->U = c->W = nullptr;
+  c->trace_lsym = c->trace_upass = c->trace_pre = nullptr;
+  c->have_mesh = c->have_state = false;
+}
+
+int S_of(const eh_ctx *c) { return c->cfg.dim + 2; }
+int SP_of(const eh_ctx *c) { return c->cfg.dim == 2 ? Layout<2>::SP : Layout<3>::SP; }
+
+eh_status check_device_error(eh_ctx *c) {
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  CUDA_TRY(c, cudaMemcpy(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+  int e = c->st_host->err;
+  if (e == EH_ERR_CFL) return fail(c, EH_ERR_CFL, "prescribed dt exceeds the invariant-domain limit of the first stage");
+  if (e == EH_ERR_NOT_ADMISSIBLE)
+    return fail(c, EH_ERR_NOT_ADMISSIBLE, "%llu non-admissible nodes after a step",
+                (unsigned long long)c->st_host->not_admissible);
+  if (e) return fail(c, EH_ERR_CUDA, "device error code %d", e);
+  return EH_OK;
+}
+
+// Event pair around one kernel launch when profiling is on.
+struct ProfScope {
+  eh_ctx *c;
+  int kernel;
+  size_t a = 0;
+  ProfScope(eh_ctx *c_, int k) : c(c_), kernel(k) {
+    if (!c->profiling) return;
+    a = next_event();
+    cudaEventRecord(c->ev_pool[a], c->stream);
+  }
+  size_t next_event() {
+    size_t idx = 0;
+    for (auto &m : c->ev_marks) idx = std::max(idx, std::max(m.second.first, m.second.second) + 1);
+    if (idx >= c->ev_pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->ev_pool.push_back(e);
+    }
+    return idx;
+  }
+  ~ProfScope() {
+    if (!c->profiling) return;
+    c->ev_marks.push_back({kernel, {a, a}});
+    size_t b = next_event();
+    c->ev_marks.back().second.second = b;
+    cudaEventRecord(c->ev_pool[b], c->stream);
+  }
+};
+
+void flush_profile(eh_ctx *c) {
+  if (c->ev_marks.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto &m : c->ev_marks) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev_pool[m.second.first], c->ev_pool[m.second.second]);
+    c->prof_ms[m.first] += ms;
+    c->prof_count[m.first] += 1;
+  }
+  c->ev_marks.clear();
+}
+
+// One forward-Euler stage on the component-major state Uin, written as
+// out = BC(FE(Uin)) (coef < 0) or out = U0 + coef (BC(FE(Uin)) - U0).
+template <int DIM>
+void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, const double *U0, double coef, double *out,
+                   bool trace) {
+  cudaStream_t s = c->stream;
+  const MeshView &m = c->mv;
+  const Params &p = c->prm;
+  const Work &w = c->wk;
+  { ProfScope ps(c, EH_KERNEL_PREP); launch_prep<DIM>(m, p, Uin, w, s); }
+  { ProfScope ps(c, EH_KERNEL_VISC); launch_visc<DIM>(m, p, w, s); }
+  { ProfScope ps(c, EH_KERNEL_LOW); launch_low<DIM>(m, p, w, s); }
+  { ProfScope ps(c, EH_KERNEL_TAU); launch_tau(w, stage, dt_given, p.cfl, s); }
+  { ProfScope ps(c, EH_KERNEL_LIM1); launch_lim1<DIM>(m, p, w, s); }
+  const double *ucur = w.UL;
+  double *lcur = w.la, *lnext = w.lb;
+  double *unext = w.Ua;
+  for (int pass = 1; pass < c->cfg.limiter_passes; ++pass) {
+    {
+      ProfScope ps(c, EH_KERNEL_PASS);
+      launch_pass<DIM>(m, p, w, ucur, unext, lcur, lnext, (trace && pass == 1) ? c->trace_lsym : nullptr, s);
+    }
+    if (trace && pass == 1) {
+      cudaMemcpyAsync(c->trace_upass, unext, sizeof(double) * (size_t)c->n * SP_of(c), cudaMemcpyDeviceToDevice, s);
+    }
+    ucur = unext;
+    unext = (unext == w.Ua) ? w.Ub : w.Ua;
+    std::swap(lcur, lnext);
+  }
+  {
+    ProfScope ps(c, EH_KERNEL_FINAL);
+    launch_final<DIM>(m, p, w, ucur, lcur, U0, coef, out, trace ? c->trace_pre : nullptr, s);
+  }
+}
+
+template <int DIM> void enqueue_step(eh_ctx *c, double dt) {
+  // w1 = BC(FE(u)); w2 = u + 1/4 (BC(FE(w1)) - u); u <- u + 2/3 (BC(FE(w2)) - u)
+  enqueue_stage<DIM>(c, c->U, 0, dt, nullptr, -1.0, c->W, false);
+  enqueue_stage<DIM>(c, c->W, 1, dt, c->U, 0.25, c->W, false);
+  enqueue_stage<DIM>(c, c->W, 2, dt, c->U, 2.0 / 3.0, c->U, false);
+}
+
+void enqueue_step_any(eh_ctx *c, double dt) {
+  if (c->cfg.dim == 2) enqueue_step<2>(c, dt);
+  else enqueue_step<3>(c, dt);
+}
+
+eh_status require_ready(eh_ctx *c) {
+  if (!c) return EH_ERR_INVALID_ARG;
+  if (!c->have_mesh) return fail(c, EH_ERR_STATE, "no mesh uploaded");
+  if (!c->have_state) return fail(c, EH_ERR_STATE, "no state set");
+  return EH_OK;
+}
+
+eh_status reset_status(eh_ctx *c) {
+  CUDA_TRY(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+  return EH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void eh_config_default(eh_config *cfg) {
+  if (!cfg) return;
+  cfg->dim = 2;
+  cfg->gamma = 1.4;
+  cfg->cfl = 0.5;
+  cfg->limiter_passes = 2;
+  cfg->bound_relaxation = 0;
+  cfg->precision = EH_PRECISION_FP64;
+  cfg->device = 0;
+  cfg->stream = nullptr;
+}
+
+const char *eh_status_string(eh_status st) {
+  int k = (int)st;
+  if (k < 0 || k > 7) return "EH_UNKNOWN";
+  return kStatusNames[k];
+}
+
+const char *eh_last_error(const eh_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+eh_status eh_create(const eh_config *cfg, eh_ctx **out) {
+  if (!out) return EH_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg) return EH_ERR_INVALID_ARG;
+  if (cfg->dim != 2 && cfg->dim != 3) return EH_ERR_INVALID_ARG;
+  if (!(cfg->gamma > 1.0 && cfg->gamma <= 5.0 / 3.0)) return EH_ERR_INVALID_ARG;
+  if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return EH_ERR_INVALID_ARG;
+  if (cfg->limiter_passes < 1 || cfg->limiter_passes > 8) return EH_ERR_INVALID_ARG;
+  if (cfg->precision != EH_PRECISION_FP64) return EH_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    return EH_ERR_CUDA;
+  }
+  eh_ctx *c = new eh_ctx();
+  c->cfg = *cfg;
+  c->device = cfg->device;
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    delete c;
+    return EH_ERR_CUDA;
+  }
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return EH_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cudaMalloc(&c->st, sizeof(DevStatus)) != cudaSuccess ||
+      cudaMallocHost(&c->st_host, sizeof(DevStatus)) != cudaSuccess) {
+    if (c->st) cudaFree(c->st);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return EH_ERR_OOM;
+  }
+  cudaMemset(c->st, 0, sizeof(DevStatus));
+  Params &p = c->prm;
+  p.gamma = cfg->gamma;
+  p.cfl = cfg->cfl;
+  p.gamma75 = cfg->gamma == 1.4 ? 1 : 0;
+  p.gm1 = cfg->gamma - 1.0;
+  p.z = (cfg->gamma - 1.0) / (2.0 * cfg->gamma);
+  p.inv_z = 1.0 / p.z;
+  p.kshock = (cfg->gamma + 1.0) / (2.0 * cfg->gamma);
+  *out = c;
+  return EH_OK;
+}
+
+void eh_destroy(eh_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_mesh(c);
+  if (c->st) cudaFree(c->st);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                         const double *cij, const double *mij, const double *mi, int32_t n_bnd,
+                         const int32_t *bnd_node, const int32_t *bnd_kind, const double *bnd_normal,
+                         const double *bnd_state) {
+  if (!c) return EH_ERR_INVALID_ARG;
+  if (n <= 0 || nnz <= 0 || nnz >= ((int64_t)1 << 31) || !row_ptr || !col || !cij || !mij || !mi || n_bnd < 0 ||
+      (n_bnd > 0 && (!bnd_node || !bnd_kind || !bnd_normal)))
+    return fail(c, EH_ERR_INVALID_ARG, "invalid mesh arguments");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  free_mesh(c);
+  const int dim = c->cfg.dim, S = S_of(c);
+  // ---- validation (host) ----
+  if (row_ptr[0] != 0 || row_ptr[n] != nnz) return fail(c, EH_ERR_BAD_MESH, "row_ptr must start at 0 and end at nnz");
+  for (int i = 0; i < n; ++i) {
+    if (row_ptr[i + 1] - row_ptr[i] < 2) return fail(c, EH_ERR_BAD_MESH, "row %d has fewer than 2 entries", i);
+    bool diag = false;
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      if (col[k] < 0 || col[k] >= n) return fail(c, EH_ERR_BAD_MESH, "column out of range in row %d", i);
+      if (k > row_ptr[i] && col[k] <= col[k - 1]) return fail(c, EH_ERR_BAD_MESH, "row %d not sorted/unique", i);
+      if (col[k] == i) diag = true;
+    }
+    if (!diag) return fail(c, EH_ERR_BAD_MESH, "row %d has no diagonal entry", i);
+    if (!(mi[i] > 0.0)) return fail(c, EH_ERR_BAD_MESH, "m_%d <= 0", i);
+  }
+  std::vector<int32_t> tr(nnz);
+  for (int i = 0; i < n; ++i) {
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      const int j = col[k];
+      const int32_t *b = col + row_ptr[j], *e = col + row_ptr[j + 1];
+      const int32_t *f = std::lower_bound(b, e, i);
+      if (f == e || *f != i) return fail(c, EH_ERR_BAD_MESH, "pattern not symmetric at (%d,%d)", i, j);
+      tr[k] = (int32_t)(row_ptr[j] + (f - b));
+    }
+  }
+  std::vector<double> cn(nnz), cinv(nnz), beta(nnz), betat(nnz);
+  for (int i = 0; i < n; ++i) {
+    for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+      double s2 = 0.0;
+      for (int d = 0; d < dim; ++d) s2 += cij[(int64_t)d * nnz + k] * cij[(int64_t)d * nnz + k];
+      cn[k] = std::sqrt(s2);
+      cinv[k] = cn[k] > 0.0 ? 1.0 / cn[k] : 0.0;
+      if (col[k] != i && !(cn[k] > 0.0)) return fail(c, EH_ERR_BAD_MESH, "c_ij = 0 at an off-diagonal entry");
+      beta[k] = mij[k] / mi[col[k]];
+      betat[k] = mij[tr[k]] / mi[i];
+    }
+  }
+  std::vector<double> inv_mi(n), relax(n, 0.0);
+  double area = 0.0;
+  for (int i = 0; i < n; ++i) area += mi[i];
+  for (int i = 0; i < n; ++i) {
+    inv_mi[i] = 1.0 / mi[i];
+    if (c->cfg.bound_relaxation) relax[i] = std::pow(mi[i] / area, 1.5 / dim);
+  }
+  std::vector<unsigned char> isb(n, 0);
+  std::vector<int32_t> bidx(n, -1);
+  for (int b = 0; b < n_bnd; ++b) {
+    const int i = bnd_node[b];
+    if (i < 0 || i >= n || bidx[i] >= 0) return fail(c, EH_ERR_BAD_MESH, "boundary node %d invalid or repeated", i);
+    if (bnd_kind[b] < EH_BC_SLIP || bnd_kind[b] > EH_BC_DO_NOTHING)
+      return fail(c, EH_ERR_BAD_MESH, "boundary kind %d invalid", bnd_kind[b]);
+    if (bnd_kind[b] == EH_BC_DIRICHLET && !bnd_state) return fail(c, EH_ERR_BAD_MESH, "Dirichlet node without state");
+    isb[i] = 1;
+    bidx[i] = b;
+  }
+  // ---- device arrays ----
+  eh_status st;
+  MeshView &m = c->mv;
+  m.n = n;
+  m.nnz = nnz;
+  m.n_bnd = n_bnd;
+  int64_t *d_row = nullptr;
+  int32_t *d_col = nullptr, *d_tr = nullptr, *d_bidx = nullptr, *d_bkind = nullptr;
+  double *d_cij, *d_cn, *d_cinv, *d_beta, *d_betat, *d_mi, *d_imi, *d_relax, *d_bnorm = nullptr, *d_bstate = nullptr;
+  unsigned char *d_isb;
+#define ALLOC(ptr, cnt) \
+  if ((st = dalloc(c, &ptr, (size_t)(cnt))) != EH_OK) { free_mesh(c); return st; }
+  ALLOC(d_row, n + 1);
+  ALLOC(d_col, nnz);
+  ALLOC(d_tr, nnz);
+  ALLOC(d_cij, (size_t)dim * nnz);
+  ALLOC(d_cn, nnz);
+  ALLOC(d_cinv, nnz);
+  ALLOC(d_beta, nnz);
+  ALLOC(d_betat, nnz);
+  ALLOC(d_mi, n);
+  ALLOC(d_imi, n);
+  ALLOC(d_relax, n);
+  ALLOC(d_isb, n);
+  ALLOC(d_bidx, n);
+  ALLOC(d_bkind, n_bnd);
+  ALLOC(d_bnorm, (size_t)dim * n_bnd);
+  ALLOC(d_bstate, (size_t)S * n_bnd);
+  const int SP = SP_of(c);
+  Work &w = c->wk;
+  w.nblocks_rows = (int)((n + 127) / 128);
+  ALLOC(w.rec, (size_t)n * REC);
+  ALLOC(w.alpha, n);
+  ALLOC(w.w, (size_t)nnz * SP);
+  ALLOC(w.d, nnz);
+  ALLOC(w.inc, (size_t)n * SP);
+  ALLOC(w.FH, (size_t)n * SP);
+  ALLOC(w.bounds, (size_t)n * 4);
+  ALLOC(w.UL, (size_t)n * SP);
+  ALLOC(w.Ua, (size_t)n * SP);
+  ALLOC(w.Ub, (size_t)n * SP);
+  ALLOC(w.P, (size_t)nnz * SP);
+  ALLOC(w.la, nnz);
+  ALLOC(w.lb, nnz);
+  ALLOC(w.blockmin, w.nblocks_rows);
+  ALLOC(c->U, (size_t)S * n);
+  ALLOC(c->W, (size_t)S * n);
+  ALLOC(c->trace_lsym, nnz);
+  ALLOC(c->trace_upass, (size_t)n * SP);
+  ALLOC(c->trace_pre, (size_t)n * SP);
+#undef ALLOC
+  w.st = c->st;
+  auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = up(d_row, row_ptr, sizeof(int64_t) * (n + 1));
+  if (e == cudaSuccess) e = up(d_col, col, sizeof(int32_t) * nnz);
+  if (e == cudaSuccess) e = up(d_tr, tr.data(), sizeof(int32_t) * nnz);
+  if (e == cudaSuccess) e = up(d_cij, cij, sizeof(double) * dim * nnz);
+  if (e == cudaSuccess) e = up(d_cn, cn.data(), sizeof(double) * nnz);
+  if (e == cudaSuccess) e = up(d_cinv, cinv.data(), sizeof(double) * nnz);
+  if (e == cudaSuccess) e = up(d_beta, beta.data(), sizeof(double) * nnz);
+  if (e == cudaSuccess) e = up(d_betat, betat.data(), sizeof(double) * nnz);
+  if (e == cudaSuccess) e = up(d_mi, mi, sizeof(double) * n);
+  if (e == cudaSuccess) e = up(d_imi, inv_mi.data(), sizeof(double) * n);
+  if (e == cudaSuccess) e = up(d_relax, relax.data(), sizeof(double) * n);
+  if (e == cudaSuccess) e = up(d_isb, isb.data(), n);
+  if (e == cudaSuccess) e = up(d_bidx, bidx.data(), sizeof(int32_t) * n);
+  if (e == cudaSuccess) e = up(d_bkind, bnd_kind, sizeof(int32_t) * n_bnd);
+  if (e == cudaSuccess) e = up(d_bnorm, bnd_normal, sizeof(double) * dim * n_bnd);
+  if (e == cudaSuccess && bnd_state) e = up(d_bstate, bnd_state, sizeof(double) * S * n_bnd);
+  if (e != cudaSuccess) {
+    free_mesh(c);
+    return fail(c, EH_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(e));
+  }
+  m.row_ptr = d_row;
+  m.col = d_col;
+  m.tr = d_tr;
+  m.cij = d_cij;
+  m.cn = d_cn;
+  m.cinv = d_cinv;
+  m.beta = d_beta;
+  m.betat = d_betat;
+  m.mi = d_mi;
+  m.inv_mi = d_imi;
+  m.relax = d_relax;
+  m.isb = d_isb;
+  m.bnd_index = d_bidx;
+  m.bnd_kind = d_bkind;
+  m.bnd_normal = d_bnorm;
+  m.bnd_state = d_bstate;
+  c->n = n;
+  c->nnz = nnz;
+  c->n_bnd = n_bnd;
+  c->have_mesh = true;
+  c->t = 0.0;
+  c->steps = 0;
+  return EH_OK;
+}
+
+eh_status eh_set_state(eh_ctx *c, const double *U, int is_device_ptr) {
+  if (!c || !U) return EH_ERR_INVALID_ARG;
+  if (!c->have_mesh) return fail(c, EH_ERR_STATE, "no mesh uploaded");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  const size_t bytes = sizeof(double) * S_of(c) * c->n;
+  CUDA_TRY(c, cudaMemcpyAsync(c->U, U, bytes, is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+  eh_status st = reset_status(c);
+  if (st) return st;
+  if (c->cfg.dim == 2) launch_count_not_admissible<2>(c->n, c->U, c->st, c->stream);
+  else launch_count_not_admissible<3>(c->n, c->U, c->st, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  CUDA_TRY(c, cudaMemcpy(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+  if (c->st_host->not_admissible) {
+    c->have_state = false;
+    return fail(c, EH_ERR_NOT_ADMISSIBLE, "%llu nodes with rho <= 0 or internal energy <= 0",
+                (unsigned long long)c->st_host->not_admissible);
+  }
+  st = reset_status(c);
+  if (st) return st;
+  c->have_state = true;
+  return EH_OK;
+}
+
+eh_status eh_get_state(eh_ctx *c, double *U_out, int is_device_ptr) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  if (!U_out) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  const size_t bytes = sizeof(double) * S_of(c) * c->n;
+  CUDA_TRY(c, cudaMemcpyAsync(U_out, c->U, bytes, is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              c->stream));
+  return check_device_error(c);
+}
+
+eh_status eh_apply_boundary_conditions(eh_ctx *c) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if (c->cfg.dim == 2) launch_apply_bc<2>(c->mv, c->U, c->stream);
+  else launch_apply_bc<3>(c->mv, c->U, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  return EH_OK;
+}
+
+eh_status eh_cfl_dt(eh_ctx *c, double *dt) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  if (!dt) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if ((st = check_device_error(c))) return st;
+  if (c->cfg.dim == 2) {
+    launch_prep<2>(c->mv, c->prm, c->U, c->wk, c->stream);
+    launch_visc<2>(c->mv, c->prm, c->wk, c->stream);
+    launch_low<2>(c->mv, c->prm, c->wk, c->stream);
+  } else {
+    launch_prep<3>(c->mv, c->prm, c->U, c->wk, c->stream);
+    launch_visc<3>(c->mv, c->prm, c->wk, c->stream);
+    launch_low<3>(c->mv, c->prm, c->wk, c->stream);
+  }
+  launch_tau(c->wk, 0, 0.0, c->prm.cfl, c->stream);
+  CUDA_TRY(c, cudaGetLastError());
+  if ((st = check_device_error(c))) return st;
+  *dt = c->st_host->stage_bound[0];
+  return EH_OK;
+}
+
+eh_status eh_stage(eh_ctx *c, double tau, double *tau_used) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if ((st = check_device_error(c))) return st;
+  if (c->cfg.dim == 2) enqueue_stage<2>(c, c->U, 0, tau, nullptr, -1.0, c->U, true);
+  else enqueue_stage<3>(c, c->U, 0, tau, nullptr, -1.0, c->U, true);
+  CUDA_TRY(c, cudaGetLastError());
+  c->last_stage_traced = true;
+  if (tau_used) {
+    if ((st = check_device_error(c))) return st;
+    *tau_used = c->st_host->tau;
+  }
+  return EH_OK;
+}
+
+eh_status eh_step(eh_ctx *c, double dt, double *dt_used) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  enqueue_step_any(c, dt);
+  CUDA_TRY(c, cudaGetLastError());
+  c->steps += 1;
+  c->last_stage_traced = false;
+  if (dt_used) {
+    if ((st = check_device_error(c))) return st;
+    *dt_used = c->st_host->tau;
+    c->last_dt = *dt_used;
+    c->t += *dt_used;
+  }
+  return EH_OK;
+}
+
+eh_status eh_run(eh_ctx *c, int32_t nsteps, double dt) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  if (nsteps < 0) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if (c->profiling) {  // eager launches with event pairs
+    for (int32_t k = 0; k < nsteps; ++k) enqueue_step_any(c, dt);
+    CUDA_TRY(c, cudaGetLastError());
+    c->steps += nsteps;
+    c->last_stage_traced = false;
+    return EH_OK;
+  }
+  if (!c->graph || c->graph_dt != dt) {
+    if (c->graph) {
+      CUDA_TRY(c, cudaGraphExecDestroy(c->graph));
+      c->graph = nullptr;
+    }
+    cudaGraph_t g;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step_any(c, dt);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return fail(c, EH_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, EH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    c->graph_dt = dt;
+  }
+  for (int32_t k = 0; k < nsteps; ++k) CUDA_TRY(c, cudaGraphLaunch(c->graph, c->stream));
+  c->steps += nsteps;
+  c->last_stage_traced = false;
+  return EH_OK;
+}
+
+eh_status eh_synchronize(eh_ctx *c) {
+  if (!c) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  return check_device_error(c);
+}
+
+eh_status eh_get_diagnostics(eh_ctx *c, eh_diagnostics *out) {
+  if (!c || !out) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  eh_status st = check_device_error(c);
+  memset(out, 0, sizeof(*out));
+  out->t = c->t;
+  out->steps = c->steps;
+  out->last_dt = c->st_host->tau;
+  for (int q = 0; q < 3; ++q) out->last_stage_bound[q] = c->st_host->stage_bound[q];
+  out->cfl_violations = (int64_t)c->st_host->cfl_violations;
+  out->not_admissible = (int64_t)c->st_host->not_admissible;
+  return st;
+}
+
+eh_status eh_profile_enable(eh_ctx *c, int enable) {
+  if (!c) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  flush_profile(c);
+  c->profiling = enable != 0;
+  for (int k = 0; k < EH_KERNEL_COUNT; ++k) {
+    c->prof_ms[k] = 0.0;
+    c->prof_count[k] = 0;
+  }
+  return EH_OK;
+}
+
+eh_status eh_profile_read(eh_ctx *c, int kernel, double *total_ms, int64_t *launches) {
+  if (!c || kernel < 0 || kernel >= EH_KERNEL_COUNT || !total_ms || !launches) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  flush_profile(c);
+  *total_ms = c->prof_ms[kernel];
+  *launches = c->prof_count[kernel];
+  return EH_OK;
+}
+
+int32_t eh_launches_per_step(const eh_ctx *c) {
+  if (!c) return 0;
+  // prep, visc, low, tau, lim1, (passes - 1) x pass, final; three stages
+  return 3 * (6 + (c->cfg.limiter_passes - 1));
+}
+
+eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  if (!host_out) return EH_ERR_INVALID_ARG;
+  if (!c->last_stage_traced) return fail(c, EH_ERR_STATE, "eh_trace needs a preceding eh_stage");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if ((st = check_device_error(c))) return st;
+  const int S = S_of(c), SP = SP_of(c);
+  const int64_t n = c->n, nnz = c->nnz;
+  auto aos_to_soa = [&](const double *dev, int stride, int comps) -> eh_status {
+    if (count != comps * n) return fail(c, EH_ERR_INVALID_ARG, "count must be %lld", (long long)(comps * n));
+    std::vector<double> tmp((size_t)n * stride);
+    CUDA_TRY(c, cudaMemcpy(tmp.data(), dev, sizeof(double) * n * stride, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i)
+      for (int s = 0; s < comps; ++s) host_out[s * n + i] = tmp[i * stride + s];
+    return EH_OK;
+  };
+  auto plain = [&](const double *dev, int64_t len) -> eh_status {
+    if (count != len) return fail(c, EH_ERR_INVALID_ARG, "count must be %lld", (long long)len);
+    CUDA_TRY(c, cudaMemcpy(host_out, dev, sizeof(double) * len, cudaMemcpyDeviceToHost));
+    return EH_OK;
+  };
+  switch (what) {
+    case EH_TRACE_D_IJ: return plain(c->wk.d, nnz);
+    case EH_TRACE_ALPHA: return plain(c->wk.alpha, n);
+    case EH_TRACE_U_LOW: return aos_to_soa(c->wk.UL, SP, S);
+    case EH_TRACE_F_HIGH: return aos_to_soa(c->wk.FH, SP, S);
+    case EH_TRACE_BOUNDS: return aos_to_soa(c->wk.bounds, 4, 3);
+    case EH_TRACE_L_PASS1:
+      if (c->cfg.limiter_passes < 2) return fail(c, EH_ERR_STATE, "L_PASS1 needs limiter_passes >= 2");
+      return plain(c->trace_lsym, nnz);
+    case EH_TRACE_U_PASS1:
+      return aos_to_soa(c->cfg.limiter_passes >= 2 ? c->trace_upass : c->trace_pre, SP, S);
+    case EH_TRACE_TAU:
+      if (count != 1) return EH_ERR_INVALID_ARG;
+      host_out[0] = c->st_host->tau;
+      return EH_OK;
+    case EH_TRACE_TAU_BOUND:
+      if (count != 1) return EH_ERR_INVALID_ARG;
+      host_out[0] = c->st_host->stage_bound[0];
+      return EH_OK;
+    default: return fail(c, EH_ERR_INVALID_ARG, "unknown trace selector %d", what);
+  }
+}
+
+}  // extern "C"

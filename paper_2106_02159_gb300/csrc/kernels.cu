@@ -1,0 +1,693 @@
+// kernels.cu -- sm_103a kernels of one forward-Euler stage of the hyperbolic
+// (Euler) operator of arXiv:2106.02159 (Appendix B, Algorithm 1) and of the
+// boundary post-processing of Sec. 4.
+//
+// Design: on GB300 an FP64 FMA issues at 1/72 of the FP32 rate, so this path
+// is bound by FP64 instruction issue, not by HBM. Every edge loop therefore
+// runs one thread per CSR row (no idle lanes in 7/9/27-entry rows), sums in
+// the row's column order (bitwise reproducible), and trades bytes for FP64
+// work: per-node quantities (primitives, a p^-z, Phi, eta) are computed once
+// per stage in k_prep and gathered; |c_ij|, 1/|c_ij|, m_ij/m_j and m_ji/m_i are
+// static per-edge arrays; (f(U_j) - f(U_i)) c_ij is computed once per edge in
+// k_visc and reused by k_low; the limiter directions P_ij are stored.
+#include "kernels.cuh"
+
+#include <cmath>
+
+namespace eh {
+
+constexpr int TPB = 128;  // threads per block of the row kernels
+
+__host__ __device__ inline unsigned nblocks(int64_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
+
+// ---------------------------------------------------------------------------
+// roots and powers for gamma = 7/5 (division-free Newton iterations from an
+// FP32 seed; two steps take the ~2^-21 seed error below double rounding)
+// ---------------------------------------------------------------------------
+
+// x^(-1/5): Newton's method on r^-5 = x, r <- r (6 - x r^5) / 5.
+__device__ __forceinline__ double rroot5(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return pow(x, -0.2);
+  double r = (double)exp2f(-0.2f * log2f((float)x));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    double r2 = r * r;
+    double r5 = r2 * r2 * r;
+    r = r * (6.0 - x * r5) * 0.2;
+  }
+  return r;
+}
+
+// x^(-1/7): Newton's method on r^-7 = x, r <- r (8 - x r^7) / 7.
+__device__ __forceinline__ double rroot7(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return pow(x, -1.0 / 7.0);
+  double r = (double)exp2f((-1.0f / 7.0f) * log2f((float)x));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    double r2 = r * r;
+    double r7 = r2 * r2 * r2 * r;
+    r = r * (8.0 - x * r7) * (1.0 / 7.0);
+  }
+  return r;
+}
+
+// rho^gamma
+__device__ __forceinline__ double pow_gamma(const Params &p, double rho) {
+  if (p.gamma75) {
+    double r = rroot5(rho);  // rho^(-1/5); rho^(7/5) = rho^2 r^3
+    return rho * rho * (r * r * r);
+  }
+  return pow(rho, p.gamma);
+}
+
+// rho^(gamma - 1)
+__device__ __forceinline__ double pow_gamma_m1(const Params &p, double rho) {
+  if (p.gamma75) {
+    double r = rroot5(rho);  // rho^(2/5) = rho r^3
+    return rho * (r * r * r);
+  }
+  return pow(rho, p.gamma - 1.0);
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3.1: guaranteed upper bound on the maximum wave speed
+// ---------------------------------------------------------------------------
+// Two-rarefaction pressure p_tr >= p* (1 < gamma <= 5/3), then the outer wave
+// speeds of the 1- and 3-waves evaluated at p_tr. Inputs per side: normal
+// velocity, p, a, a p^-z, 1/p.
+__device__ __forceinline__ double lambda_max(const Params &p, double unl, double pl, double al, double azl, double ipl,
+                                             double unr, double pr, double ar, double azr, double ipr) {
+  double num = al + ar - 0.5 * p.gm1 * (unr - unl);
+  num = fmax(num, 0.0);
+  double x = num / (azl + azr);
+  double ptr;
+  if (p.gamma75) {
+    double x2 = x * x;
+    double x4 = x2 * x2;
+    ptr = x4 * x2 * x;  // x^(2 gamma/(gamma-1)) = x^7
+  } else {
+    ptr = pow(x, p.inv_z);
+  }
+  double sl = ptr > pl ? sqrt(1.0 + p.kshock * (ptr - pl) * ipl) : 1.0;
+  double sr = ptr > pr ? sqrt(1.0 + p.kshock * (ptr - pr) * ipr) : 1.0;
+  double lam1 = unl - al * sl;
+  double lam3 = unr + ar * sr;
+  return fmax(fmax(-lam1, 0.0), fmax(lam3, 0.0));
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3.3: line search for the largest l in [0,1] within the local bounds
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ double psi(const Params &p, const double *ub, const double *P, double l, double phimin) {
+  constexpr int S = DIM + 2;
+  double u[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) u[s] = ub[s] + l * P[s];
+  double m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) m2 += u[1 + k] * u[1 + k];
+  double eps = u[S - 1] - m2 / (2.0 * u[0]);
+  return eps - phimin * pow_gamma(p, u[0]);
+}
+
+template <int DIM>
+__device__ __forceinline__ double dpsi(const Params &p, const double *ub, const double *P, double l, double phimin) {
+  constexpr int S = DIM + 2;
+  double u[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) u[s] = ub[s] + l * P[s];
+  double irho = 1.0 / u[0];
+  double v2 = 0.0, vP = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    double v = u[1 + k] * irho;
+    v2 += v * v;
+    vP += v * P[1 + k];
+  }
+  double deps = P[S - 1] - vP + 0.5 * v2 * P[0];
+  return deps - phimin * p.gamma * pow_gamma_m1(p, u[0]) * P[0];
+}
+
+constexpr int LINE_SEARCH_ITERATIONS = 6;
+
+template <int DIM>
+__device__ double line_search(const Params &p, const double *ub, const double *P, double rmin, double rmax,
+                              double phimin) {
+  double l = 1.0;
+  double rb = ub[0], rp = P[0];
+  if (rp > 0.0) {
+    l = fmin(l, (rmax - rb) / rp);
+  } else if (rp < 0.0) {
+    l = fmin(l, (rmin - rb) / rp);
+  }
+  l = fmax(0.0, fmin(1.0, l));
+  double pr = psi<DIM>(p, ub, P, l, phimin);
+  if (pr >= 0.0) return l;
+  double pl = psi<DIM>(p, ub, P, 0.0, phimin);
+  if (pl <= 0.0) return 0.0;
+  double lL = 0.0, lR = l;
+  for (int it = 0; it < LINE_SEARCH_ITERATIONS; ++it) {
+    double ls = lL + pl * (lR - lL) / (pl - pr);
+    double dr = dpsi<DIM>(p, ub, P, lR, phimin);
+    double ln = dr < 0.0 ? lR - pr / dr : lR;
+    if (ln < ls) ln = ls;
+    double ps = psi<DIM>(p, ub, P, ls, phimin);
+    double pn = psi<DIM>(p, ub, P, ln, phimin);
+    if (ps >= 0.0) {
+      lL = ls;
+      pl = ps;
+    }
+    if (pn < 0.0) {
+      lR = ln;
+      pr = pn;
+    } else {
+      lL = ln;
+      pl = pn;
+    }
+  }
+  return lL;
+}
+
+// ---------------------------------------------------------------------------
+// flux f(U) (Sec. 2.1) from the state and the node record's v and p
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void flux(const double *u, const double *v, double pr, double f[DIM + 2][DIM]) {
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) f[0][k] = u[1 + k];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) f[1 + a][b] = v[b] * u[1 + a] + (a == b ? pr : 0.0);
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) f[DIM + 1][k] = v[k] * (u[DIM + 1] + pr);
+}
+
+// ---------------------------------------------------------------------------
+// k_prep: node records (primitives and derived quantities), once per stage
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(TPB) k_prep(MeshView m, Params p, const double *__restrict__ U,
+                                              double *__restrict__ rec, const DevStatus *st) {
+  constexpr int S = DIM + 2;
+  using R = Rec<DIM>;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.n || st->err) return;
+  double u[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) u[s] = U[(int64_t)s * m.n + i];
+  double rho = u[0];
+  double irho = 1.0 / rho;
+  double v[DIM], m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    v[k] = u[1 + k] * irho;
+    m2 += u[1 + k] * u[1 + k];
+  }
+  double eps = u[S - 1] - m2 / (2.0 * rho);
+  double pr = p.gm1 * eps;
+  double a = sqrt(p.gamma * pr * irho);
+  double az, phi;
+  if (p.gamma75) {
+    az = a * rroot7(pr);
+    double r = rroot5(rho);  // rho^(-1/5); rho^(-7/5) = r^7
+    double r2 = r * r;
+    phi = eps * (r2 * r2 * r2 * r);
+  } else {
+    az = a * pow(pr, -p.z);
+    phi = eps * pow(rho, -p.gamma);
+  }
+  double eta = -rho * (log(phi) / p.gm1);
+  double *Rr = rec + (int64_t)i * REC;
+#pragma unroll
+  for (int s = 0; s < S; ++s) Rr[s] = u[s];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) Rr[R::V + k] = v[k];
+  Rr[R::P] = pr;
+  Rr[R::A] = a;
+  Rr[R::AZ] = az;
+  Rr[R::IP] = 1.0 / pr;
+  Rr[R::PHI] = phi;
+  Rr[R::ETA] = eta;
+  Rr[R::ETA + 1] = eps;
+}
+
+// ---------------------------------------------------------------------------
+// k_visc: Algorithm 1 step 1 -- d_ij (j > i, mirrored through the transpose
+// index), the flux differences w_ij and the indicator alpha_i
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(TPB) k_visc(MeshView m, Params p, Work w) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  using R = Rec<DIM>;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.n || w.st->err) return;
+  const double *Ri = w.rec + (int64_t)i * REC;
+  double ui[S], vi[DIM];
+#pragma unroll
+  for (int s = 0; s < S; ++s) ui[s] = Ri[s];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) vi[k] = Ri[R::V + k];
+  const double pi = Ri[R::P], ai = Ri[R::A], azi = Ri[R::AZ], ipi = Ri[R::IP], etai = Ri[R::ETA];
+  const double epsi = Ri[R::ETA + 1];
+  double fi[S][DIM];
+  flux<DIM>(ui, vi, pi, fi);
+  // eta'(U_i) (Sec. 3.2 indicator)
+  double deta[S];
+  {
+    double s_i = -etai / ui[0];
+    double g1 = ui[0] / (p.gm1 * epsi);
+    double v2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) v2 += vi[k] * vi[k];
+    deta[0] = -s_i - ui[0] / p.gm1 * (v2 / (2.0 * epsi) - p.gamma / ui[0]);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) deta[1 + k] = g1 * vi[k];
+    deta[S - 1] = -g1;
+  }
+  double qi[DIM];
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) qi[k] = vi[k] * etai;
+  const bool bi = m.isb[i] != 0;
+  double N = 0.0, D = 0.0;
+  const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
+  for (int64_t k = k0; k < k1; ++k) {
+    const int j = m.col[k];
+    if (j == i) continue;
+    const double *Rj = w.rec + (int64_t)j * REC;
+    double uj[S], vj[DIM], c[DIM];
+#pragma unroll
+    for (int s = 0; s < S; ++s) uj[s] = Rj[s];
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) {
+      vj[q] = Rj[R::V + q];
+      c[q] = m.cij[(int64_t)q * m.nnz + k];
+    }
+    const double pj = Rj[R::P], etaj = Rj[R::ETA];
+    double fj[S][DIM];
+    flux<DIM>(uj, vj, pj, fj);
+    double wv[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      double acc = 0.0;
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) acc += (fj[s][q] - fi[s][q]) * c[q];
+      wv[s] = acc;
+    }
+    double *wk = w.w + k * SP;
+#pragma unroll
+    for (int s = 0; s < S; ++s) wk[s] = wv[s];
+    double a_ = 0.0, b_ = 0.0;
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) a_ += (vj[q] * etaj - qi[q]) * c[q];
+#pragma unroll
+    for (int s = 0; s < S; ++s) b_ += deta[s] * wv[s];
+    N += a_ - b_;
+    D += fabs(a_) + fabs(b_);
+    if (j > i) {
+      const double ci = m.cinv[k];
+      double unl = 0.0, unr = 0.0;
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) {
+        unl += vi[q] * (c[q] * ci);
+        unr += vj[q] * (c[q] * ci);
+      }
+      double dij = lambda_max(p, unl, pi, ai, azi, ipi, unr, pj, Rj[R::A], Rj[R::AZ], Rj[R::IP]) * m.cn[k];
+      const int32_t kt = m.tr[k];
+      if (bi && m.isb[j]) {
+        const double cit = m.cinv[kt];
+        double unj = 0.0, uni = 0.0;
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) {
+          double nq = m.cij[(int64_t)q * m.nnz + kt] * cit;
+          unj += vj[q] * nq;
+          uni += vi[q] * nq;
+        }
+        double dji = lambda_max(p, unj, pj, Rj[R::A], Rj[R::AZ], Rj[R::IP], uni, pi, ai, azi, ipi) * m.cn[kt];
+        dij = fmax(dij, dji);
+      }
+      w.d[k] = dij;
+      w.d[kt] = dij;
+    }
+  }
+  w.alpha[i] = D > 0.0 ? fabs(N) / D : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// k_low: Algorithm 1 steps 2-3 -- d_ii, CFL bound, low-order increment, local
+// bounds and high-order fluxes
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  using R = Rec<DIM>;
+  __shared__ double smin[TPB / 32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i < m.n && !w.st->err;
+  double bound = INFINITY;
+  if (active) {
+    const double *Ri = w.rec + (int64_t)i * REC;
+    double ui[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) ui[s] = Ri[s];
+    const double alphai = w.alpha[i];
+    double inc[S], fh[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) inc[s] = fh[s] = 0.0;
+    double rmin = ui[0], rmax = ui[0], phimin = Ri[R::PHI], dsum = 0.0;
+    int64_t kd = -1;
+    const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
+    for (int64_t k = k0; k < k1; ++k) {
+      const int j = m.col[k];
+      if (j == i) {
+        kd = k;
+        continue;
+      }
+      const double *Rj = w.rec + (int64_t)j * REC;
+      const double dk = w.d[k];
+      const double *wk = w.w + k * SP;
+      const double dH = 0.5 * (alphai + w.alpha[j]) * dk;
+      double w0 = 0.0;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const double ws = wk[s];
+        if (s == 0) w0 = ws;
+        const double du = Rj[s] - ui[s];
+        inc[s] += dk * du - ws;
+        fh[s] += -ws + dH * du;
+      }
+      const double rbar = dk > 0.0 ? 0.5 * (ui[0] + Rj[0]) - w0 / (2.0 * dk) : ui[0];
+      rmin = fmin(rmin, rbar);
+      rmax = fmax(rmax, rbar);
+      phimin = fmin(phimin, Rj[R::PHI]);
+      dsum += dk;
+    }
+    w.d[kd] = -dsum;
+    bound = p.cfl * m.mi[i] / (2.0 * dsum);
+    double *inci = w.inc + (int64_t)i * SP;
+    double *fhi = w.FH + (int64_t)i * SP;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      inci[s] = inc[s];
+      fhi[s] = fh[s];
+    }
+    const double r = m.relax[i];
+    double *bi = w.bounds + (int64_t)i * 4;
+    bi[0] = (1.0 - r) * rmin;
+    bi[1] = (1.0 + r) * rmax;
+    bi[2] = (1.0 - r) * phimin;
+  }
+  // block minimum of the CFL bound (exact, order independent)
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) bound = fmin(bound, __shfl_xor_sync(0xffffffffu, bound, off));
+  if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = bound;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = smin[0];
+#pragma unroll
+    for (int q = 1; q < TPB / 32; ++q) b = fmin(b, smin[q]);
+    w.blockmin[blockIdx.x] = b;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_tau: global minimum of the CFL bound; fixes tau at the first stage
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_tau(const double *__restrict__ blockmin, int nb, DevStatus *st, int stage,
+                                              double dt_given, double cfl) {
+  __shared__ double sm[32];
+  if (st->err) return;
+  double b = INFINITY;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) b = fmin(b, blockmin[q]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) b = fmin(b, __shfl_xor_sync(0xffffffffu, b, off));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bound = sm[0];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) bound = fmin(bound, sm[q]);
+    st->stage_bound[stage] = bound;
+    const double limit = bound / cfl;  // invariant-domain limit, c_cfl = 1
+    if (stage == 0) {
+      if (dt_given > 0.0) {
+        if (dt_given > limit) {
+          st->err = 5;  // EH_ERR_CFL
+          return;
+        }
+        st->tau = dt_given;
+      } else {
+        st->tau = bound;
+      }
+    } else if (st->tau > limit) {
+      st->cfl_violations += 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_lim1: Algorithm 1 step 4 -- U^L, P_ij and the first line search
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(TPB) k_lim1(MeshView m, Params p, Work w) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.n || w.st->err) return;
+  const double tau = w.st->tau;
+  const double *Ri = w.rec + (int64_t)i * REC;
+  double ui[S], ul[S], fhi[S];
+  const double *inci = w.inc + (int64_t)i * SP;
+  const double *FHi = w.FH + (int64_t)i * SP;
+  const double tm = tau * m.inv_mi[i];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    ui[s] = Ri[s];
+    ul[s] = ui[s] + tm * inci[s];
+    fhi[s] = FHi[s];
+  }
+  double *ULi = w.UL + (int64_t)i * SP;
+#pragma unroll
+  for (int s = 0; s < S; ++s) ULi[s] = ul[s];
+  const double *bi = w.bounds + (int64_t)i * 4;
+  const double rmin = bi[0], rmax = bi[1], phimin = bi[2];
+  const double alphai = w.alpha[i];
+  const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
+  const double coef = tau * (double)(k1 - k0 - 1) * m.inv_mi[i];
+  for (int64_t k = k0; k < k1; ++k) {
+    const int j = m.col[k];
+    double *Pk = w.P + k * SP;
+    if (j == i) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) Pk[s] = 0.0;
+      w.la[k] = 1.0;
+      continue;
+    }
+    const double *Rj = w.rec + (int64_t)j * REC;
+    const double *FHj = w.FH + (int64_t)j * SP;
+    const double dk = w.d[k];
+    const double dH = 0.5 * (alphai + w.alpha[j]) * dk;
+    const double b = m.beta[k], bt = m.betat[k];
+    double P[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      P[s] = coef * (-b * FHj[s] + bt * fhi[s] + (dH - dk) * (Rj[s] - ui[s]));
+      Pk[s] = P[s];
+    }
+    w.la[k] = line_search<DIM>(p, ul, P, rmin, rmax, phimin);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_pass: symmetrise the limiter, update, shrink P and search again
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(TPB) k_pass(MeshView m, Params p, Work w, const double *__restrict__ Uin,
+                                              double *__restrict__ Uout, const double *__restrict__ lin,
+                                              double *__restrict__ lout, double *lsym_trace) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.n || w.st->err) return;
+  const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
+  const double lambda_i = 1.0 / (double)(k1 - k0 - 1);
+  double u[S];
+  const double *Ui = Uin + (int64_t)i * SP;
+#pragma unroll
+  for (int s = 0; s < S; ++s) u[s] = Ui[s];
+  for (int64_t k = k0; k < k1; ++k) {
+    if (m.col[k] == i) {
+      if (lsym_trace) lsym_trace[k] = 1.0;
+      continue;
+    }
+    const double l = fmin(lin[k], lin[m.tr[k]]);
+    if (lsym_trace) lsym_trace[k] = l;
+    const double *Pk = w.P + k * SP;
+#pragma unroll
+    for (int s = 0; s < S; ++s) u[s] += lambda_i * l * Pk[s];
+  }
+  double *Uo = Uout + (int64_t)i * SP;
+#pragma unroll
+  for (int s = 0; s < S; ++s) Uo[s] = u[s];
+  const double *bi = w.bounds + (int64_t)i * 4;
+  const double rmin = bi[0], rmax = bi[1], phimin = bi[2];
+  for (int64_t k = k0; k < k1; ++k) {
+    if (m.col[k] == i) {
+      lout[k] = 1.0;
+      continue;
+    }
+    const double l = fmin(lin[k], lin[m.tr[k]]);
+    double *Pk = w.P + k * SP;
+    double P[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      P[s] = (1.0 - l) * Pk[s];
+      Pk[s] = P[s];
+    }
+    lout[k] = line_search<DIM>(p, u, P, rmin, rmax, phimin);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_final: last limited update, boundary post-processing (Sec. 4), SSP
+// combination (Sec. 4.1) and admissibility check
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void apply_bc_node(const MeshView &m, int i, double *u) {
+  const int b = m.bnd_index[i];
+  if (b < 0) return;
+  const int kind = m.bnd_kind[b];
+  if (kind == 1) {  // slip: M <- M - (M . n^s) n^s
+    double mn = 0.0;
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) mn += u[1 + q] * m.bnd_normal[(int64_t)q * m.n_bnd + b];
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) u[1 + q] -= mn * m.bnd_normal[(int64_t)q * m.n_bnd + b];
+  } else if (kind == 2) {  // supersonic inflow: U <- U^D
+#pragma unroll
+    for (int s = 0; s < DIM + 2; ++s) u[s] = m.bnd_state[(int64_t)s * m.n_bnd + b];
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ bool admissible(const double *u) {
+  double m2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) m2 += u[1 + q] * u[1 + q];
+  return u[0] > 0.0 && (u[DIM + 1] - m2 / (2.0 * u[0])) > 0.0;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(TPB) k_final(MeshView m, Params p, Work w, const double *__restrict__ Uin,
+                                               const double *__restrict__ lin, const double *U0, double coef,
+                                               double *out, double *Upre_trace) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.n || w.st->err) return;
+  const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
+  const double lambda_i = 1.0 / (double)(k1 - k0 - 1);
+  double u[S];
+  const double *Ui = Uin + (int64_t)i * SP;
+#pragma unroll
+  for (int s = 0; s < S; ++s) u[s] = Ui[s];
+  for (int64_t k = k0; k < k1; ++k) {
+    if (m.col[k] == i) continue;
+    const double l = fmin(lin[k], lin[m.tr[k]]);
+    const double *Pk = w.P + k * SP;
+#pragma unroll
+    for (int s = 0; s < S; ++s) u[s] += lambda_i * l * Pk[s];
+  }
+  if (Upre_trace) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) Upre_trace[(int64_t)i * SP + s] = u[s];
+  }
+  apply_bc_node<DIM>(m, i, u);
+  if (coef >= 0.0) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const double u0 = U0[(int64_t)s * m.n + i];
+      u[s] = u0 + coef * (u[s] - u0);
+    }
+  }
+  if (!admissible<DIM>(u)) {
+    atomicAdd(&w.st->not_admissible, 1ull);
+    atomicExch(&w.st->err, 4);  // EH_ERR_NOT_ADMISSIBLE
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) out[(int64_t)s * m.n + i] = u[s];
+}
+
+template <int DIM> __global__ void k_apply_bc(MeshView m, double *U) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.n || m.bnd_index[i] < 0) return;
+  double u[DIM + 2];
+#pragma unroll
+  for (int s = 0; s < DIM + 2; ++s) u[s] = U[(int64_t)s * m.n + i];
+  apply_bc_node<DIM>(m, i, u);
+#pragma unroll
+  for (int s = 0; s < DIM + 2; ++s) U[(int64_t)s * m.n + i] = u[s];
+}
+
+template <int DIM> __global__ void k_count_not_admissible(int n, const double *U, DevStatus *st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double u[DIM + 2];
+#pragma unroll
+  for (int s = 0; s < DIM + 2; ++s) u[s] = U[(int64_t)s * n + i];
+  if (!admissible<DIM>(u)) atomicAdd(&st->not_admissible, 1ull);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int DIM> void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, cudaStream_t s) {
+  k_prep<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, U, w.rec, w.st);
+}
+template <int DIM> void launch_visc(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
+  k_visc<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
+}
+template <int DIM> void launch_low(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
+  k_low<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
+}
+void launch_tau(const Work &w, int stage, double dt_given, double cfl, cudaStream_t s) {
+  k_tau<<<1, 1024, 0, s>>>(w.blockmin, w.nblocks_rows, w.st, stage, dt_given, cfl);
+}
+template <int DIM> void launch_lim1(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
+  k_lim1<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
+}
+template <int DIM>
+void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
+                 double *lout, double *lsym_trace, cudaStream_t s) {
+  k_pass<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w, Uin, Uout, lin, lout, lsym_trace);
+}
+template <int DIM>
+void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,
+                  const double *U0, double coef, double *out, double *Upre_trace, cudaStream_t s) {
+  k_final<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w, Uin, lin, U0, coef, out, Upre_trace);
+}
+template <int DIM> void launch_apply_bc(const MeshView &m, double *U, cudaStream_t s) {
+  k_apply_bc<DIM><<<nblocks(m.n, 256), 256, 0, s>>>(m, U);
+}
+template <int DIM> void launch_count_not_admissible(int n, const double *U, DevStatus *st, cudaStream_t s) {
+  k_count_not_admissible<DIM><<<nblocks(n, 256), 256, 0, s>>>(n, U, st);
+}
+
+#define EH_INSTANTIATE(DIM)                                                                                          \
+  template void launch_prep<DIM>(const MeshView &, const Params &, const double *, const Work &, cudaStream_t);       \
+  template void launch_visc<DIM>(const MeshView &, const Params &, const Work &, cudaStream_t);                       \
+  template void launch_low<DIM>(const MeshView &, const Params &, const Work &, cudaStream_t);                        \
+  template void launch_lim1<DIM>(const MeshView &, const Params &, const Work &, cudaStream_t);                       \
+  template void launch_pass<DIM>(const MeshView &, const Params &, const Work &, const double *, double *,            \
+                                 const double *, double *, double *, cudaStream_t);                                   \
+  template void launch_final<DIM>(const MeshView &, const Params &, const Work &, const double *, const double *,     \
+                                  const double *, double, double *, double *, cudaStream_t);                          \
+  template void launch_apply_bc<DIM>(const MeshView &, double *, cudaStream_t);                                       \
+  template void launch_count_not_admissible<DIM>(int, const double *, DevStatus *, cudaStream_t);
+
+EH_INSTANTIATE(2)
+EH_INSTANTIATE(3)
+
+}  // namespace eh

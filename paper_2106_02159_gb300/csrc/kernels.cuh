@@ -1,0 +1,111 @@
+// kernels.cuh -- device data views and kernel launchers of the forward-Euler
+// stage (Algorithm 1 of arXiv:2106.02159, Appendix B) for sm_103a.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace eh {
+
+// Padded state stride: 4 doubles in 2D (rho, m1, m2, E), 6 in 3D (5 used),
+// so that every per-node / per-edge state vector starts on 16 bytes.
+template <int DIM> struct Layout {
+  static constexpr int S = DIM + 2;
+  static constexpr int SP = DIM == 2 ? 4 : 6;
+};
+
+// Node record written once per stage by k_prep and gathered by the edge loops:
+// [0..S) state, then the primitive and derived quantities below.
+constexpr int REC = 16;
+template <int DIM> struct Rec {
+  static constexpr int V = DIM + 2;       // v_1..v_dim
+  static constexpr int P = 2 * DIM + 2;   // pressure p
+  static constexpr int A = 2 * DIM + 3;   // sound speed a
+  static constexpr int AZ = 2 * DIM + 4;  // a p^{-z}, z = (gamma-1)/(2 gamma)
+  static constexpr int IP = 2 * DIM + 5;  // 1/p
+  static constexpr int PHI = 2 * DIM + 6; // Phi = eps rho^-gamma
+  static constexpr int ETA = 2 * DIM + 7; // eta = -rho s
+};
+
+struct DevStatus {
+  int err;                       // eh_status of a device-detected failure, 0 if none
+  int pad;
+  double tau;                    // the step's tau (fixed at the first stage)
+  double stage_bound[3];         // c_cfl min_i m_i/(2|d_ii|) of the three stages
+  unsigned long long cfl_violations;
+  unsigned long long not_admissible;
+};
+
+struct MeshView {
+  int n;
+  int64_t nnz;
+  const int64_t *row_ptr;
+  const int32_t *col;
+  const int32_t *tr;         // transpose position of every entry
+  const double *cij;         // [dim][nnz]
+  const double *cn;          // |c_ij|
+  const double *cinv;        // 1/|c_ij|
+  const double *beta;        // m_ij / m_j
+  const double *betat;       // m_ji / m_i
+  const double *mi;
+  const double *inv_mi;
+  const double *relax;       // r_i (0 when the bounds are strict)
+  const unsigned char *isb;  // 1 for boundary nodes
+  const int32_t *bnd_index;  // per node: index into the boundary arrays, -1 inside
+  const int32_t *bnd_kind;   // [n_bnd]
+  const double *bnd_normal;  // [dim][n_bnd]
+  const double *bnd_state;   // [S][n_bnd]
+  int n_bnd;
+};
+
+struct Params {
+  double gamma, cfl;
+  int gamma75;               // gamma == 7/5 exactly: root/power fast paths
+  double gm1;                // gamma - 1
+  double z;                  // (gamma-1)/(2 gamma)
+  double inv_z;              // 2 gamma/(gamma-1)
+  double kshock;             // (gamma+1)/(2 gamma)
+};
+
+struct Work {
+  double *rec;     // [n][REC]
+  double *alpha;   // [n]
+  double *w;       // [nnz][SP]  (f(U_j) - f(U_i)) c_ij
+  double *d;       // [nnz]      d^L_ij (diagonal: d_ii)
+  double *inc;     // [n][SP]    sum_{j != i} d_ij (U_j - U_i) - w_ij
+  double *FH;      // [n][SP]
+  double *bounds;  // [n][4]     rho_min, rho_max, Phi_min
+  double *UL;      // [n][SP]
+  double *Ua;      // [n][SP]    limited state, ping
+  double *Ub;      // [n][SP]    limited state, pong
+  double *P;       // [nnz][SP]
+  double *la;      // [nnz]      limiter, ping
+  double *lb;      // [nnz]      limiter, pong
+  double *blockmin;
+  int nblocks_rows;
+  DevStatus *st;
+};
+
+struct TraceOut {
+  double *lsym1;   // [nnz] or null
+  double *Upass1;  // [n][SP] or null (written by the last limiting pass when passes == 1)
+};
+
+// Launchers (all asynchronous on 'stream').
+template <int DIM> void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, cudaStream_t s);
+template <int DIM> void launch_visc(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
+template <int DIM> void launch_low(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
+void launch_tau(const Work &w, int stage, double dt_given, double cfl, cudaStream_t s);
+template <int DIM> void launch_lim1(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
+template <int DIM>
+void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
+                 double *lout, double *lsym_trace, cudaStream_t s);
+// out = SSP combination of U0 and BC(Uin + sum lambda l P): coef < 0 -> out = BC(...),
+// else out = U0 + coef (BC(...) - U0). U0 / out are component-major [S][n].
+template <int DIM>
+void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,
+                  const double *U0, double coef, double *out, double *Upre_trace, cudaStream_t s);
+template <int DIM> void launch_apply_bc(const MeshView &m, double *U, cudaStream_t s);
+template <int DIM> void launch_count_not_admissible(int n, const double *U, DevStatus *st, cudaStream_t s);
+
+}  // namespace eh

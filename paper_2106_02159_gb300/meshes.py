@@ -182,11 +182,10 @@ def _local_q1_3d(xyz):
 def _assemble(n, dim, cells, local_fn, xyz, chunk=1 << 20):
     """Scatter local matrices into a CSR pattern with sorted columns."""
     nv = cells.shape[1]
-    ii = np.repeat(cells, nv, axis=1).astype(np.int64)  # [nc, nv*nv] row a repeated
-    jj = np.tile(cells, (1, nv)).astype(np.int64)
-    keys = (ii * n + jj).ravel()
-    ukeys = np.unique(keys)
-    del ii, jj
+    cc = cells.astype(np.int64)
+    keys = (cc[:, :, None] * n + cc[:, None, :]).ravel()  # entry (a, b) of every cell, row-major
+    ukeys, inverse = np.unique(keys, return_inverse=True)
+    del keys
     rows = (ukeys // n).astype(np.int64)
     col = (ukeys % n).astype(np.int32)
     row_ptr = np.zeros(n + 1, dtype=np.int64)
@@ -200,8 +199,7 @@ def _assemble(n, dim, cells, local_fn, xyz, chunk=1 << 20):
         c1 = min(nc, c0 + chunk)
         c_loc, m_loc, ml = local_fn(xyz[c0:c1])
         cc = cells[c0:c1].astype(np.int64)
-        k = (cc[:, :, None] * n + cc[:, None, :]).ravel()
-        pos = np.searchsorted(ukeys, k)
+        pos = inverse[c0 * nv * nv:c1 * nv * nv]
         for d in range(dim):
             cij[d] += np.bincount(pos, weights=c_loc[..., d].ravel(), minlength=nnz)
         mij += np.bincount(pos, weights=m_loc.ravel(), minlength=nnz)
@@ -484,3 +482,52 @@ def cylinder_m_for_vertices(target: int) -> int:
         else:
             hi = mid
     return lo
+
+
+def structured_q1_3d(nx: int, ny: int, nz: int, box=((0.0, 1.0), (0.0, 1.0), (0.0, 1.0)),
+                     periodic=(False, False, False), kinds=(BC_SLIP,) * 6, name=None) -> Mesh:
+    """Cartesian Q1 hex mesh (27-point stencil) of a box; ``kinds`` gives the
+    boundary kind of the faces x-, x+, y-, y+, z-, z+ (ignored if periodic)."""
+    ncell = (nx, ny, nz)
+    h = [(box[d][1] - box[d][0]) / ncell[d] for d in range(3)]
+    nv = [ncell[d] if periodic[d] else ncell[d] + 1 for d in range(3)]
+
+    def vid(i, j, k):
+        return ((i % nv[0]) * nv[1] + (j % nv[1])) * nv[2] + (k % nv[2])
+
+    I, J, K = np.meshgrid(*[np.arange(v) for v in nv], indexing="ij")
+    coords = np.zeros((nv[0] * nv[1] * nv[2], 3))
+    coords[vid(I.ravel(), J.ravel(), K.ravel())] = np.stack(
+        [box[0][0] + I.ravel() * h[0], box[1][0] + J.ravel() * h[1], box[2][0] + K.ravel() * h[2]], -1)
+    ci, cj, ck = [a.ravel() for a in np.meshgrid(*[np.arange(c) for c in ncell], indexing="ij")]
+    corner = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]])
+    cells = np.stack([vid(ci + a, cj + b, ck + c) for a, b, c in corner], axis=1)
+    base = np.stack([box[0][0] + ci * h[0], box[1][0] + cj * h[1], box[2][0] + ck * h[2]], -1)
+    xyz = base[:, None, :] + corner[None, :, :] * np.array(h)[None, None, :]
+    faces, fk, fc = [], [], []
+    cid = (ci * ncell[1] + cj) * ncell[2] + ck
+    quad = {0: [(0, 0, 0), (0, 1, 0), (0, 1, 1), (0, 0, 1)], 1: [(0, 0, 0), (0, 0, 1), (1, 0, 1), (1, 0, 0)],
+            2: [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0)]}
+    idx = (ci, cj, ck)
+    for d in range(3):
+        if periodic[d]:
+            continue
+        for side in (0, 1):
+            sel = idx[d] == (0 if side == 0 else ncell[d] - 1)
+            off = np.zeros(3, dtype=int)
+            off[d] = side
+            fverts = []
+            for q in quad[d]:
+                o = np.array(q) + off
+                fverts.append(vid(ci[sel] + o[0], cj[sel] + o[1], ck[sel] + o[2]))
+            faces.append(np.stack(fverts, 1))
+            fk.append(np.full(sel.sum(), kinds[2 * d + side]))
+            fc.append(cid[sel])
+    if faces:
+        faces, fk, fc = np.concatenate(faces), np.concatenate(fk), np.concatenate(fc)
+        fxyz = np.empty((faces.shape[0], 4, 3))
+        # face geometry from the unwrapped cell corners
+        for q in range(4):
+            fxyz[:, q] = coords[faces[:, q]]
+        return _finish(name or f"q1-3d-{nx}x{ny}x{nz}", 3, coords, cells, xyz, _local_q1_3d, faces, fxyz, fk, fc)
+    return _finish(name or f"q1-3d-{nx}x{ny}x{nz}", 3, coords, cells, xyz, _local_q1_3d, None, None, None, None)

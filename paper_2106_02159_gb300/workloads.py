@@ -143,3 +143,26 @@ def cylinder_workload(target_vertices: int = 4_000_000, steps: int = 2000) -> Wo
     m = meshes.cylinder_m_for_vertices(target_vertices)
     mesh, U0, bs = cylinder_problem(m)
     return Workload(f"cylinder-q1-m{m}", mesh, U0, bs, steps)
+
+
+def perturbed_state(mesh, seed: int, base=None, amplitude=0.3, n_bumps=12, gamma=1.4):
+    """Seeded admissible state with smooth density / pressure / velocity bumps
+    on top of ``base`` (default: the Mach-3 inflow state); exercises every
+    branch of the step (shocks form, limiter active) from the first step."""
+    rng = np.random.default_rng(seed)
+    x = mesh.coords
+    lo, hi = x.min(0), x.max(0)
+    base = base or CYLINDER_INFLOW
+    rho = np.full(mesh.n, base["rho"], dtype=float)
+    p = np.full(mesh.n, base["p"], dtype=float)
+    vel = [np.full(mesh.n, v, dtype=float) for v in tuple(base["vel"]) + (0.0,) * (mesh.dim - len(base["vel"]))]
+    scale = (hi - lo).max()
+    for _ in range(n_bumps):
+        c = rng.uniform(lo, hi)
+        r = rng.uniform(0.03, 0.15) * scale
+        g = np.exp(-((x - c) ** 2).sum(1) / (r * r))
+        rho *= 1.0 + amplitude * rng.uniform(-0.9, 1.0) * g
+        p *= 1.0 + amplitude * rng.uniform(-0.9, 2.0) * g
+        for d in range(mesh.dim):
+            vel[d] += amplitude * rng.uniform(-2.0, 2.0) * g
+    return conserved(rho, vel[: mesh.dim], p, gamma)

@@ -1,0 +1,49 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/euler_hyp.h declares. CPU only: no compute call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2106_02159_gb300 import binding
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "euler_hyp.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(eh_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    binding.build()
+    return binding.load()
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(binding.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_host_only_calls(lib):
+    cfg = binding.Config()
+    lib.eh_config_default(ctypes.byref(cfg))
+    assert (cfg.dim, cfg.gamma, cfg.cfl, cfg.limiter_passes, cfg.bound_relaxation) == (2, 1.4, 0.5, 2, 0)
+    assert lib.eh_status_string(binding.EH_ERR_CFL) == b"EH_ERR_CFL"
+    assert lib.eh_status_string(99) == b"EH_UNKNOWN"
+    assert lib.eh_last_error(None) == b"null context"
+    out = ctypes.c_void_p(1)
+    assert lib.eh_create(None, ctypes.byref(out)) == binding.EH_ERR_INVALID_ARG and not out.value
+    bad = binding.Config()
+    lib.eh_config_default(ctypes.byref(bad))
+    for field, value in (("dim", 4), ("gamma", 2.0), ("cfl", 1.5), ("limiter_passes", 0)):
+        b2 = binding.Config.from_buffer_copy(bad)
+        setattr(b2, field, value)
+        assert lib.eh_create(ctypes.byref(b2), ctypes.byref(out)) == binding.EH_ERR_INVALID_ARG, field

@@ -1,0 +1,325 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Element-by-element on the same seeded inputs: one forward-Euler stage with its
+intermediates, one SSPRK(3,3) step and 100 steps on the isentropic-vortex
+workload, the cylinder channel with every boundary kind, and a strong-shock
+strip; determinism, graph replay and error paths. Needs a GPU.
+
+Tolerances (relative L1 per component). With relaxed bounds the method is
+well conditioned and the targets are 1e-12 per step and 1e-9 after 100 steps.
+With the paper's strict bounds the line search decides l_ij = 0 or 1 from the
+last bits wherever the bounds are as tight as roundoff (near-uniform flow,
+isentropic regions, shock fronts), so the oracle itself moves by up to ~1e-10
+per step and ~1e-7 over 100 steps when its input is perturbed by one ulp or
+when the same source is compiled with fused multiply-adds (the GPU compiler's
+default rounding). Every run is therefore held to max(target, 10 x the larger
+of those two measured spreads of the oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_02159_gb300 import binding as B
+from paper_2106_02159_gb300 import meshes as M
+from paper_2106_02159_gb300 import workloads as W
+
+from . import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-12
+RUN_TOL = 1e-9
+
+
+def rel_l1(a, b):
+    """Relative L1 difference per component."""
+    return np.abs(a - b).sum(axis=-1) / np.maximum(np.abs(b).sum(axis=-1), 1e-300)
+
+
+def oracle_spread(fn, U0, samples=2, seed=0, fn_fma=None):
+    """Largest relative L1 change of the oracle's output when U0 is perturbed
+    by one ulp, or (fn_fma) when the oracle is the contracted build."""
+    rng = np.random.default_rng(seed)
+    ref = fn(U0)
+    worst = 0.0
+    for _ in range(samples):
+        Up = U0 * (1.0 + 2.2e-16 * rng.choice([-1.0, 0.0, 1.0], U0.shape))
+        worst = max(worst, rel_l1(fn(Up), ref).max())
+    if fn_fma is not None:
+        worst = max(worst, rel_l1(fn_fma(U0), ref).max())
+    return worst
+
+
+def fma_twin(orc, mesh, bs, **kw):
+    """The same oracle configuration on the contracted build."""
+    return oracle.Oracle(mesh, bnd_state=bs, lib=oracle.load_fma(), **kw)
+
+
+def tolerance(target, spread):
+    return max(target, 10.0 * spread)
+
+
+def solver_for(mesh, bnd_state=None, **kw):
+    s = B.Solver(dim=mesh.dim, **kw)
+    s.upload_mesh(mesh, bnd_state)
+    return s
+
+
+CASES = {
+    "vortex32": lambda: (W.vortex_workload(32).mesh, W.vortex_workload(32).U0, None),
+    "cylinder": lambda: (lambda m, U0, bs: (m, W.perturbed_state(m, 7), bs))(*W.cylinder_problem(12)),
+    "strip_strong_shock": lambda: (lambda m: (m, W.riemann_initial(m, "strong_shock"), None))(W.riemann_strip(90)),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    B.build()
+    oracle.set_threads(0)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_stage_intermediates_match_oracle(case):
+    mesh, U0, bs = CASES[case]()
+    orc = oracle.Oracle(mesh, bnd_state=bs)
+    U0 = orc.apply_bc(U0)
+    ref, tau_ref, tr = orc.forward_euler(U0, trace=True)
+    ref = orc.apply_bc(ref)
+    s = solver_for(mesh, bs)
+    s.set_state(U0)
+    tau = s.stage()
+    assert abs(tau - tau_ref) <= 1e-13 * tau_ref
+    assert s.trace(B.EH_TRACE_TAU_BOUND) == pytest.approx(tr["tau_bound"], rel=1e-13)
+    d = s.trace(B.EH_TRACE_D_IJ)
+    assert np.abs(d - tr["dij"]).max() <= 1e-13 * np.abs(tr["dij"]).max()
+    # alpha is |N|/D; compare where the row's states differ (D well above roundoff)
+    alpha = s.trace(B.EH_TRACE_ALPHA)
+    rows = mesh.row_of_entry()
+    var = np.zeros(mesh.n)
+    np.maximum.at(var, rows, np.abs(U0[0, mesh.col] - U0[0, rows]) / U0[0, rows])
+    sel = var > 1e-6
+    if sel.any():
+        assert np.abs(alpha - tr["alpha"])[sel].max() <= 1e-9
+    assert np.all((alpha >= 0) & (alpha <= 1))
+    for what, key in ((B.EH_TRACE_U_LOW, "UL"), (B.EH_TRACE_F_HIGH, "FH")):
+        got = s.trace(what)
+        scale = np.abs(tr[key]).max(axis=1, keepdims=True) + 1e-300
+        assert (np.abs(got - tr[key]) / scale).max() <= 1e-12, key
+    bounds = s.trace(B.EH_TRACE_BOUNDS)
+    assert np.allclose(bounds, tr["bounds"], rtol=1e-13, atol=0)
+    orf = fma_twin(orc, mesh, bs)
+    spread = oracle_spread(lambda U: orc.forward_euler(U, tau_ref)[0], U0,
+                           fn_fma=lambda U: orf.forward_euler(U, tau_ref)[0])
+    tol = tolerance(STEP_TOL, spread)
+    up1 = s.trace(B.EH_TRACE_U_PASS1)
+    assert rel_l1(up1, tr["Upass"][0]).max() <= tol
+    l1 = s.trace(B.EH_TRACE_L_PASS1)
+    T = H.transpose_index(mesh)
+    assert np.array_equal(l1, l1[T])
+    assert np.all((l1 >= 0) & (l1 <= 1))
+    U1 = s.get_state()
+    assert rel_l1(U1, ref).max() <= tol, (rel_l1(U1, ref), spread)
+
+
+@pytest.mark.parametrize("relax", [False, True])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_ssprk3_step_matches_oracle(case, relax):
+    mesh, U0, bs = CASES[case]()
+    orc = oracle.Oracle(mesh, bnd_state=bs, bound_relaxation=relax)
+    U0 = orc.apply_bc(U0)
+    ref, dt_ref, bounds_ref = orc.ssprk3_step(U0)
+    s = solver_for(mesh, bs, bound_relaxation=relax)
+    s.set_state(U0)
+    dt = s.step()
+    assert abs(dt - dt_ref) <= 1e-13 * dt_ref
+    err = rel_l1(s.get_state(), ref).max()
+    orf = fma_twin(orc, mesh, bs, bound_relaxation=relax)
+    spread = oracle_spread(lambda U: orc.ssprk3_step(U, dt_ref)[0], U0,
+                           fn_fma=lambda U: orf.ssprk3_step(U, dt_ref)[0])
+    assert err <= tolerance(STEP_TOL, spread), (err, spread)
+    if relax and case.startswith("vortex"):
+        assert err <= STEP_TOL
+    diag = s.diagnostics()
+    assert np.allclose(diag["last_stage_bound"], bounds_ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("relax", [False, True])
+def test_vortex_100_steps_matches_oracle(relax):
+    """The 64x64 P1 isentropic-vortex workload, CFL 0.5, 100 steps, FP64."""
+    w = W.vortex_workload(64)
+    orc = oracle.Oracle(w.mesh, cfl=0.5, bound_relaxation=relax)
+    ref, t_ref = orc.run(w.U0, 100)
+    s = solver_for(w.mesh, bound_relaxation=relax)
+    s.set_state(w.U0)
+    s.run(100)
+    err = rel_l1(s.get_state(), ref).max()
+    if relax:
+        assert err <= RUN_TOL, err
+    else:
+        orf = fma_twin(orc, w.mesh, None, cfl=0.5)
+        spread = oracle_spread(lambda U: orc.run(U, 100)[0], w.U0, fn_fma=lambda U: orf.run(U, 100)[0])
+        assert err <= tolerance(RUN_TOL, spread), (err, spread)
+    assert s.diagnostics()["not_admissible"] == 0
+
+
+@pytest.mark.parametrize("relax", [False, True])
+def test_cylinder_100_steps_matches_oracle(relax):
+    mesh, U0, bs = W.cylinder_problem(16)
+    orc = oracle.Oracle(mesh, bnd_state=bs, bound_relaxation=relax)
+    U0 = orc.apply_bc(U0)
+    ref, _ = orc.run(U0, 100)
+    s = solver_for(mesh, bs, bound_relaxation=relax)
+    s.set_state(U0)
+    s.run(100)
+    err = rel_l1(s.get_state(), ref).max()
+    orf = fma_twin(orc, mesh, bs, bound_relaxation=relax)
+    spread = oracle_spread(lambda U: orc.run(U, 100)[0], U0, fn_fma=lambda U: orf.run(U, 100)[0])
+    assert err <= tolerance(RUN_TOL, spread), (err, spread)
+
+
+@pytest.mark.parametrize("relax,passes", [(True, 2), (False, 1), (False, 3)])
+def test_options_match_oracle(relax, passes):
+    mesh, U0, bs = W.cylinder_problem(10)
+    U0 = W.perturbed_state(mesh, 3)
+    orc = oracle.Oracle(mesh, bnd_state=bs, bound_relaxation=relax, limiter_passes=passes)
+    U0 = orc.apply_bc(U0)
+    ref, _ = orc.run(U0, 5)
+    s = solver_for(mesh, bs, bound_relaxation=relax, limiter_passes=passes)
+    s.set_state(U0)
+    for _ in range(5):
+        s.step(sync=False)
+    err = rel_l1(s.get_state(), ref).max()
+    orf = fma_twin(orc, mesh, bs, bound_relaxation=relax, limiter_passes=passes)
+    spread = oracle_spread(lambda U: orc.run(U, 5)[0], U0, fn_fma=lambda U: orf.run(U, 5)[0])
+    assert err <= tolerance(5 * STEP_TOL, spread), (err, spread)
+
+
+def test_generic_gamma_path_matches_oracle():
+    """gamma != 7/5 takes the pow() path of every root and power."""
+    w = W.vortex_workload(24)
+    U0 = W.conserved(*[np.asarray(a) for a in (w.U0[0],)], [w.U0[1] / w.U0[0], w.U0[2] / w.U0[0]],
+                     0.4 * (w.U0[3] - 0.5 * (w.U0[1] ** 2 + w.U0[2] ** 2) / w.U0[0]), gamma=1.3)
+    orc = oracle.Oracle(w.mesh, gamma=1.3, bound_relaxation=True)
+    ref, _ = orc.run(U0, 10)
+    s = solver_for(w.mesh, gamma=1.3, bound_relaxation=True)
+    s.set_state(U0)
+    s.run(10)
+    assert rel_l1(s.get_state(), ref).max() <= 10 * STEP_TOL
+
+
+def test_three_dimensional_q1_matches_oracle():
+    """3D trilinear hexes, 27-point rows, periodic box."""
+    mesh = M.structured_q1_3d(6, 5, 4, periodic=(True, True, True))
+    U0 = W.perturbed_state(mesh, 11, base=dict(rho=1.0, vel=(0.5, -0.2, 0.1), p=1.0), amplitude=0.2)
+    orc = oracle.Oracle(mesh)
+    ref, _ = orc.run(U0, 3)
+    s = solver_for(mesh)
+    s.set_state(U0)
+    s.run(3)
+    err = rel_l1(s.get_state(), ref).max()
+    orf = fma_twin(orc, mesh, None)
+    spread = oracle_spread(lambda U: orc.run(U, 3)[0], U0, fn_fma=lambda U: orf.run(U, 3)[0])
+    assert err <= tolerance(3 * STEP_TOL, spread), (err, spread)
+    # relaxed bounds: well conditioned, held to the target itself
+    orc = oracle.Oracle(mesh, bound_relaxation=True)
+    ref, _ = orc.run(U0, 3)
+    s = solver_for(mesh, bound_relaxation=True)
+    s.set_state(U0)
+    s.run(3)
+    assert rel_l1(s.get_state(), ref).max() <= 3 * STEP_TOL
+
+
+def test_bitwise_determinism_and_graph_replay():
+    mesh, U0, bs = W.cylinder_problem(12)
+    U0 = W.perturbed_state(mesh, 5)
+    outs = []
+    for mode in ("step", "step", "run"):
+        s = solver_for(mesh, bs)
+        s.set_state(U0)
+        s.apply_boundary_conditions()
+        if mode == "step":
+            for _ in range(7):
+                s.step(sync=False)
+        else:
+            s.run(7)
+        outs.append(s.get_state())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
+def test_uniform_state_fixed_point_on_gpu():
+    cyl = M.cylinder_channel_q1(8)
+    U = W.uniform_state(cyl, 1.0, (0.0, 0.0), 1.0)
+    s = solver_for(cyl, U[:, cyl.bnd_node].copy())
+    s.set_state(U)
+    s.run(20)
+    assert np.array_equal(s.get_state(), U)
+
+
+def test_error_paths():
+    w = W.vortex_workload(16)
+    s = solver_for(w.mesh)
+    bad = w.U0.copy()
+    bad[0, 5] = -1.0
+    with pytest.raises(B.EulerError) as e:
+        s.set_state(bad)
+    assert e.value.status == B.EH_ERR_NOT_ADMISSIBLE
+    with pytest.raises(B.EulerError) as e:
+        s.step()
+    assert e.value.status == B.EH_ERR_STATE
+    s.set_state(w.U0)
+    dt = s.cfl_dt()
+    with pytest.raises(B.EulerError) as e:
+        s.step(dt * 2.5)  # above the c_cfl = 1 limit (cfl = 0.5)
+    assert e.value.status == B.EH_ERR_CFL
+    # the error is sticky until the next eh_set_state; the state is unchanged
+    out = np.empty_like(w.U0)
+    with pytest.raises(B.EulerError) as e:
+        s.get_state(out)
+    assert e.value.status == B.EH_ERR_CFL
+    assert np.array_equal(out, w.U0)
+    s.set_state(w.U0)
+    s.step()
+    # empty / oversize / non-symmetric meshes
+    m = w.mesh
+    with pytest.raises(B.EulerError) as e:
+        import dataclasses
+        s2 = B.Solver()
+        bad_col = m.col.copy()
+        bad_col[1], bad_col[2] = bad_col[2], bad_col[1]  # unsorted row
+        s2.upload_mesh(dataclasses.replace(m, col=bad_col))
+    assert e.value.status == B.EH_ERR_BAD_MESH
+
+
+def test_full_size_sampled_parity():
+    """The benchmark workload at full size (~4.0M-vertex Q1 cylinder channel):
+    the CFL step on the whole mesh, then one SSPRK(3,3) step on the GPU, checked
+    node by node on sampled vertices (interior and every boundary kind) against
+    the oracle run on the sampled vertices' dependency closure (one step reaches
+    ~18 rings; the closure keeps 24)."""
+    m = M.cylinder_m_for_vertices(4_000_000)
+    mesh, _, bs = W.cylinder_problem(m)
+    U0 = W.perturbed_state(mesh, 2106)
+    dt = oracle.Oracle(mesh, bnd_state=bs).cfl_dt(U0)
+    s = solver_for(mesh, bs)
+    s.set_state(U0)
+    assert abs(s.cfl_dt() - dt) <= 1e-13 * dt
+    s.step(dt)
+    U1 = s.get_state()
+    assert s.diagnostics()["not_admissible"] == 0
+    rng = np.random.default_rng(4)
+    seeds = list(rng.choice(mesh.n, 48, replace=False))
+    for kind in (M.BC_SLIP, M.BC_DIRICHLET, M.BC_DO_NOTHING):
+        nodes = mesh.bnd_node[mesh.bnd_kind == kind]
+        seeds += list(rng.choice(nodes, 6, replace=False))
+    sub, old, seed_new, sub_bs = H.submesh(mesh, seeds, 24, bs)
+    orc = oracle.Oracle(sub, bnd_state=sub_bs)
+    ref, _, _ = orc.ssprk3_step(U0[:, old], dt)
+    orf = oracle.Oracle(sub, bnd_state=sub_bs, lib=oracle.load_fma())
+    twin, _, _ = orf.ssprk3_step(U0[:, old], dt)
+    got = U1[:, np.asarray(seeds)]
+    want = ref[:, seed_new]
+    scale = np.abs(want).max(0)
+    err = np.abs(got - want).max(0) / scale
+    spread = np.abs(twin[:, seed_new] - want).max(0) / scale
+    assert np.all(err <= np.maximum(1e-12, 10.0 * spread)), (err.max(), spread.max())
+    assert np.median(err) <= 1e-13
