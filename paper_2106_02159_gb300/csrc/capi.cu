@@ -402,7 +402,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   const int SP = SP_of(c);
   Work &w = c->wk;
   w.nblocks_rows = (int)((n + 127) / 128);
-  ALLOC(w.rec, (size_t)n * REC);
+  ALLOC(w.rec, (size_t)n * REC_MAX);
   ALLOC(w.alpha, n);
   ALLOC(w.w, (size_t)nnz * SP);
   ALLOC(w.d, nnz);

@@ -6,8 +6,8 @@
 // is bound by FP64 instruction issue, not by HBM. Every edge loop therefore
 // runs one thread per CSR row (no idle lanes in 7/9/27-entry rows), sums in
 // the row's column order (bitwise reproducible), and trades bytes for FP64
-// work: per-node quantities (primitives, a p^-z, Phi, eta) are computed once
-// per stage in k_prep and gathered; |c_ij|, 1/|c_ij|, m_ij/m_j and m_ji/m_i are
+// work: per-node quantities (primitives, a p^-z, Phi, eta, the flux f(U)) are
+// computed once per stage in k_prep and gathered; |c_ij|, 1/|c_ij|, m_ij/m_j and m_ji/m_i are
 // static per-edge arrays; (f(U_j) - f(U_i)) c_ij is computed once per edge in
 // k_visc and reused by k_low; the limiter directions P_ij are stored.
 #include "kernels.cuh"
@@ -131,17 +131,40 @@ __device__ __forceinline__ double dpsi(const Params &p, const double *ub, const 
 
 constexpr int LINE_SEARCH_ITERATIONS = 6;
 
+// phimin5 = phimin^5 (used by the gamma = 7/5 fast check only).
 template <int DIM>
 __device__ double line_search(const Params &p, const double *ub, const double *P, double rmin, double rmax,
-                              double phimin) {
+                              double phimin, double phimin5) {
+  constexpr int S = DIM + 2;
   double l = 1.0;
-  double rb = ub[0], rp = P[0];
+  const double rb = ub[0], rp = P[0];
+  // density: the division is needed only when l = 1 leaves [rho_min, rho_max]
   if (rp > 0.0) {
-    l = fmin(l, (rmax - rb) / rp);
+    if (rb + rp > rmax) l = fmin(l, (rmax - rb) / rp);
   } else if (rp < 0.0) {
-    l = fmin(l, (rmin - rb) / rp);
+    if (rb + rp < rmin) l = fmin(l, (rmin - rb) / rp);
   }
   l = fmax(0.0, fmin(1.0, l));
+  // entropy at l: for gamma = 7/5, psi(l) >= 0 <=> (eps rho)^5 >= Phi_min^5 rho^12
+  // when eps rho > 0 -- no division and no root on the common path
+  if (p.gamma75) {
+    double u[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) u[s] = ub[s] + l * P[s];
+    const double rho = u[0];
+    if (rho > 1e-6 && rho < 1e6) {
+      double m2 = 0.0;
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) m2 += u[1 + q] * u[1 + q];
+      const double er = u[S - 1] * rho - 0.5 * m2;
+      if (er > 0.0) {
+        const double r2 = rho * rho, r4 = r2 * r2, r12 = r4 * r4 * r4;
+        const double e2 = er * er;
+        const double lhs = e2 * e2 * er, rhs = phimin5 * r12;
+        if (rhs < 1e300 && lhs >= rhs) return l;
+      }
+    }
+  }
   double pr = psi<DIM>(p, ub, P, l, phimin);
   if (pr >= 0.0) return l;
   double pl = psi<DIM>(p, ub, P, 0.0, phimin);
@@ -219,7 +242,7 @@ __global__ void __launch_bounds__(TPB) k_prep(MeshView m, Params p, const double
     phi = eps * pow(rho, -p.gamma);
   }
   double eta = -rho * (log(phi) / p.gm1);
-  double *Rr = rec + (int64_t)i * REC;
+  double *Rr = rec + (int64_t)i * R::SIZE;
 #pragma unroll
   for (int s = 0; s < S; ++s) Rr[s] = u[s];
 #pragma unroll
@@ -230,7 +253,13 @@ __global__ void __launch_bounds__(TPB) k_prep(MeshView m, Params p, const double
   Rr[R::IP] = 1.0 / pr;
   Rr[R::PHI] = phi;
   Rr[R::ETA] = eta;
-  Rr[R::ETA + 1] = eps;
+  Rr[R::EPS] = eps;
+  double f[S][DIM];
+  flux<DIM>(u, v, pr, f);
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) Rr[R::F + s * DIM + q] = f[s][q];
 }
 
 // ---------------------------------------------------------------------------
@@ -244,16 +273,19 @@ __global__ void __launch_bounds__(TPB) k_visc(MeshView m, Params p, Work w) {
   using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || w.st->err) return;
-  const double *Ri = w.rec + (int64_t)i * REC;
+  const double *Ri = w.rec + (int64_t)i * R::SIZE;
   double ui[S], vi[DIM];
 #pragma unroll
   for (int s = 0; s < S; ++s) ui[s] = Ri[s];
 #pragma unroll
   for (int k = 0; k < DIM; ++k) vi[k] = Ri[R::V + k];
   const double pi = Ri[R::P], ai = Ri[R::A], azi = Ri[R::AZ], ipi = Ri[R::IP], etai = Ri[R::ETA];
-  const double epsi = Ri[R::ETA + 1];
+  const double epsi = Ri[R::EPS];
   double fi[S][DIM];
-  flux<DIM>(ui, vi, pi, fi);
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) fi[s][q] = Ri[R::F + s * DIM + q];
   // eta'(U_i) (Sec. 3.2 indicator)
   double deta[S];
   {
@@ -276,7 +308,7 @@ __global__ void __launch_bounds__(TPB) k_visc(MeshView m, Params p, Work w) {
   for (int64_t k = k0; k < k1; ++k) {
     const int j = m.col[k];
     if (j == i) continue;
-    const double *Rj = w.rec + (int64_t)j * REC;
+    const double *Rj = w.rec + (int64_t)j * R::SIZE;
     double uj[S], vj[DIM], c[DIM];
 #pragma unroll
     for (int s = 0; s < S; ++s) uj[s] = Rj[s];
@@ -286,14 +318,12 @@ __global__ void __launch_bounds__(TPB) k_visc(MeshView m, Params p, Work w) {
       c[q] = m.cij[(int64_t)q * m.nnz + k];
     }
     const double pj = Rj[R::P], etaj = Rj[R::ETA];
-    double fj[S][DIM];
-    flux<DIM>(uj, vj, pj, fj);
     double wv[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       double acc = 0.0;
 #pragma unroll
-      for (int q = 0; q < DIM; ++q) acc += (fj[s][q] - fi[s][q]) * c[q];
+      for (int q = 0; q < DIM; ++q) acc += (Rj[R::F + s * DIM + q] - fi[s][q]) * c[q];
       wv[s] = acc;
     }
     double *wk = w.w + k * SP;
@@ -349,7 +379,7 @@ __global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
   const bool active = i < m.n && !w.st->err;
   double bound = INFINITY;
   if (active) {
-    const double *Ri = w.rec + (int64_t)i * REC;
+    const double *Ri = w.rec + (int64_t)i * R::SIZE;
     double ui[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) ui[s] = Ri[s];
@@ -357,7 +387,10 @@ __global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
     double inc[S], fh[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) inc[s] = fh[s] = 0.0;
-    double rmin = ui[0], rmax = ui[0], phimin = Ri[R::PHI], dsum = 0.0;
+    // bar-state densities rho_bar = num / den, den = 2 d_ij > 0; the running
+    // minimum / maximum is kept as a fraction and compared by cross-multiplication
+    double nmin = ui[0], dmin = 1.0, nmax = ui[0], dmax = 1.0;
+    double phimin = Ri[R::PHI], dsum = 0.0;
     int64_t kd = -1;
     const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
     for (int64_t k = k0; k < k1; ++k) {
@@ -366,7 +399,7 @@ __global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
         kd = k;
         continue;
       }
-      const double *Rj = w.rec + (int64_t)j * REC;
+      const double *Rj = w.rec + (int64_t)j * R::SIZE;
       const double dk = w.d[k];
       const double *wk = w.w + k * SP;
       const double dH = 0.5 * (alphai + w.alpha[j]) * dk;
@@ -379,9 +412,18 @@ __global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
         inc[s] += dk * du - ws;
         fh[s] += -ws + dH * du;
       }
-      const double rbar = dk > 0.0 ? 0.5 * (ui[0] + Rj[0]) - w0 / (2.0 * dk) : ui[0];
-      rmin = fmin(rmin, rbar);
-      rmax = fmax(rmax, rbar);
+      if (dk > 0.0) {
+        const double num = dk * (ui[0] + Rj[0]) - w0;
+        const double den = 2.0 * dk;
+        if (num * dmin < nmin * den) {
+          nmin = num;
+          dmin = den;
+        }
+        if (num * dmax > nmax * den) {
+          nmax = num;
+          dmax = den;
+        }
+      }
       phimin = fmin(phimin, Rj[R::PHI]);
       dsum += dk;
     }
@@ -394,6 +436,8 @@ __global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
       inci[s] = inc[s];
       fhi[s] = fh[s];
     }
+    const double rmin = dmin == 1.0 ? nmin : nmin / dmin;
+    const double rmax = dmax == 1.0 ? nmax : nmax / dmax;
     const double r = m.relax[i];
     double *bi = w.bounds + (int64_t)i * 4;
     bi[0] = (1.0 - r) * rmin;
@@ -454,10 +498,11 @@ template <int DIM>
 __global__ void __launch_bounds__(TPB) k_lim1(MeshView m, Params p, Work w) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
+  using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || w.st->err) return;
   const double tau = w.st->tau;
-  const double *Ri = w.rec + (int64_t)i * REC;
+  const double *Ri = w.rec + (int64_t)i * R::SIZE;
   double ui[S], ul[S], fhi[S];
   const double *inci = w.inc + (int64_t)i * SP;
   const double *FHi = w.FH + (int64_t)i * SP;
@@ -473,6 +518,7 @@ __global__ void __launch_bounds__(TPB) k_lim1(MeshView m, Params p, Work w) {
   for (int s = 0; s < S; ++s) ULi[s] = ul[s];
   const double *bi = w.bounds + (int64_t)i * 4;
   const double rmin = bi[0], rmax = bi[1], phimin = bi[2];
+  const double phimin2 = phimin * phimin, phimin5 = phimin2 * phimin2 * phimin;
   const double alphai = w.alpha[i];
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
   const double coef = tau * (double)(k1 - k0 - 1) * m.inv_mi[i];
@@ -485,7 +531,7 @@ __global__ void __launch_bounds__(TPB) k_lim1(MeshView m, Params p, Work w) {
       w.la[k] = 1.0;
       continue;
     }
-    const double *Rj = w.rec + (int64_t)j * REC;
+    const double *Rj = w.rec + (int64_t)j * R::SIZE;
     const double *FHj = w.FH + (int64_t)j * SP;
     const double dk = w.d[k];
     const double dH = 0.5 * (alphai + w.alpha[j]) * dk;
@@ -496,7 +542,7 @@ __global__ void __launch_bounds__(TPB) k_lim1(MeshView m, Params p, Work w) {
       P[s] = coef * (-b * FHj[s] + bt * fhi[s] + (dH - dk) * (Rj[s] - ui[s]));
       Pk[s] = P[s];
     }
-    w.la[k] = line_search<DIM>(p, ul, P, rmin, rmax, phimin);
+    w.la[k] = line_search<DIM>(p, ul, P, rmin, rmax, phimin, phimin5);
   }
 }
 
@@ -533,6 +579,7 @@ __global__ void __launch_bounds__(TPB) k_pass(MeshView m, Params p, Work w, cons
   for (int s = 0; s < S; ++s) Uo[s] = u[s];
   const double *bi = w.bounds + (int64_t)i * 4;
   const double rmin = bi[0], rmax = bi[1], phimin = bi[2];
+  const double phimin2 = phimin * phimin, phimin5 = phimin2 * phimin2 * phimin;
   for (int64_t k = k0; k < k1; ++k) {
     if (m.col[k] == i) {
       lout[k] = 1.0;
@@ -546,7 +593,7 @@ __global__ void __launch_bounds__(TPB) k_pass(MeshView m, Params p, Work w, cons
       P[s] = (1.0 - l) * Pk[s];
       Pk[s] = P[s];
     }
-    lout[k] = line_search<DIM>(p, u, P, rmin, rmax, phimin);
+    lout[k] = line_search<DIM>(p, u, P, rmin, rmax, phimin, phimin5);
   }
 }
 

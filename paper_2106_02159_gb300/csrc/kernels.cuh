@@ -15,8 +15,8 @@ template <int DIM> struct Layout {
 };
 
 // Node record written once per stage by k_prep and gathered by the edge loops:
-// [0..S) state, then the primitive and derived quantities below.
-constexpr int REC = 16;
+// [0..S) state, then the primitive and derived quantities below, then the
+// flux f(U) (S x DIM, row-major).
 template <int DIM> struct Rec {
   static constexpr int V = DIM + 2;       // v_1..v_dim
   static constexpr int P = 2 * DIM + 2;   // pressure p
@@ -25,7 +25,12 @@ template <int DIM> struct Rec {
   static constexpr int IP = 2 * DIM + 5;  // 1/p
   static constexpr int PHI = 2 * DIM + 6; // Phi = eps rho^-gamma
   static constexpr int ETA = 2 * DIM + 7; // eta = -rho s
+  static constexpr int EPS = 2 * DIM + 8; // internal energy eps
+  static constexpr int F = 2 * DIM + 9;   // flux f(U)[s][q] at F + s * DIM + q
+  static constexpr int SIZE = DIM == 2 ? 24 : 32;
+  static_assert(F + (DIM + 2) * DIM <= SIZE, "node record too small");
 };
+constexpr int REC_MAX = 32;  // record stride allocated for either dimension
 
 struct DevStatus {
   int err;                       // eh_status of a device-detected failure, 0 if none
@@ -68,7 +73,7 @@ struct Params {
 };
 
 struct Work {
-  double *rec;     // [n][REC]
+  double *rec;     // [n][Rec<DIM>::SIZE]
   double *alpha;   // [n]
   double *w;       // [nnz][SP]  (f(U_j) - f(U_i)) c_ij
   double *d;       // [nnz]      d^L_ij (diagonal: d_ii)
