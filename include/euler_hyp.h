@@ -168,6 +168,37 @@ enum {
 eh_status eh_profile_enable(eh_ctx *ctx, int enable);
 eh_status eh_profile_read(eh_ctx *ctx, int kernel, double *total_ms, int64_t *launches);
 
+/* Allocation-free CFL time step. (The paper has no counterpart: this is a
+ * service of the library, not a step of the method.)
+ *
+ * For callers that cannot allocate device memory when they need a time step --
+ * a host framework that owns all device memory through its own pool and does
+ * not let plug-in libraries call cudaMalloc, or a real-time loop where an
+ * allocation (which can synchronise the device) is not allowed. It needs no
+ * eh_ctx. It computes tau = cfl * min_i m_i / (2 sum_{j != i} d_ij) with d_ij
+ * the graph viscosity of the state (the same quantity as eh_cfl_dt) from the
+ * caller's own device arrays:
+ *   row_ptr[n+1] (int64), col[nnz] (int32): CSR as for eh_upload_mesh (sorted,
+ *     diagonal present, symmetric pattern -- not checked here);
+ *   cij[dim][nnz], mi[n]; is_boundary[n] (1 for boundary nodes) or NULL when
+ *     no node lies on the boundary; U[dim+2][n] an admissible state;
+ *   dt_out: device pointer to one double, written by the last kernel.
+ * Work is queued on 'stream' (a cudaStream_t, NULL for the default stream) of
+ * the current device; the call does not synchronise.
+ * Scratch: a file-scope device array of EH_CFL_NOALLOC_MAX_ROWS / 128 doubles
+ * (512 KiB) that every GPU loading the library keeps until the process ends;
+ * n above EH_CFL_NOALLOC_MAX_ROWS returns EH_ERR_INVALID_ARG before any work.
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call overwrites the entries it reads, so nothing needs clearing, but
+ * all calls share the array: two calls whose kernels overlap on the GPU (on
+ * different streams without ordering) race and give wrong results.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+#define EH_CFL_NOALLOC_MAX_ROWS (1 << 23)
+eh_status eh_cfl_dt_noalloc(int32_t dim, double gamma, double cfl, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                            const int32_t *col, const double *cij, const double *mi,
+                            const unsigned char *is_boundary, const double *U, double *dt_out, void *stream);
+
 /* Number of kernel launches one eh_step issues (for accounting). */
 int32_t eh_launches_per_step(const eh_ctx *ctx);
 

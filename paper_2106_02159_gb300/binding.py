@@ -18,7 +18,7 @@ _ROOT = os.path.dirname(_HERE)
 CSRC = os.path.join(_HERE, "csrc")
 BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libeuler_hyp.so")
-SOURCES = ("kernels.cu", "capi.cu")
+SOURCES = ("kernels.cu", "capi.cu", "noalloc.cu")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 
@@ -33,7 +33,8 @@ EH_PRECISION_FP64, EH_PRECISION_MIXED = 0, 1
 EXPORTS = ("eh_config_default", "eh_create", "eh_upload_mesh", "eh_set_state", "eh_get_state",
            "eh_apply_boundary_conditions", "eh_cfl_dt", "eh_stage", "eh_step", "eh_run", "eh_synchronize",
            "eh_get_diagnostics", "eh_trace", "eh_profile_enable", "eh_profile_read", "eh_launches_per_step",
-           "eh_last_error", "eh_status_string", "eh_destroy")
+           "eh_last_error", "eh_status_string", "eh_destroy", "eh_cfl_dt_noalloc")
+CFL_NOALLOC_MAX_ROWS = 1 << 23
 KERNEL_NAMES = ("prep", "visc", "low", "tau", "lim1", "pass", "final")
 
 
@@ -102,6 +103,7 @@ def load(path: str | None = None):
     lib.eh_status_string.restype = ctypes.c_char_p
     lib.eh_destroy.argtypes = [vp]
     lib.eh_destroy.restype = None
+    lib.eh_cfl_dt_noalloc.argtypes = [i32, ctypes.c_double, ctypes.c_double, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("eh_config_default", "eh_destroy", "eh_launches_per_step", "eh_last_error",
                         "eh_status_string"):
@@ -109,6 +111,22 @@ def load(path: str | None = None):
     if path == LIB_PATH:
         _lib = lib
     return lib
+
+
+def cfl_dt_noalloc(dim, gamma, cfl, row_ptr, col, cij, mi, is_boundary, U, dt_out, stream=None, lib=None):
+    """eh_cfl_dt_noalloc on CUDA tensors (device pointers; nothing is allocated
+    by the library). dt_out: a one-element float64 CUDA tensor. Queues the
+    work on ``stream`` (a torch.cuda.Stream or None) without synchronising."""
+    lib = lib or load()
+    n = int(mi.shape[0])
+    if n > CFL_NOALLOC_MAX_ROWS:
+        raise ValueError(f"eh_cfl_dt_noalloc handles at most {CFL_NOALLOC_MAX_ROWS} rows, got {n}")
+    ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    st = lib.eh_cfl_dt_noalloc(dim, gamma, cfl, n, int(col.shape[0]), ptr(row_ptr), ptr(col), ptr(cij), ptr(mi),
+                               ptr(is_boundary), ptr(U), ptr(dt_out),
+                               None if stream is None else ctypes.c_void_p(stream.cuda_stream))
+    if st != EH_OK:
+        raise EulerError(st, f"eh_cfl_dt_noalloc: {lib.eh_status_string(st).decode()}")
 
 
 class EulerError(RuntimeError):
