@@ -13,8 +13,10 @@ e2e     : the same metric through the C ABI with host buffers: every step
           copies the state from pinned host memory in (eh_set_state) and back
           out (eh_get_state), inside the timed region.
 roofline: the kernel with the largest share of the step time (CUDA events
-          around each kernel on the solver's stream), its algorithmic bytes per
-          launch over its mean duration, against the measured HBM copy rate.
+          around each kernel on the solver's stream): its algorithmic FP64 flops
+          per launch over its mean duration against the FP64 peak (every kernel
+          of this path is bound by FP64 issue on GB300); its algorithmic bytes
+          against the measured HBM copy rate are reported beside it.
 cpu_baseline : the FP64 oracle on the host cores, on a window of the same mesh.
 
 --impl reference runs the oracle (the CPU reference of this repository) for
@@ -172,6 +174,39 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
     return per[0] * n + per[1] * nnz
 
 
+def algorithmic_fp64_flops(kernel: str, n: int, nnz: int, dim: int) -> float:
+    """FP64 floating-point operations each kernel performs per launch on the
+    common path (+, -, *, /, sqrt = 1; fused multiply-add = 2; comparisons,
+    min/max and the data-dependent branches -- shock sqrt terms, the density
+    division when l = 1 is infeasible, the entropy iteration -- not counted),
+    from the formulas of each kernel: a count per off-diagonal entry times
+    nnz - n plus a count per node times n."""
+    S = dim + 2
+    e = nnz - n
+    per_entry = {
+        "prep": 0,
+        "visc": 3 * S * dim + 4 * dim + 2 * S + 4 + (5 * dim + 15) / 2.0,
+        "low": 7 * S + 12,
+        "lim1": 9 * S + 2 * dim + 18,
+        "pass": 5 * S + 2 * dim + 16,
+        "final": 2 * S + 1,
+        "tau": 0,
+    }[kernel]
+    per_node = {
+        "prep": 4 * dim + S * dim + 45,
+        "visc": 3 * dim + 12,
+        "low": 11,
+        "lim1": 2 * S + 6,
+        "pass": 3,
+        "final": 4 * dim + 3 * S,
+        "tau": 0,
+    }[kernel]
+    return per_entry * e + per_node * n
+
+
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
 def peaks():
     try:
         d = json.load(open(MEASURED_PEAKS))
@@ -324,10 +359,17 @@ def run_ours(args, dist):
     top_ms = prof[top][0] / prof[top][1]
     hbm, hbm_src = peaks()
     bytes_top = algorithmic_bytes(top, mesh.n, mesh.nnz, mesh.dim)
-    achieved = bytes_top / (top_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": f"k_{top}", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": hbm_src,
-                "algorithmic_bytes_per_launch": bytes_top, "mean_launch_ms": top_ms,
+    flops_top = algorithmic_fp64_flops(top, mesh.n, mesh.nnz, mesh.dim)
+    achieved = flops_top / (top_ms * 1e-3) / 1e12
+    hbm_achieved = bytes_top / (top_ms * 1e-3) / 1e9
+    # every kernel of the step is bound by FP64 issue on GB300 (ncu: FP64 pipe
+    # 83-86% of peak, DRAM <= 1 TB/s), so the roofline is the FP64 ALU one
+    roofline = {"bound": "alu", "kernel": f"k_{top}", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz); probe-measured FMA rate 1.01",
+                "algorithmic_fp64_flops_per_launch": flops_top, "mean_launch_ms": top_ms,
+                "hbm": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
+                        "peak_source": hbm_src, "algorithmic_bytes_per_launch": bytes_top},
                 "kernel_shares": {k: round(v, 4) for k, v in sorted(shares.items(), key=lambda t: -t[1])}}
 
     # ---- end to end through the C ABI with host buffers ----
