@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--precision", choices=("fp64", "mixed"), default="fp64",
+                    help="fp64: everything in FP64; mixed: FP32 c_ij, lambda_max, d_ij, high-order fluxes")
     return ap.parse_args()
 
 
@@ -150,8 +152,9 @@ def make_workload(args):
         m = meshes.cylinder_m_for_vertices(args.vertices)
         mesh, U0, bs = workloads.cylinder_problem(m)
         w = workloads.Workload(f"cylinder-q1-m{m}", mesh, U0, bs, 2000)
+        prec = "FP64" if args.precision == "fp64" else "mixed FP32/FP64"
         desc = ("2D Mach-3 cylinder channel, Q1, ring-graded O-grid + Cartesian blocks, "
-                f"{mesh.n} vertices, CFL 0.5, FP64, strict local bounds")
+                f"{mesh.n} vertices, CFL 0.5, {prec}, strict local bounds")
     return w, desc
 
 
@@ -319,8 +322,9 @@ def run_ours(args, dist):
     mesh = w.mesh
     S = mesh.dim + 2
     stream = torch.cuda.Stream()
+    precision = binding.EH_PRECISION_MIXED if args.precision == "mixed" else binding.EH_PRECISION_FP64
     solver = binding.Solver(dim=mesh.dim, cfl=w.cfl, gamma=w.gamma, device=dist.local_rank,
-                            stream=stream.cuda_stream)
+                            stream=stream.cuda_stream, precision=precision)
     solver.upload_mesh(mesh, w.bnd_state)
     solver.set_state(w.U0)
     solver.apply_boundary_conditions()
@@ -394,7 +398,7 @@ def run_ours(args, dist):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/f64", "data": "synthetic",
             "config": {"workload": desc, "vertices": mesh.n, "nnz": mesh.nnz, "rk_stages_per_step": 3,
                        "limiter_passes": 2, "parallelism": f"replicas x{dist.world}",
                        "l2": "inputs larger than L2 (edge arrays ~{:.1f} GB per stage)".format(

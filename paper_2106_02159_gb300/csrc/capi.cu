@@ -163,18 +163,18 @@ void flush_profile(eh_ctx *c) {
 
 // One forward-Euler stage on the component-major state Uin, written as
 // out = BC(FE(Uin)) (coef < 0) or out = U0 + coef (BC(FE(Uin)) - U0).
-template <int DIM>
+template <int DIM, typename T>
 void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, const double *U0, double coef, double *out,
                    bool trace) {
   cudaStream_t s = c->stream;
   const MeshView &m = c->mv;
   const Params &p = c->prm;
   const Work &w = c->wk;
-  { ProfScope ps(c, EH_KERNEL_PREP); launch_prep<DIM>(m, p, Uin, w, s); }
-  { ProfScope ps(c, EH_KERNEL_VISC); launch_visc<DIM>(m, p, w, s); }
-  { ProfScope ps(c, EH_KERNEL_LOW); launch_low<DIM>(m, p, w, s); }
+  { ProfScope ps(c, EH_KERNEL_PREP); launch_prep<DIM, T>(m, p, Uin, w, s); }
+  { ProfScope ps(c, EH_KERNEL_VISC); launch_visc<DIM, T>(m, p, w, s); }
+  { ProfScope ps(c, EH_KERNEL_LOW); launch_low<DIM, T>(m, p, w, s); }
   { ProfScope ps(c, EH_KERNEL_TAU); launch_tau(w, stage, dt_given, p.cfl, s); }
-  { ProfScope ps(c, EH_KERNEL_LIM1); launch_lim1<DIM>(m, p, w, s); }
+  { ProfScope ps(c, EH_KERNEL_LIM1); launch_lim1<DIM, T>(m, p, w, s); }
   const double *ucur = w.UL;
   double *lcur = w.la, *lnext = w.lb;
   double *unext = w.Ua;
@@ -196,16 +196,45 @@ void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, con
   }
 }
 
-template <int DIM> void enqueue_step(eh_ctx *c, double dt) {
+template <int DIM, typename T> void enqueue_step(eh_ctx *c, double dt) {
   // w1 = BC(FE(u)); w2 = u + 1/4 (BC(FE(w1)) - u); u <- u + 2/3 (BC(FE(w2)) - u)
-  enqueue_stage<DIM>(c, c->U, 0, dt, nullptr, -1.0, c->W, false);
-  enqueue_stage<DIM>(c, c->W, 1, dt, c->U, 0.25, c->W, false);
-  enqueue_stage<DIM>(c, c->W, 2, dt, c->U, 2.0 / 3.0, c->U, false);
+  enqueue_stage<DIM, T>(c, c->U, 0, dt, nullptr, -1.0, c->W, false);
+  enqueue_stage<DIM, T>(c, c->W, 1, dt, c->U, 0.25, c->W, false);
+  enqueue_stage<DIM, T>(c, c->W, 2, dt, c->U, 2.0 / 3.0, c->U, false);
 }
 
+bool mixed(const eh_ctx *c) { return c->cfg.precision == EH_PRECISION_MIXED; }
+
 void enqueue_step_any(eh_ctx *c, double dt) {
-  if (c->cfg.dim == 2) enqueue_step<2>(c, dt);
-  else enqueue_step<3>(c, dt);
+  if (c->cfg.dim == 2) {
+    if (mixed(c)) enqueue_step<2, float>(c, dt); else enqueue_step<2, double>(c, dt);
+  } else {
+    if (mixed(c)) enqueue_step<3, float>(c, dt); else enqueue_step<3, double>(c, dt);
+  }
+}
+
+void enqueue_stage_any(eh_ctx *c, double tau) {
+  if (c->cfg.dim == 2) {
+    if (mixed(c)) enqueue_stage<2, float>(c, c->U, 0, tau, nullptr, -1.0, c->U, true);
+    else enqueue_stage<2, double>(c, c->U, 0, tau, nullptr, -1.0, c->U, true);
+  } else {
+    if (mixed(c)) enqueue_stage<3, float>(c, c->U, 0, tau, nullptr, -1.0, c->U, true);
+    else enqueue_stage<3, double>(c, c->U, 0, tau, nullptr, -1.0, c->U, true);
+  }
+}
+
+template <int DIM, typename T> void enqueue_cfl(eh_ctx *c) {
+  launch_prep<DIM, T>(c->mv, c->prm, c->U, c->wk, c->stream);
+  launch_visc<DIM, T>(c->mv, c->prm, c->wk, c->stream);
+  launch_low<DIM, T>(c->mv, c->prm, c->wk, c->stream);
+}
+
+void enqueue_cfl_any(eh_ctx *c) {
+  if (c->cfg.dim == 2) {
+    if (mixed(c)) enqueue_cfl<2, float>(c); else enqueue_cfl<2, double>(c);
+  } else {
+    if (mixed(c)) enqueue_cfl<3, float>(c); else enqueue_cfl<3, double>(c);
+  }
 }
 
 eh_status require_ready(eh_ctx *c) {
@@ -252,7 +281,7 @@ eh_status eh_create(const eh_config *cfg, eh_ctx **out) {
   if (!(cfg->gamma > 1.0 && cfg->gamma <= 5.0 / 3.0)) return EH_ERR_INVALID_ARG;
   if (!(cfg->cfl > 0.0 && cfg->cfl <= 1.0)) return EH_ERR_INVALID_ARG;
   if (cfg->limiter_passes < 1 || cfg->limiter_passes > 8) return EH_ERR_INVALID_ARG;
-  if (cfg->precision != EH_PRECISION_FP64) return EH_ERR_INVALID_ARG;
+  if (cfg->precision != EH_PRECISION_FP64 && cfg->precision != EH_PRECISION_MIXED) return EH_ERR_INVALID_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
     cudaGetLastError();
@@ -404,10 +433,31 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   w.nblocks_rows = (int)((n + 127) / 128);
   ALLOC(w.rec, (size_t)n * REC_MAX);
   ALLOC(w.alpha, n);
-  ALLOC(w.w, (size_t)nnz * SP);
-  ALLOC(w.d, nnz);
   ALLOC(w.inc, (size_t)n * SP);
-  ALLOC(w.FH, (size_t)n * SP);
+  float *f_cij = nullptr, *f_cn = nullptr, *f_cinv = nullptr;
+  if (c->cfg.precision == EH_PRECISION_MIXED) {
+    // FP32 c_ij, |c_ij|, 1/|c_ij|, node record, w_ij, d_ij and F^H
+    float *f_rec, *f_w, *f_d, *f_fh;
+    ALLOC(f_cij, (size_t)dim * nnz);
+    ALLOC(f_cn, nnz);
+    ALLOC(f_cinv, nnz);
+    ALLOC(f_rec, (size_t)n * REC_MAX);
+    ALLOC(f_w, (size_t)nnz * SP);
+    ALLOC(f_d, nnz);
+    ALLOC(f_fh, (size_t)n * SP);
+    w.vrec = f_rec;
+    w.vw = f_w;
+    w.vd = f_d;
+    w.vFH = f_fh;
+  } else {
+    ALLOC(w.w, (size_t)nnz * SP);
+    ALLOC(w.d, nnz);
+    ALLOC(w.FH, (size_t)n * SP);
+    w.vrec = w.rec;
+    w.vw = w.w;
+    w.vd = w.d;
+    w.vFH = w.FH;
+  }
   ALLOC(w.bounds, (size_t)n * 4);
   ALLOC(w.UL, (size_t)n * SP);
   ALLOC(w.Ua, (size_t)n * SP);
@@ -444,6 +494,16 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   if (e == cudaSuccess) e = up(d_bkind, bnd_kind, sizeof(int32_t) * n_bnd);
   if (e == cudaSuccess) e = up(d_bnorm, bnd_normal, sizeof(double) * dim * n_bnd);
   if (e == cudaSuccess && bnd_state) e = up(d_bstate, bnd_state, sizeof(double) * S * n_bnd);
+  if (e == cudaSuccess && f_cij) {
+    std::vector<float> tmp((size_t)dim * nnz);
+    for (size_t q = 0; q < tmp.size(); ++q) tmp[q] = (float)cij[q];
+    e = up(f_cij, tmp.data(), sizeof(float) * tmp.size());
+    tmp.resize(nnz);
+    for (int64_t k = 0; e == cudaSuccess && k < nnz; ++k) tmp[k] = (float)cn[k];
+    if (e == cudaSuccess) e = up(f_cn, tmp.data(), sizeof(float) * nnz);
+    for (int64_t k = 0; e == cudaSuccess && k < nnz; ++k) tmp[k] = (float)cinv[k];
+    if (e == cudaSuccess) e = up(f_cinv, tmp.data(), sizeof(float) * nnz);
+  }
   if (e != cudaSuccess) {
     free_mesh(c);
     return fail(c, EH_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(e));
@@ -460,6 +520,9 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   m.inv_mi = d_imi;
   m.relax = d_relax;
   m.isb = d_isb;
+  m.vcij = f_cij ? (const void *)f_cij : (const void *)d_cij;
+  m.vcn = f_cn ? (const void *)f_cn : (const void *)d_cn;
+  m.vcinv = f_cinv ? (const void *)f_cinv : (const void *)d_cinv;
   m.bnd_index = d_bidx;
   m.bnd_kind = d_bkind;
   m.bnd_normal = d_bnorm;
@@ -525,15 +588,7 @@ eh_status eh_cfl_dt(eh_ctx *c, double *dt) {
   if (!dt) return EH_ERR_INVALID_ARG;
   CUDA_TRY(c, cudaSetDevice(c->device));
   if ((st = check_device_error(c))) return st;
-  if (c->cfg.dim == 2) {
-    launch_prep<2>(c->mv, c->prm, c->U, c->wk, c->stream);
-    launch_visc<2>(c->mv, c->prm, c->wk, c->stream);
-    launch_low<2>(c->mv, c->prm, c->wk, c->stream);
-  } else {
-    launch_prep<3>(c->mv, c->prm, c->U, c->wk, c->stream);
-    launch_visc<3>(c->mv, c->prm, c->wk, c->stream);
-    launch_low<3>(c->mv, c->prm, c->wk, c->stream);
-  }
+  enqueue_cfl_any(c);
   launch_tau(c->wk, 0, 0.0, c->prm.cfl, c->stream);
   CUDA_TRY(c, cudaGetLastError());
   if ((st = check_device_error(c))) return st;
@@ -546,8 +601,7 @@ eh_status eh_stage(eh_ctx *c, double tau, double *tau_used) {
   if (st) return st;
   CUDA_TRY(c, cudaSetDevice(c->device));
   if ((st = check_device_error(c))) return st;
-  if (c->cfg.dim == 2) enqueue_stage<2>(c, c->U, 0, tau, nullptr, -1.0, c->U, true);
-  else enqueue_stage<3>(c, c->U, 0, tau, nullptr, -1.0, c->U, true);
+  enqueue_stage_any(c, tau);
   CUDA_TRY(c, cudaGetLastError());
   c->last_stage_traced = true;
   if (tau_used) {
@@ -676,11 +730,33 @@ eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {
     CUDA_TRY(c, cudaMemcpy(host_out, dev, sizeof(double) * len, cudaMemcpyDeviceToHost));
     return EH_OK;
   };
+  // d_ij and F^H live in the viscosity precision (float in mixed mode)
+  auto vcopy = [&](const void *dev, int64_t len, std::vector<double> &dst) -> eh_status {
+    dst.resize(len);
+    if (mixed(c)) {
+      std::vector<float> tmp(len);
+      CUDA_TRY(c, cudaMemcpy(tmp.data(), dev, sizeof(float) * len, cudaMemcpyDeviceToHost));
+      for (int64_t q = 0; q < len; ++q) dst[q] = tmp[q];
+    } else {
+      CUDA_TRY(c, cudaMemcpy(dst.data(), dev, sizeof(double) * len, cudaMemcpyDeviceToHost));
+    }
+    return EH_OK;
+  };
+  std::vector<double> buf;
   switch (what) {
-    case EH_TRACE_D_IJ: return plain(c->wk.d, nnz);
+    case EH_TRACE_D_IJ:
+      if (count != nnz) return fail(c, EH_ERR_INVALID_ARG, "count must be %lld", (long long)nnz);
+      if ((st = vcopy(c->wk.vd, nnz, buf))) return st;
+      std::copy(buf.begin(), buf.end(), host_out);
+      return EH_OK;
     case EH_TRACE_ALPHA: return plain(c->wk.alpha, n);
     case EH_TRACE_U_LOW: return aos_to_soa(c->wk.UL, SP, S);
-    case EH_TRACE_F_HIGH: return aos_to_soa(c->wk.FH, SP, S);
+    case EH_TRACE_F_HIGH:
+      if (count != S * n) return fail(c, EH_ERR_INVALID_ARG, "count must be %lld", (long long)(S * n));
+      if ((st = vcopy(c->wk.vFH, n * SP, buf))) return st;
+      for (int64_t i = 0; i < n; ++i)
+        for (int s = 0; s < S; ++s) host_out[s * n + i] = buf[i * SP + s];
+      return EH_OK;
     case EH_TRACE_BOUNDS: return aos_to_soa(c->wk.bounds, 4, 3);
     case EH_TRACE_L_PASS1:
       if (c->cfg.limiter_passes < 2) return fail(c, EH_ERR_STATE, "L_PASS1 needs limiter_passes >= 2");

@@ -13,6 +13,7 @@
 #include "kernels.cuh"
 
 #include <cmath>
+#include <type_traits>
 
 namespace eh {
 
@@ -75,24 +76,26 @@ __device__ __forceinline__ double pow_gamma_m1(const Params &p, double rho) {
 // Two-rarefaction pressure p_tr >= p* (1 < gamma <= 5/3), then the outer wave
 // speeds of the 1- and 3-waves evaluated at p_tr. Inputs per side: normal
 // velocity, p, a, a p^-z, 1/p.
-__device__ __forceinline__ double lambda_max(const Params &p, double unl, double pl, double al, double azl, double ipl,
-                                             double unr, double pr, double ar, double azr, double ipr) {
-  double num = al + ar - 0.5 * p.gm1 * (unr - unl);
-  num = fmax(num, 0.0);
-  double x = num / (azl + azr);
-  double ptr;
+template <typename T>
+__device__ __forceinline__ T lambda_max(const Params &p, T unl, T pl, T al, T azl, T ipl, T unr, T pr, T ar, T azr,
+                                        T ipr) {
+  T num = al + ar - T(0.5) * T(p.gm1) * (unr - unl);
+  num = fmax(num, T(0));
+  T x = num / (azl + azr);
+  T ptr;
   if (p.gamma75) {
-    double x2 = x * x;
-    double x4 = x2 * x2;
+    T x2 = x * x;
+    T x4 = x2 * x2;
     ptr = x4 * x2 * x;  // x^(2 gamma/(gamma-1)) = x^7
   } else {
-    ptr = pow(x, p.inv_z);
+    ptr = pow(x, T(p.inv_z));
   }
-  double sl = ptr > pl ? sqrt(1.0 + p.kshock * (ptr - pl) * ipl) : 1.0;
-  double sr = ptr > pr ? sqrt(1.0 + p.kshock * (ptr - pr) * ipr) : 1.0;
-  double lam1 = unl - al * sl;
-  double lam3 = unr + ar * sr;
-  return fmax(fmax(-lam1, 0.0), fmax(lam3, 0.0));
+  const T ks = T(p.kshock);
+  T sl = ptr > pl ? sqrt(T(1) + ks * (ptr - pl) * ipl) : T(1);
+  T sr = ptr > pr ? sqrt(T(1) + ks * (ptr - pr) * ipr) : T(1);
+  T lam1 = unl - al * sl;
+  T lam3 = unr + ar * sr;
+  return fmax(fmax(-lam1, T(0)), fmax(lam3, T(0)));
 }
 
 // ---------------------------------------------------------------------------
@@ -210,9 +213,9 @@ __device__ __forceinline__ void flux(const double *u, const double *v, double pr
 // ---------------------------------------------------------------------------
 // k_prep: node records (primitives and derived quantities), once per stage
 // ---------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_prep(MeshView m, Params p, const double *__restrict__ U,
-                                              double *__restrict__ rec, const DevStatus *st) {
+                                              double *__restrict__ rec, T *__restrict__ vrec, const DevStatus *st) {
   constexpr int S = DIM + 2;
   using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -260,76 +263,87 @@ __global__ void __launch_bounds__(TPB) k_prep(MeshView m, Params p, const double
   for (int s = 0; s < S; ++s)
 #pragma unroll
     for (int q = 0; q < DIM; ++q) Rr[R::F + s * DIM + q] = f[s][q];
+  if constexpr (!std::is_same<T, double>::value) {
+    // the same record in the viscosity precision (mixed mode)
+    T *Rv = vrec + (int64_t)i * R::SIZE;
+#pragma unroll
+    for (int q = 0; q < R::F + S * DIM; ++q) Rv[q] = (T)Rr[q];
+  }
 }
 
 // ---------------------------------------------------------------------------
 // k_visc: Algorithm 1 step 1 -- d_ij (j > i, mirrored through the transpose
 // index), the flux differences w_ij and the indicator alpha_i
 // ---------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_visc(MeshView m, Params p, Work w) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
   using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || w.st->err) return;
-  const double *Ri = w.rec + (int64_t)i * R::SIZE;
-  double ui[S], vi[DIM];
+  const T *rec = (const T *)w.vrec;
+  const T *cij = (const T *)m.vcij;
+  const T *cn = (const T *)m.vcn;
+  const T *cinv = (const T *)m.vcinv;
+  T *warr = (T *)w.vw;
+  T *darr = (T *)w.vd;
+  const T *Ri = rec + (int64_t)i * R::SIZE;
+  T ui[S], vi[DIM];
 #pragma unroll
   for (int s = 0; s < S; ++s) ui[s] = Ri[s];
 #pragma unroll
   for (int k = 0; k < DIM; ++k) vi[k] = Ri[R::V + k];
-  const double pi = Ri[R::P], ai = Ri[R::A], azi = Ri[R::AZ], ipi = Ri[R::IP], etai = Ri[R::ETA];
-  const double epsi = Ri[R::EPS];
-  double fi[S][DIM];
+  const T pi = Ri[R::P], ai = Ri[R::A], azi = Ri[R::AZ], ipi = Ri[R::IP], etai = Ri[R::ETA];
+  const T epsi = Ri[R::EPS];
+  T fi[S][DIM];
 #pragma unroll
   for (int s = 0; s < S; ++s)
 #pragma unroll
     for (int q = 0; q < DIM; ++q) fi[s][q] = Ri[R::F + s * DIM + q];
   // eta'(U_i) (Sec. 3.2 indicator)
-  double deta[S];
+  T deta[S];
   {
-    double s_i = -etai / ui[0];
-    double g1 = ui[0] / (p.gm1 * epsi);
-    double v2 = 0.0;
+    const T gm1 = T(p.gm1);
+    T s_i = -etai / ui[0];
+    T g1 = ui[0] / (gm1 * epsi);
+    T v2 = T(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) v2 += vi[k] * vi[k];
-    deta[0] = -s_i - ui[0] / p.gm1 * (v2 / (2.0 * epsi) - p.gamma / ui[0]);
+    deta[0] = -s_i - ui[0] / gm1 * (v2 / (T(2) * epsi) - T(p.gamma) / ui[0]);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) deta[1 + k] = g1 * vi[k];
     deta[S - 1] = -g1;
   }
-  double qi[DIM];
+  T qi[DIM];
 #pragma unroll
   for (int k = 0; k < DIM; ++k) qi[k] = vi[k] * etai;
   const bool bi = m.isb[i] != 0;
-  double N = 0.0, D = 0.0;
+  T N = T(0), D = T(0);
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
   for (int64_t k = k0; k < k1; ++k) {
     const int j = m.col[k];
     if (j == i) continue;
-    const double *Rj = w.rec + (int64_t)j * R::SIZE;
-    double uj[S], vj[DIM], c[DIM];
-#pragma unroll
-    for (int s = 0; s < S; ++s) uj[s] = Rj[s];
+    const T *Rj = rec + (int64_t)j * R::SIZE;
+    T vj[DIM], c[DIM];
 #pragma unroll
     for (int q = 0; q < DIM; ++q) {
       vj[q] = Rj[R::V + q];
-      c[q] = m.cij[(int64_t)q * m.nnz + k];
+      c[q] = cij[(int64_t)q * m.nnz + k];
     }
-    const double pj = Rj[R::P], etaj = Rj[R::ETA];
-    double wv[S];
+    const T pj = Rj[R::P], etaj = Rj[R::ETA];
+    T wv[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      double acc = 0.0;
+      T acc = T(0);
 #pragma unroll
       for (int q = 0; q < DIM; ++q) acc += (Rj[R::F + s * DIM + q] - fi[s][q]) * c[q];
       wv[s] = acc;
     }
-    double *wk = w.w + k * SP;
+    T *wk = warr + k * SP;
 #pragma unroll
     for (int s = 0; s < S; ++s) wk[s] = wv[s];
-    double a_ = 0.0, b_ = 0.0;
+    T a_ = T(0), b_ = T(0);
 #pragma unroll
     for (int q = 0; q < DIM; ++q) a_ += (vj[q] * etaj - qi[q]) * c[q];
 #pragma unroll
@@ -337,39 +351,39 @@ __global__ void __launch_bounds__(TPB) k_visc(MeshView m, Params p, Work w) {
     N += a_ - b_;
     D += fabs(a_) + fabs(b_);
     if (j > i) {
-      const double ci = m.cinv[k];
-      double unl = 0.0, unr = 0.0;
+      const T ci = cinv[k];
+      T unl = T(0), unr = T(0);
 #pragma unroll
       for (int q = 0; q < DIM; ++q) {
         unl += vi[q] * (c[q] * ci);
         unr += vj[q] * (c[q] * ci);
       }
-      double dij = lambda_max(p, unl, pi, ai, azi, ipi, unr, pj, Rj[R::A], Rj[R::AZ], Rj[R::IP]) * m.cn[k];
+      T dij = lambda_max<T>(p, unl, pi, ai, azi, ipi, unr, pj, Rj[R::A], Rj[R::AZ], Rj[R::IP]) * cn[k];
       const int32_t kt = m.tr[k];
       if (bi && m.isb[j]) {
-        const double cit = m.cinv[kt];
-        double unj = 0.0, uni = 0.0;
+        const T cit = cinv[kt];
+        T unj = T(0), uni = T(0);
 #pragma unroll
         for (int q = 0; q < DIM; ++q) {
-          double nq = m.cij[(int64_t)q * m.nnz + kt] * cit;
+          T nq = cij[(int64_t)q * m.nnz + kt] * cit;
           unj += vj[q] * nq;
           uni += vi[q] * nq;
         }
-        double dji = lambda_max(p, unj, pj, Rj[R::A], Rj[R::AZ], Rj[R::IP], uni, pi, ai, azi, ipi) * m.cn[kt];
+        T dji = lambda_max<T>(p, unj, pj, Rj[R::A], Rj[R::AZ], Rj[R::IP], uni, pi, ai, azi, ipi) * cn[kt];
         dij = fmax(dij, dji);
       }
-      w.d[k] = dij;
-      w.d[kt] = dij;
+      darr[k] = dij;
+      darr[kt] = dij;
     }
   }
-  w.alpha[i] = D > 0.0 ? fabs(N) / D : 0.0;
+  w.alpha[i] = D > T(0) ? (double)(fabs(N) / D) : 0.0;
 }
 
 // ---------------------------------------------------------------------------
 // k_low: Algorithm 1 steps 2-3 -- d_ii, CFL bound, low-order increment, local
 // bounds and high-order fluxes
 // ---------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
@@ -384,9 +398,16 @@ __global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
 #pragma unroll
     for (int s = 0; s < S; ++s) ui[s] = Ri[s];
     const double alphai = w.alpha[i];
-    double inc[S], fh[S];
+    T *darr = (T *)w.vd;
+    const T *warr = (const T *)w.vw;
+    // U^L increment and the bounds in FP64; F^H in the viscosity precision T
+    double inc[S];
+    T fh[S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) inc[s] = fh[s] = 0.0;
+    for (int s = 0; s < S; ++s) {
+      inc[s] = 0.0;
+      fh[s] = T(0);
+    }
     // bar-state densities rho_bar = num / den, den = 2 d_ij > 0; the running
     // minimum / maximum is kept as a fraction and compared by cross-multiplication
     double nmin = ui[0], dmin = 1.0, nmax = ui[0], dmax = 1.0;
@@ -400,17 +421,19 @@ __global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
         continue;
       }
       const double *Rj = w.rec + (int64_t)j * R::SIZE;
-      const double dk = w.d[k];
-      const double *wk = w.w + k * SP;
-      const double dH = 0.5 * (alphai + w.alpha[j]) * dk;
+      const T dkT = darr[k];
+      const double dk = (double)dkT;
+      const T *wk = warr + k * SP;
+      const T dH = T(0.5 * (alphai + w.alpha[j])) * dkT;
       double w0 = 0.0;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const double ws = wk[s];
+        const T wsT = wk[s];
+        const double ws = (double)wsT;
         if (s == 0) w0 = ws;
         const double du = Rj[s] - ui[s];
         inc[s] += dk * du - ws;
-        fh[s] += -ws + dH * du;
+        fh[s] += -wsT + dH * (T)du;
       }
       if (dk > 0.0) {
         const double num = dk * (ui[0] + Rj[0]) - w0;
@@ -427,10 +450,10 @@ __global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
       phimin = fmin(phimin, Rj[R::PHI]);
       dsum += dk;
     }
-    w.d[kd] = -dsum;
+    darr[kd] = (T)(-dsum);
     bound = p.cfl * m.mi[i] / (2.0 * dsum);
     double *inci = w.inc + (int64_t)i * SP;
-    double *fhi = w.FH + (int64_t)i * SP;
+    T *fhi = (T *)w.vFH + (int64_t)i * SP;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       inci[s] = inc[s];
@@ -494,7 +517,7 @@ __global__ void __launch_bounds__(1024) k_tau(const double *__restrict__ blockmi
 // ---------------------------------------------------------------------------
 // k_lim1: Algorithm 1 step 4 -- U^L, P_ij and the first line search
 // ---------------------------------------------------------------------------
-template <int DIM>
+template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB) k_lim1(MeshView m, Params p, Work w) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
@@ -505,13 +528,15 @@ __global__ void __launch_bounds__(TPB) k_lim1(MeshView m, Params p, Work w) {
   const double *Ri = w.rec + (int64_t)i * R::SIZE;
   double ui[S], ul[S], fhi[S];
   const double *inci = w.inc + (int64_t)i * SP;
-  const double *FHi = w.FH + (int64_t)i * SP;
+  const T *FHarr = (const T *)w.vFH;
+  const T *darr = (const T *)w.vd;
+  const T *FHi = FHarr + (int64_t)i * SP;
   const double tm = tau * m.inv_mi[i];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     ui[s] = Ri[s];
     ul[s] = ui[s] + tm * inci[s];
-    fhi[s] = FHi[s];
+    fhi[s] = (double)FHi[s];
   }
   double *ULi = w.UL + (int64_t)i * SP;
 #pragma unroll
@@ -532,14 +557,14 @@ __global__ void __launch_bounds__(TPB) k_lim1(MeshView m, Params p, Work w) {
       continue;
     }
     const double *Rj = w.rec + (int64_t)j * R::SIZE;
-    const double *FHj = w.FH + (int64_t)j * SP;
-    const double dk = w.d[k];
+    const T *FHj = FHarr + (int64_t)j * SP;
+    const double dk = (double)darr[k];
     const double dH = 0.5 * (alphai + w.alpha[j]) * dk;
     const double b = m.beta[k], bt = m.betat[k];
     double P[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      P[s] = coef * (-b * FHj[s] + bt * fhi[s] + (dH - dk) * (Rj[s] - ui[s]));
+      P[s] = coef * (-b * (double)FHj[s] + bt * fhi[s] + (dH - dk) * (Rj[s] - ui[s]));
       Pk[s] = P[s];
     }
     w.la[k] = line_search<DIM>(p, ul, P, rmin, rmax, phimin, phimin5);
@@ -690,20 +715,21 @@ template <int DIM> __global__ void k_count_not_admissible(int n, const double *U
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int DIM> void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, cudaStream_t s) {
-  k_prep<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, U, w.rec, w.st);
+template <int DIM, typename T>
+void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, cudaStream_t s) {
+  k_prep<DIM, T><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, U, w.rec, (T *)w.vrec, w.st);
 }
-template <int DIM> void launch_visc(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
-  k_visc<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
+template <int DIM, typename T> void launch_visc(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
+  k_visc<DIM, T><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
 }
-template <int DIM> void launch_low(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
-  k_low<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
+template <int DIM, typename T> void launch_low(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
+  k_low<DIM, T><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
 }
 void launch_tau(const Work &w, int stage, double dt_given, double cfl, cudaStream_t s) {
   k_tau<<<1, 1024, 0, s>>>(w.blockmin, w.nblocks_rows, w.st, stage, dt_given, cfl);
 }
-template <int DIM> void launch_lim1(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
-  k_lim1<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
+template <int DIM, typename T> void launch_lim1(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
+  k_lim1<DIM, T><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
 }
 template <int DIM>
 void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
@@ -722,11 +748,18 @@ template <int DIM> void launch_count_not_admissible(int n, const double *U, DevS
   k_count_not_admissible<DIM><<<nblocks(n, 256), 256, 0, s>>>(n, U, st);
 }
 
+#define EH_INSTANTIATE_T(DIM, T)                                                                                     \
+  template void launch_prep<DIM, T>(const MeshView &, const Params &, const double *, const Work &, cudaStream_t);    \
+  template void launch_visc<DIM, T>(const MeshView &, const Params &, const Work &, cudaStream_t);                    \
+  template void launch_low<DIM, T>(const MeshView &, const Params &, const Work &, cudaStream_t);                     \
+  template void launch_lim1<DIM, T>(const MeshView &, const Params &, const Work &, cudaStream_t);
+
+EH_INSTANTIATE_T(2, double)
+EH_INSTANTIATE_T(3, double)
+EH_INSTANTIATE_T(2, float)
+EH_INSTANTIATE_T(3, float)
+
 #define EH_INSTANTIATE(DIM)                                                                                          \
-  template void launch_prep<DIM>(const MeshView &, const Params &, const double *, const Work &, cudaStream_t);       \
-  template void launch_visc<DIM>(const MeshView &, const Params &, const Work &, cudaStream_t);                       \
-  template void launch_low<DIM>(const MeshView &, const Params &, const Work &, cudaStream_t);                        \
-  template void launch_lim1<DIM>(const MeshView &, const Params &, const Work &, cudaStream_t);                       \
   template void launch_pass<DIM>(const MeshView &, const Params &, const Work &, const double *, double *,            \
                                  const double *, double *, double *, cudaStream_t);                                   \
   template void launch_final<DIM>(const MeshView &, const Params &, const Work &, const double *, const double *,     \

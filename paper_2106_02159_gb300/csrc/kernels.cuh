@@ -56,6 +56,11 @@ struct MeshView {
   const double *inv_mi;
   const double *relax;       // r_i (0 when the bounds are strict)
   const unsigned char *isb;  // 1 for boundary nodes
+  // arrays in the precision of the viscosity / flux part (double in FP64 mode,
+  // float in mixed mode): c_ij [dim][nnz], |c_ij|, 1/|c_ij|
+  const void *vcij;
+  const void *vcn;
+  const void *vcinv;
   const int32_t *bnd_index;  // per node: index into the boundary arrays, -1 inside
   const int32_t *bnd_kind;   // [n_bnd]
   const double *bnd_normal;  // [dim][n_bnd]
@@ -89,6 +94,12 @@ struct Work {
   double *blockmin;
   int nblocks_rows;
   DevStatus *st;
+  // viscosity / flux precision arrays (aliases of rec, w, d, FH in FP64 mode;
+  // float arrays in mixed mode)
+  void *vrec;      // [n][Rec::SIZE] node record in that precision
+  void *vw;        // [nnz][SP]
+  void *vd;        // [nnz]
+  void *vFH;       // [n][SP]
 };
 
 struct TraceOut {
@@ -96,12 +107,14 @@ struct TraceOut {
   double *Upass1;  // [n][SP] or null (written by the last limiting pass when passes == 1)
 };
 
-// Launchers (all asynchronous on 'stream').
-template <int DIM> void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, cudaStream_t s);
-template <int DIM> void launch_visc(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
-template <int DIM> void launch_low(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
+// Launchers (all asynchronous on 'stream'). T is the precision of the
+// viscosity / high-order-flux part: double (FP64 mode) or float (mixed mode).
+template <int DIM, typename T>
+void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, cudaStream_t s);
+template <int DIM, typename T> void launch_visc(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
+template <int DIM, typename T> void launch_low(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
 void launch_tau(const Work &w, int stage, double dt_given, double cfl, cudaStream_t s);
-template <int DIM> void launch_lim1(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
+template <int DIM, typename T> void launch_lim1(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
 template <int DIM>
 void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
                  double *lout, double *lsym_trace, cudaStream_t s);
