@@ -51,7 +51,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("cylinder", "vortex"), default="cylinder")
+    ap.add_argument("--workload", choices=("cylinder", "vortex", "batch", "serve", "cylinder3d"),
+                    default="cylinder")
+    ap.add_argument("--requests", type=int, default=48, help="serve workload: requests in the trace")
+    ap.add_argument("--instances", type=int, default=256, help="batch workload: number of instances")
     ap.add_argument("--vertices", type=int, default=4_000_000)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--profile-steps", type=int, default=3)
@@ -416,12 +419,212 @@ def run_ours(args, dist):
     solver.close()
 
 
+def run_batch(args, dist):
+    """Batched sweep: independent Q1 cylinder instances (m log-uniform in
+    [8, 256], i.e. 32x8 to 1024x256 cells; Mach uniform in [1.5, 4]; seed 4) in
+    one context -- every kernel launch covers all instances, each with its own
+    CFL step -- against a per-instance launch loop of the plain FP64 path."""
+    import torch
+    from paper_2106_02159_gb300 import binding, meshes, workloads
+    torch.cuda.set_device(dist.local_rank)
+    binding.build()
+    sweep = workloads.batch_sweep(args.instances)
+    inst = [workloads.cylinder_instance(m, mach) for m, mach in sweep]
+    mesh, off, bs = meshes.concatenate([x[0] for x in inst], [x[2] for x in inst])
+    U0 = np.concatenate([x[1] for x in inst], axis=1)
+    precision = binding.EH_PRECISION_MIXED if args.precision == "mixed" else binding.EH_PRECISION_FP64
+    stream = torch.cuda.Stream()
+    s = binding.Solver(dim=2, precision=precision, device=dist.local_rank, stream=stream.cuda_stream)
+    s.upload_mesh(mesh, bs)
+    s.set_instances(off)
+    s.set_state(U0)
+    s.apply_boundary_conditions()
+    chosen = s.autotune(1)
+    s.run(args.warmup)
+    s.synchronize()
+    clocks = Clocks(dist.local_rank)
+    dist.barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.run(args.steps)
+    e1.record(stream)
+    stream.synchronize()
+    clk = clocks.stop()
+    s.synchronize()
+    ms = dist.max(e0.elapsed_time(e1))
+    value = mesh.n * 3 * args.steps * dist.world / (ms * 1e-3)
+    diag = s.diagnostics()
+    s.close()
+    # the baseline: a loop over instances, one plain FP64 context each
+    loop = []
+    for m, u, b in inst:
+        q = binding.Solver(dim=2, device=dist.local_rank, stream=stream.cuda_stream)
+        q.upload_mesh(m, b)
+        q.set_state(u)
+        q.apply_boundary_conditions()
+        loop.append(q)
+    for q in loop:
+        q.run(args.warmup)
+    torch.cuda.synchronize()
+    loop_steps = max(1, args.steps // 4)
+    e0.record(stream)
+    for _ in range(loop_steps):
+        for q in loop:
+            q.step(sync=False)
+    e1.record(stream)
+    stream.synchronize()
+    loop_ms = dist.max(e0.elapsed_time(e1))
+    loop_value = mesh.n * 3 * loop_steps * dist.world / (loop_ms * 1e-3)
+    for q in loop:
+        q.close()
+    if dist.rank == 0:
+        cells = [4 * m * m for m, _ in sweep]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/f64", "data": "synthetic",
+            "config": {"workload": f"batched sweep: {len(inst)} independent Q1 cylinder instances, n_y = m cells "
+                                   f"(m log-uniform in [8, 256]), Mach uniform in [1.5, 4], seed 4, CFL 0.5, "
+                                   f"{args.precision}, one launch per kernel for all instances (CUDA graph)",
+                       "instances": len(inst), "vertices": mesh.n, "nnz": mesh.nnz,
+                       "cells_min_max": [min(cells), max(cells)], "block_sizes": chosen,
+                       "invariant_violations": diag["not_admissible"]},
+            "clocks": clk,
+            "per_instance_loop": {"value": loop_value, "unit": UNIT, "steps": loop_steps,
+                                  "ms_per_step": loop_ms / loop_steps, "dtype": "f64",
+                                  "what": "one plain FP64 context per instance, eh_step launched instance after instance"},
+            "speedup_vs_loop": value / loop_value,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, dist):
+    """Served stream: a seeded Poisson trace (mean 50 requests/s) of 2D Euler
+    solves on P1/Q1 cylinder meshes (vertices log-uniform in [1e4, 2.5e5],
+    Mach uniform in [1.5, 4]) to t_final = 0.25, served with continuous
+    batching in mixed precision; against the same requests solved one after
+    another with the plain FP64 path (their service times replayed against the
+    same arrivals)."""
+    import torch
+    from paper_2106_02159_gb300 import binding, serve
+    torch.cuda.set_device(dist.local_rank)
+    binding.build()
+    if dist.rank != 0:
+        return
+    reqs = serve.poisson_trace(args.requests, rate=50.0, seed=5, n_range=(1e4, 2.5e5), t_final=0.25)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
+    precision = binding.EH_PRECISION_MIXED if args.precision == "mixed" else binding.EH_PRECISION_FP64
+    # warm the library and the caches once
+    serve.solve_alone(reqs[0], precision)
+    t0 = time.perf_counter()
+    results = serve.SolveServer(budget, precision=precision, device=dist.local_rank).run(reqs)
+    makespan = time.perf_counter() - t0
+    tts = np.array([r.time_to_solution for r in results])
+    dof = sum(r.n * 3 * r.steps for r in results)
+    # sequential plain FP64 baseline: each solve alone, then queueing replayed
+    service = []
+    for r in reqs:
+        a = time.perf_counter()
+        _, steps = serve.solve_alone(r, binding.EH_PRECISION_FP64)
+        service.append((time.perf_counter() - a, steps))
+    finish, seq_tts = 0.0, []
+    for r, (svc, _) in zip(reqs, service):
+        finish = max(finish, r.arrival) + svc
+        seq_tts.append(finish - r.arrival)
+    seq_tts = np.array(seq_tts)
+    seq_dof = sum(r.mesh.n * 3 * st for r, (_, st) in zip(reqs, service))
+    line = {
+        "metric": "p50/p99 time-to-solution (served)", "value": float(np.percentile(tts, 99)), "unit": "s",
+        "p50_s": float(np.percentile(tts, 50)), "p99_s": float(np.percentile(tts, 99)),
+        "n_gpus": 1, "steps": int(sum(r.steps for r in results)), "warmup": 1, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/f64",
+        "data": "synthetic",
+        "aggregate": {"value": dof / makespan, "unit": UNIT, "makespan_s": makespan},
+        "load": {"offered_requests_per_s": 50.0, "served_requests_per_s": len(results) / makespan},
+        "config": {"workload": f"served stream: {len(reqs)} requests, Poisson arrivals (mean 50/s, seed 5), "
+                               "P1/Q1 cylinder meshes, vertices log-uniform in [1e4, 2.5e5], Mach uniform in "
+                               "[1.5, 4], t_final 0.25, continuous batching (admission by free device memory, "
+                               "one context and stream per request, states resident)",
+                   "hbm_budget_bytes": budget, "precision": args.precision},
+        "sequential_plain_fp64": {"p50_s": float(np.percentile(seq_tts, 50)), "p99_s": float(np.percentile(seq_tts, 99)),
+                                  "aggregate": seq_dof / sum(x for x, _ in service), "unit": UNIT},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_cylinder3d(args, dist):
+    """3D Mach-3 cylinder: the 2D cross-section (~94k vertices) extruded over
+    z in [0, 2] with periodic layers to ~30M vertices (27-point rows), inflow
+    rho = 1.4, u = (3, 0, 0), p = 1, slip on walls and cylinder; the same
+    steps in FP64 and in mixed precision, with the L1 error per field of the
+    mixed run against the FP64 run."""
+    import torch
+    from paper_2106_02159_gb300 import binding, meshes, workloads
+    torch.cuda.set_device(dist.local_rank)
+    binding.build()
+    target = max(args.vertices, 1) if args.vertices != 4_000_000 else 30_000_000
+    m2 = meshes.cylinder_m_for_vertices(94_000)
+    base = meshes.cylinder_channel_q1(m2)
+    nz = max(3, int(round(target / base.n)))
+    mesh = meshes.extruded_q1(base, nz, 2.0)
+    U0 = workloads.uniform_state(mesh, 1.4, (3.0, 0.0, 0.0), 1.0)
+    bs = np.ascontiguousarray(U0[:, mesh.bnd_node])
+    out = {}
+    for prec in ("fp64", "mixed"):
+        stream = torch.cuda.Stream()
+        p = binding.EH_PRECISION_MIXED if prec == "mixed" else binding.EH_PRECISION_FP64
+        s = binding.Solver(dim=3, precision=p, device=dist.local_rank, stream=stream.cuda_stream)
+        s.upload_mesh(mesh, bs)
+        s.set_state(U0)
+        s.apply_boundary_conditions()
+        s.run(args.warmup)
+        s.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.run(args.steps)
+        e1.record(stream)
+        stream.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.synchronize()
+        out[prec] = dict(value=mesh.n * 3 * args.steps / (ms * 1e-3), ms_per_step=ms / args.steps,
+                         U=s.get_state(), violations=s.diagnostics()["not_admissible"])
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    Uf, Um = out["fp64"]["U"], out["mixed"]["U"]
+    names = ("rho", "m_x", "m_y", "m_z", "E")
+    norms = np.abs(Uf).sum(1)
+    err = np.abs(Um - Uf).sum(1) / np.maximum(norms, 1e-3 * norms.max())
+    if dist.rank == 0:
+        line = {"metric": METRIC, "value": out["fp64"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": out["fp64"]["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"3D Mach-3 cylinder, Q1 hexes: the {base.n}-vertex 2D cross-section "
+                                       f"extruded over z in [0,2] with {nz} periodic layers, {mesh.n} vertices, "
+                                       f"27-point rows, CFL 0.5, strict local bounds",
+                           "vertices": mesh.n, "nnz": mesh.nnz},
+                "mixed": {"value": out["mixed"]["value"], "unit": UNIT, "ms_per_step": out["mixed"]["ms_per_step"],
+                          "speedup_vs_fp64": out["mixed"]["value"] / out["fp64"]["value"],
+                          "l1_rel_error_vs_fp64_run": dict(zip(names, err.tolist())),
+                          "after_steps": args.warmup + args.steps},
+                "invariant_violations": {"fp64": out["fp64"]["violations"], "mixed": out["mixed"]["violations"]}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     dist = Dist()
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.workload == "batch":
+            run_batch(args, dist)
+        elif args.workload == "serve":
+            run_serve(args, dist)
+        elif args.workload == "cylinder3d":
+            run_cylinder3d(args, dist)
         else:
             run_ours(args, dist)
     finally:

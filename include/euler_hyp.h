@@ -199,6 +199,32 @@ eh_status eh_cfl_dt_noalloc(int32_t dim, double gamma, double cfl, int32_t n, in
                             const int32_t *col, const double *cij, const double *mi,
                             const unsigned char *is_boundary, const double *U, double *dt_out, void *stream);
 
+/* Independent instances in one context (batched solves). After
+ * eh_upload_mesh of a block-diagonal mesh -- instance k owns the rows
+ * [row_offset[k], row_offset[k+1]) and no CSR entry couples two instances --
+ * this declares the split. Every step then advances all instances in the same
+ * kernel launches, each with its own CFL step (eq. dtCfl per instance), its
+ * own simulated time and, if t_final (host, ninst values, or NULL) is given, a
+ * last step shortened to land on t_final[k]; finished instances stay frozen
+ * (tau = 0). Resets the instance times. Errors: EH_ERR_INVALID_ARG for bad
+ * offsets, EH_ERR_BAD_MESH if an entry couples two instances. */
+eh_status eh_set_instances(eh_ctx *ctx, int32_t ninst, const int64_t *row_offset, const double *t_final);
+
+/* Per-instance simulated time t[ninst], last tau[ninst] and CFL bounds of the
+ * last step's three stages stage_bound[3][ninst] (host arrays; any may be
+ * NULL). Synchronises. */
+eh_status eh_get_instances(eh_ctx *ctx, double *t, double *last_dt, double *stage_bound);
+
+/* Block-size autotuner: runs 'steps_per_candidate' SSPRK(3,3) steps with 64,
+ * 128 and 256 rows per block, times every kernel with CUDA events and keeps
+ * the fastest block size per kernel kind. The state and the instance times
+ * are restored afterwards. chosen (may be NULL) receives EH_KERNEL_COUNT
+ * block sizes. */
+eh_status eh_autotune(eh_ctx *ctx, int32_t steps_per_candidate, int32_t *chosen);
+
+/* Current block size of every kernel kind (EH_KERNEL_COUNT values). */
+eh_status eh_get_block_sizes(const eh_ctx *ctx, int32_t *tpb);
+
 /* Number of kernel launches one eh_step issues (for accounting). */
 int32_t eh_launches_per_step(const eh_ctx *ctx);
 

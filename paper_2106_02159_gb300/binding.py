@@ -33,7 +33,8 @@ EH_PRECISION_FP64, EH_PRECISION_MIXED = 0, 1
 EXPORTS = ("eh_config_default", "eh_create", "eh_upload_mesh", "eh_set_state", "eh_get_state",
            "eh_apply_boundary_conditions", "eh_cfl_dt", "eh_stage", "eh_step", "eh_run", "eh_synchronize",
            "eh_get_diagnostics", "eh_trace", "eh_profile_enable", "eh_profile_read", "eh_launches_per_step",
-           "eh_last_error", "eh_status_string", "eh_destroy", "eh_cfl_dt_noalloc")
+           "eh_last_error", "eh_status_string", "eh_destroy", "eh_cfl_dt_noalloc", "eh_set_instances",
+           "eh_get_instances", "eh_autotune", "eh_get_block_sizes")
 CFL_NOALLOC_MAX_ROWS = 1 << 23
 KERNEL_NAMES = ("prep", "visc", "low", "tau", "lim1", "pass", "final")
 
@@ -103,6 +104,10 @@ def load(path: str | None = None):
     lib.eh_status_string.restype = ctypes.c_char_p
     lib.eh_destroy.argtypes = [vp]
     lib.eh_destroy.restype = None
+    lib.eh_set_instances.argtypes = [vp, i32, vp, vp]
+    lib.eh_get_instances.argtypes = [vp, vp, vp, vp]
+    lib.eh_autotune.argtypes = [vp, i32, vp]
+    lib.eh_get_block_sizes.argtypes = [vp, vp]
     lib.eh_cfl_dt_noalloc.argtypes = [i32, ctypes.c_double, ctypes.c_double, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("eh_config_default", "eh_destroy", "eh_launches_per_step", "eh_last_error",
@@ -263,6 +268,29 @@ class Solver:
             self._check(self.lib.eh_profile_read(self.ctx, k, ctypes.byref(ms), ctypes.byref(cnt)), "eh_profile_read")
             out[name] = (ms.value, cnt.value)
         return out
+
+    def set_instances(self, row_offset, t_final=None):
+        """Declare the uploaded (block-diagonal) mesh as independent instances."""
+        off = _arr(row_offset, np.int64)
+        tf = None if t_final is None else _arr(t_final, np.float64)
+        self._check(self.lib.eh_set_instances(self.ctx, off.size - 1, _p(off), _p(tf)), "eh_set_instances")
+        self.ninst = off.size - 1
+
+    def instances(self) -> dict:
+        k = getattr(self, "ninst", 1)
+        t, dt, b = np.empty(k), np.empty(k), np.empty((3, k))
+        self._check(self.lib.eh_get_instances(self.ctx, _p(t), _p(dt), _p(b)), "eh_get_instances")
+        return dict(t=t, last_dt=dt, stage_bound=b)
+
+    def autotune(self, steps_per_candidate=2) -> dict:
+        chosen = np.zeros(len(KERNEL_NAMES), dtype=np.int32)
+        self._check(self.lib.eh_autotune(self.ctx, int(steps_per_candidate), _p(chosen)), "eh_autotune")
+        return dict(zip(KERNEL_NAMES, chosen.tolist()))
+
+    def block_sizes(self) -> dict:
+        out = np.zeros(len(KERNEL_NAMES), dtype=np.int32)
+        self._check(self.lib.eh_get_block_sizes(self.ctx, _p(out)), "eh_get_block_sizes")
+        return dict(zip(KERNEL_NAMES, out.tolist()))
 
     def launches_per_step(self) -> int:
         return int(self.lib.eh_launches_per_step(self.ctx))

@@ -50,6 +50,12 @@ struct eh_ctx {
   std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_marks;  // kernel, (start, stop) event indices
   double prof_ms[EH_KERNEL_COUNT] = {0};
   int64_t prof_count[EH_KERNEL_COUNT] = {0};
+  // block size (rows per block) of every kernel kind
+  int tpb[EH_KERNEL_COUNT] = {128, 128, 128, 1024, 128, 128, 128};
+  // independent instances
+  int ninst = 1;
+  std::vector<void *> inst_allocs;
+  double *Usave = nullptr;  // state saved while autotuning
 };
 
 namespace {
@@ -91,11 +97,17 @@ template <typename T> eh_status dalloc(eh_ctx *c, T **p, size_t count) {
   return EH_OK;
 }
 
+void free_instances(eh_ctx *c) {
+  for (void *q : c->inst_allocs) cudaFree(q);
+  c->inst_allocs.clear();
+}
+
 void free_mesh(eh_ctx *c) {
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
+  free_instances(c);
   for (void *q : c->allocs) cudaFree(q);
   c->allocs.clear();
   c->mv = MeshView{};
@@ -170,18 +182,20 @@ void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, con
   const MeshView &m = c->mv;
   const Params &p = c->prm;
   const Work &w = c->wk;
-  { ProfScope ps(c, EH_KERNEL_PREP); launch_prep<DIM, T>(m, p, Uin, w, s); }
-  { ProfScope ps(c, EH_KERNEL_VISC); launch_visc<DIM, T>(m, p, w, s); }
-  { ProfScope ps(c, EH_KERNEL_LOW); launch_low<DIM, T>(m, p, w, s); }
-  { ProfScope ps(c, EH_KERNEL_TAU); launch_tau(w, stage, dt_given, p.cfl, s); }
-  { ProfScope ps(c, EH_KERNEL_LIM1); launch_lim1<DIM, T>(m, p, w, s); }
+  const int *tpb = c->tpb;
+  { ProfScope ps(c, EH_KERNEL_PREP); launch_prep<DIM, T>(m, p, Uin, w, tpb[EH_KERNEL_PREP], s); }
+  { ProfScope ps(c, EH_KERNEL_VISC); launch_visc<DIM, T>(m, p, w, tpb[EH_KERNEL_VISC], s); }
+  { ProfScope ps(c, EH_KERNEL_LOW); launch_low<DIM, T>(m, p, w, tpb[EH_KERNEL_LOW], s); }
+  { ProfScope ps(c, EH_KERNEL_TAU); launch_tau(m, w, stage, dt_given, p.cfl, !trace, s); }
+  { ProfScope ps(c, EH_KERNEL_LIM1); launch_lim1<DIM, T>(m, p, w, tpb[EH_KERNEL_LIM1], s); }
   const double *ucur = w.UL;
   double *lcur = w.la, *lnext = w.lb;
   double *unext = w.Ua;
   for (int pass = 1; pass < c->cfg.limiter_passes; ++pass) {
     {
       ProfScope ps(c, EH_KERNEL_PASS);
-      launch_pass<DIM>(m, p, w, ucur, unext, lcur, lnext, (trace && pass == 1) ? c->trace_lsym : nullptr, s);
+      launch_pass<DIM>(m, p, w, ucur, unext, lcur, lnext, (trace && pass == 1) ? c->trace_lsym : nullptr,
+                       tpb[EH_KERNEL_PASS], s);
     }
     if (trace && pass == 1) {
       cudaMemcpyAsync(c->trace_upass, unext, sizeof(double) * (size_t)c->n * SP_of(c), cudaMemcpyDeviceToDevice, s);
@@ -192,7 +206,7 @@ void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, con
   }
   {
     ProfScope ps(c, EH_KERNEL_FINAL);
-    launch_final<DIM>(m, p, w, ucur, lcur, U0, coef, out, trace ? c->trace_pre : nullptr, s);
+    launch_final<DIM>(m, p, w, ucur, lcur, U0, coef, out, trace ? c->trace_pre : nullptr, tpb[EH_KERNEL_FINAL], s);
   }
 }
 
@@ -224,9 +238,63 @@ void enqueue_stage_any(eh_ctx *c, double tau) {
 }
 
 template <int DIM, typename T> void enqueue_cfl(eh_ctx *c) {
-  launch_prep<DIM, T>(c->mv, c->prm, c->U, c->wk, c->stream);
-  launch_visc<DIM, T>(c->mv, c->prm, c->wk, c->stream);
-  launch_low<DIM, T>(c->mv, c->prm, c->wk, c->stream);
+  launch_prep<DIM, T>(c->mv, c->prm, c->U, c->wk, c->tpb[EH_KERNEL_PREP], c->stream);
+  launch_visc<DIM, T>(c->mv, c->prm, c->wk, c->tpb[EH_KERNEL_VISC], c->stream);
+  launch_low<DIM, T>(c->mv, c->prm, c->wk, c->tpb[EH_KERNEL_LOW], c->stream);
+}
+
+// (Re)allocates the per-instance arrays for 'ninst' instances with row offsets
+// 'off' (host, ninst+1 entries) and end times 'tf' (host, or NULL = none).
+eh_status setup_instances(eh_ctx *c, int ninst, const int64_t *off, const double *tf) {
+  free_instances(c);
+  auto ialloc = [&](void **p, size_t bytes) -> eh_status {
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 8));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, EH_ERR_OOM, "cudaMalloc of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    c->inst_allocs.push_back(*p);
+    return EH_OK;
+  };
+  eh_status st;
+  void *p_off, *p_tau, *p_bound, *p_t, *p_tf, *p_bits, *p_inst = nullptr;
+  if ((st = ialloc(&p_off, sizeof(int64_t) * (ninst + 1)))) return st;
+  if ((st = ialloc(&p_tau, sizeof(double) * ninst))) return st;
+  if ((st = ialloc(&p_bound, sizeof(double) * 3 * ninst))) return st;
+  if ((st = ialloc(&p_t, sizeof(double) * ninst))) return st;
+  if ((st = ialloc(&p_tf, sizeof(double) * ninst))) return st;
+  if ((st = ialloc(&p_bits, sizeof(unsigned long long) * ninst))) return st;
+  std::vector<unsigned long long> inf_bits(ninst, 0x7FF0000000000000ull);
+  CUDA_TRY(c, cudaMemcpy(p_bits, inf_bits.data(), sizeof(unsigned long long) * ninst, cudaMemcpyHostToDevice));
+  std::vector<double> tfinal(ninst, INFINITY);
+  if (tf)
+    for (int k = 0; k < ninst; ++k) tfinal[k] = tf[k] > 0.0 ? tf[k] : INFINITY;
+  CUDA_TRY(c, cudaMemcpy(p_off, off, sizeof(int64_t) * (ninst + 1), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemset(p_tau, 0, sizeof(double) * ninst));
+  CUDA_TRY(c, cudaMemset(p_bound, 0, sizeof(double) * 3 * ninst));
+  CUDA_TRY(c, cudaMemset(p_t, 0, sizeof(double) * ninst));
+  CUDA_TRY(c, cudaMemcpy(p_tf, tfinal.data(), sizeof(double) * ninst, cudaMemcpyHostToDevice));
+  if (ninst > 1) {
+    std::vector<int32_t> inst(c->n);
+    for (int k = 0; k < ninst; ++k)
+      for (int64_t i = off[k]; i < off[k + 1]; ++i) inst[i] = k;
+    if ((st = ialloc(&p_inst, sizeof(int32_t) * c->n))) return st;
+    CUDA_TRY(c, cudaMemcpy(p_inst, inst.data(), sizeof(int32_t) * c->n, cudaMemcpyHostToDevice));
+  }
+  c->ninst = ninst;
+  c->mv.ninst = ninst;
+  c->mv.inst = (const int32_t *)p_inst;
+  c->mv.inst_row_off = (const int64_t *)p_off;
+  c->wk.tau_inst = (double *)p_tau;
+  c->wk.bound_inst = (double *)p_bound;
+  c->wk.t_inst = (double *)p_t;
+  c->wk.tfinal_inst = (double *)p_tf;
+  c->wk.bound_bits = (unsigned long long *)p_bits;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return EH_OK;
 }
 
 void enqueue_cfl_any(eh_ctx *c) {
@@ -430,7 +498,6 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   ALLOC(d_bstate, (size_t)S * n_bnd);
   const int SP = SP_of(c);
   Work &w = c->wk;
-  w.nblocks_rows = (int)((n + 127) / 128);
   ALLOC(w.rec, (size_t)n * REC_MAX);
   ALLOC(w.alpha, n);
   ALLOC(w.inc, (size_t)n * SP);
@@ -465,7 +532,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   ALLOC(w.P, (size_t)nnz * SP);
   ALLOC(w.la, nnz);
   ALLOC(w.lb, nnz);
-  ALLOC(w.blockmin, w.nblocks_rows);
+  ALLOC(c->Usave, (size_t)S * n);
   ALLOC(c->U, (size_t)S * n);
   ALLOC(c->W, (size_t)S * n);
   ALLOC(c->trace_lsym, nnz);
@@ -530,6 +597,11 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   c->n = n;
   c->nnz = nnz;
   c->n_bnd = n_bnd;
+  const int64_t one[2] = {0, (int64_t)n};
+  if ((st = setup_instances(c, 1, one, nullptr)) != EH_OK) {
+    free_mesh(c);
+    return st;
+  }
   c->have_mesh = true;
   c->t = 0.0;
   c->steps = 0;
@@ -589,7 +661,7 @@ eh_status eh_cfl_dt(eh_ctx *c, double *dt) {
   CUDA_TRY(c, cudaSetDevice(c->device));
   if ((st = check_device_error(c))) return st;
   enqueue_cfl_any(c);
-  launch_tau(c->wk, 0, 0.0, c->prm.cfl, c->stream);
+  launch_tau(c->mv, c->wk, 0, 0.0, c->prm.cfl, false, c->stream);
   CUDA_TRY(c, cudaGetLastError());
   if ((st = check_device_error(c))) return st;
   *dt = c->st_host->stage_bound[0];
@@ -681,6 +753,88 @@ eh_status eh_get_diagnostics(eh_ctx *c, eh_diagnostics *out) {
   return st;
 }
 
+eh_status eh_set_instances(eh_ctx *c, int32_t ninst, const int64_t *row_offset, const double *t_final) {
+  if (!c || ninst < 1 || !row_offset) return EH_ERR_INVALID_ARG;
+  if (!c->have_mesh) return fail(c, EH_ERR_STATE, "no mesh uploaded");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (row_offset[0] != 0 || row_offset[ninst] != c->n)
+    return fail(c, EH_ERR_INVALID_ARG, "instance offsets must start at 0 and end at n");
+  for (int k = 0; k < ninst; ++k)
+    if (row_offset[k + 1] <= row_offset[k]) return fail(c, EH_ERR_INVALID_ARG, "instance %d is empty", k);
+  // no CSR entry may couple two instances
+  std::vector<int64_t> rp(c->n + 1);
+  std::vector<int32_t> col(c->nnz);
+  CUDA_TRY(c, cudaMemcpy(rp.data(), c->mv.row_ptr, sizeof(int64_t) * (c->n + 1), cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(col.data(), c->mv.col, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < ninst; ++k)
+    for (int64_t i = row_offset[k]; i < row_offset[k + 1]; ++i)
+      for (int64_t q = rp[i]; q < rp[i + 1]; ++q)
+        if (col[q] < row_offset[k] || col[q] >= row_offset[k + 1])
+          return fail(c, EH_ERR_BAD_MESH, "row %lld couples instances", (long long)i);
+  return setup_instances(c, ninst, row_offset, t_final);
+}
+
+eh_status eh_get_instances(eh_ctx *c, double *t, double *last_dt, double *stage_bound) {
+  if (!c) return EH_ERR_INVALID_ARG;
+  if (!c->have_mesh) return fail(c, EH_ERR_STATE, "no mesh uploaded");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const size_t b = sizeof(double) * c->ninst;
+  if (t) CUDA_TRY(c, cudaMemcpy(t, c->wk.t_inst, b, cudaMemcpyDeviceToHost));
+  if (last_dt) CUDA_TRY(c, cudaMemcpy(last_dt, c->wk.tau_inst, b, cudaMemcpyDeviceToHost));
+  if (stage_bound) CUDA_TRY(c, cudaMemcpy(stage_bound, c->wk.bound_inst, 3 * b, cudaMemcpyDeviceToHost));
+  return check_device_error(c);
+}
+
+eh_status eh_autotune(eh_ctx *c, int32_t steps_per_candidate, int32_t *chosen) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  if (steps_per_candidate < 1) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if ((st = check_device_error(c))) return st;
+  const size_t bytes = sizeof(double) * S_of(c) * c->n;
+  const size_t tb = sizeof(double) * c->ninst;
+  std::vector<double> t_saved(c->ninst);
+  CUDA_TRY(c, cudaMemcpyAsync(c->Usave, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpy(t_saved.data(), c->wk.t_inst, tb, cudaMemcpyDeviceToHost));
+  const int cands[3] = {64, 128, 256};
+  double best_ms[EH_KERNEL_COUNT];
+  int best[EH_KERNEL_COUNT];
+  for (int k = 0; k < EH_KERNEL_COUNT; ++k) {
+    best_ms[k] = INFINITY;
+    best[k] = c->tpb[k];
+  }
+  const bool was_profiling = c->profiling;
+  for (int q = 0; q < 3; ++q) {
+    for (int k = 0; k < EH_KERNEL_COUNT; ++k)
+      if (k != EH_KERNEL_TAU) c->tpb[k] = cands[q];
+    if ((st = eh_profile_enable(c, 1))) return st;
+    CUDA_TRY(c, cudaMemcpyAsync(c->U, c->Usave, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    for (int32_t r = 0; r < steps_per_candidate; ++r) enqueue_step_any(c, 0.0);
+    CUDA_TRY(c, cudaGetLastError());
+    flush_profile(c);
+    for (int k = 0; k < EH_KERNEL_COUNT; ++k)
+      if (k != EH_KERNEL_TAU && c->prof_count[k] && c->prof_ms[k] < best_ms[k]) {
+        best_ms[k] = c->prof_ms[k];
+        best[k] = cands[q];
+      }
+  }
+  eh_profile_enable(c, was_profiling ? 1 : 0);
+  for (int k = 0; k < EH_KERNEL_COUNT; ++k) {
+    c->tpb[k] = best[k];
+    if (chosen) chosen[k] = best[k];
+  }
+  // put the state and the instance times back
+  CUDA_TRY(c, cudaMemcpyAsync(c->U, c->Usave, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->wk.t_inst, t_saved.data(), tb, cudaMemcpyHostToDevice, c->stream));
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return check_device_error(c);
+}
+
 eh_status eh_profile_enable(eh_ctx *c, int enable) {
   if (!c) return EH_ERR_INVALID_ARG;
   CUDA_TRY(c, cudaSetDevice(c->device));
@@ -699,6 +853,12 @@ eh_status eh_profile_read(eh_ctx *c, int kernel, double *total_ms, int64_t *laun
   flush_profile(c);
   *total_ms = c->prof_ms[kernel];
   *launches = c->prof_count[kernel];
+  return EH_OK;
+}
+
+eh_status eh_get_block_sizes(const eh_ctx *c, int32_t *tpb) {
+  if (!c || !tpb) return EH_ERR_INVALID_ARG;
+  for (int k = 0; k < EH_KERNEL_COUNT; ++k) tpb[k] = c->tpb[k];
   return EH_OK;
 }
 

@@ -17,7 +17,8 @@
 
 namespace eh {
 
-constexpr int TPB = 128;  // threads per block of the row kernels
+// threads (= rows) per block of the row kernels: chosen per kernel at run time
+// (default 128, see eh_autotune), at most TPB_MAX
 
 __host__ __device__ inline unsigned nblocks(int64_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
 
@@ -214,7 +215,7 @@ __device__ __forceinline__ void flux(const double *u, const double *v, double pr
 // k_prep: node records (primitives and derived quantities), once per stage
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-__global__ void __launch_bounds__(TPB) k_prep(MeshView m, Params p, const double *__restrict__ U,
+__global__ void __launch_bounds__(TPB_MAX) k_prep(MeshView m, Params p, const double *__restrict__ U,
                                               double *__restrict__ rec, T *__restrict__ vrec, const DevStatus *st) {
   constexpr int S = DIM + 2;
   using R = Rec<DIM>;
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(TPB) k_prep(MeshView m, Params p, const double
 // index), the flux differences w_ij and the indicator alpha_i
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-__global__ void __launch_bounds__(TPB) k_visc(MeshView m, Params p, Work w) {
+__global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
   using R = Rec<DIM>;
@@ -384,15 +385,14 @@ __global__ void __launch_bounds__(TPB) k_visc(MeshView m, Params p, Work w) {
 // bounds and high-order fluxes
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-__global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
+__global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
   using R = Rec<DIM>;
-  __shared__ double smin[TPB / 32];
+  __shared__ double smin[TPB_MAX / 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = i < m.n && !w.st->err;
   double bound = INFINITY;
-  if (active) {
+  if (i < m.n && !w.st->err) {
     const double *Ri = w.rec + (int64_t)i * R::SIZE;
     double ui[S];
 #pragma unroll
@@ -467,50 +467,62 @@ __global__ void __launch_bounds__(TPB) k_low(MeshView m, Params p, Work w) {
     bi[1] = (1.0 + r) * rmax;
     bi[2] = (1.0 - r) * phimin;
   }
-  // block minimum of the CFL bound (exact, order independent)
+  // per-instance minimum of the CFL bound (exact and order independent: the
+  // bit patterns of positive doubles order like their values). A block whose
+  // rows lie in one instance reduces first and issues one atomic.
+  const int first = blockIdx.x * blockDim.x;
+  const int last = min(first + (int)blockDim.x, m.n) - 1;
+  const int k_first = m.inst ? m.inst[first] : 0;
+  const int k_last = m.inst ? m.inst[last] : 0;
+  if (k_first == k_last) {
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) bound = fmin(bound, __shfl_xor_sync(0xffffffffu, bound, off));
-  if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = bound;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = smin[0];
-#pragma unroll
-    for (int q = 1; q < TPB / 32; ++q) b = fmin(b, smin[q]);
-    w.blockmin[blockIdx.x] = b;
+    for (int off = 16; off > 0; off >>= 1) bound = fmin(bound, __shfl_xor_sync(0xffffffffu, bound, off));
+    if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = bound;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = smin[0];
+      for (int q = 1; q < (int)(blockDim.x >> 5); ++q) b = fmin(b, smin[q]);
+      if (b < INFINITY) atomicMin(&w.bound_bits[k_first], (unsigned long long)__double_as_longlong(b));
+    }
+  } else if (i < m.n && bound < INFINITY) {
+    atomicMin(&w.bound_bits[m.inst[i]], (unsigned long long)__double_as_longlong(bound));
   }
 }
 
 // ---------------------------------------------------------------------------
-// k_tau: global minimum of the CFL bound; fixes tau at the first stage
+// k_tau: each instance's CFL bound (the minimum gathered by k_low); fixes the
+// instance's tau at the first stage (Sec. 3.1) and resets the minimum
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_tau(const double *__restrict__ blockmin, int nb, DevStatus *st, int stage,
-                                              double dt_given, double cfl) {
-  __shared__ double sm[32];
-  if (st->err) return;
-  double b = INFINITY;
-  for (int q = threadIdx.x; q < nb; q += blockDim.x) b = fmin(b, blockmin[q]);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) b = fmin(b, __shfl_xor_sync(0xffffffffu, b, off));
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = b;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double bound = sm[0];
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) bound = fmin(bound, sm[q]);
-    st->stage_bound[stage] = bound;
-    const double limit = bound / cfl;  // invariant-domain limit, c_cfl = 1
-    if (stage == 0) {
-      if (dt_given > 0.0) {
-        if (dt_given > limit) {
-          st->err = 5;  // EH_ERR_CFL
-          return;
-        }
-        st->tau = dt_given;
-      } else {
-        st->tau = bound;
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+
+__global__ void __launch_bounds__(256) k_tau(MeshView m, Work w, int stage, double dt_given, double cfl,
+                                             int advance_time) {
+  DevStatus *st = w.st;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m.ninst || st->err) return;
+  const double bound = __longlong_as_double((long long)w.bound_bits[k]);
+  w.bound_bits[k] = kInfBits;
+  w.bound_inst[stage * m.ninst + k] = bound;
+  if (k == 0) st->stage_bound[stage] = bound;
+  const double limit = bound / cfl;  // invariant-domain limit, c_cfl = 1
+  if (stage == 0) {
+    double tau;
+    if (dt_given > 0.0) {
+      if (dt_given > limit) {
+        atomicExch(&st->err, 5);  // EH_ERR_CFL
+        return;
       }
-    } else if (st->tau > limit) {
-      st->cfl_violations += 1;
+      tau = dt_given;
+    } else {
+      tau = bound;
     }
+    const double left = w.tfinal_inst[k] - w.t_inst[k];
+    if (tau > left) tau = left > 0.0 ? left : 0.0;  // land on t_final; finished instances stay frozen
+    w.tau_inst[k] = tau;
+    if (k == 0) st->tau = tau;
+  } else {
+    if (w.tau_inst[k] > limit) atomicAdd(&st->cfl_violations, 1ull);
+    if (advance_time && stage == 2) w.t_inst[k] += w.tau_inst[k];
   }
 }
 
@@ -518,13 +530,13 @@ __global__ void __launch_bounds__(1024) k_tau(const double *__restrict__ blockmi
 // k_lim1: Algorithm 1 step 4 -- U^L, P_ij and the first line search
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-__global__ void __launch_bounds__(TPB) k_lim1(MeshView m, Params p, Work w) {
+__global__ void __launch_bounds__(TPB_MAX) k_lim1(MeshView m, Params p, Work w) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
   using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || w.st->err) return;
-  const double tau = w.st->tau;
+  const double tau = w.tau_inst[m.inst ? m.inst[i] : 0];
   const double *Ri = w.rec + (int64_t)i * R::SIZE;
   double ui[S], ul[S], fhi[S];
   const double *inci = w.inc + (int64_t)i * SP;
@@ -575,7 +587,7 @@ __global__ void __launch_bounds__(TPB) k_lim1(MeshView m, Params p, Work w) {
 // k_pass: symmetrise the limiter, update, shrink P and search again
 // ---------------------------------------------------------------------------
 template <int DIM>
-__global__ void __launch_bounds__(TPB) k_pass(MeshView m, Params p, Work w, const double *__restrict__ Uin,
+__global__ void __launch_bounds__(TPB_MAX) k_pass(MeshView m, Params p, Work w, const double *__restrict__ Uin,
                                               double *__restrict__ Uout, const double *__restrict__ lin,
                                               double *__restrict__ lout, double *lsym_trace) {
   constexpr int S = DIM + 2;
@@ -652,7 +664,7 @@ __device__ __forceinline__ bool admissible(const double *u) {
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(TPB) k_final(MeshView m, Params p, Work w, const double *__restrict__ Uin,
+__global__ void __launch_bounds__(TPB_MAX) k_final(MeshView m, Params p, Work w, const double *__restrict__ Uin,
                                                const double *__restrict__ lin, const double *U0, double coef,
                                                double *out, double *Upre_trace) {
   constexpr int S = DIM + 2;
@@ -676,7 +688,9 @@ __global__ void __launch_bounds__(TPB) k_final(MeshView m, Params p, Work w, con
 #pragma unroll
     for (int s = 0; s < S; ++s) Upre_trace[(int64_t)i * SP + s] = u[s];
   }
-  apply_bc_node<DIM>(m, i, u);
+  // a finished instance (tau = 0) keeps its state bit for bit: the stage is
+  // the identity there, and re-applying the post-processing would not be
+  if (w.tau_inst[m.inst ? m.inst[i] : 0] != 0.0) apply_bc_node<DIM>(m, i, u);
   if (coef >= 0.0) {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -716,30 +730,34 @@ template <int DIM> __global__ void k_count_not_admissible(int n, const double *U
 // launchers
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, cudaStream_t s) {
-  k_prep<DIM, T><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, U, w.rec, (T *)w.vrec, w.st);
+void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, int tpb, cudaStream_t s) {
+  k_prep<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, U, w.rec, (T *)w.vrec, w.st);
 }
-template <int DIM, typename T> void launch_visc(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
-  k_visc<DIM, T><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
+template <int DIM, typename T>
+void launch_visc(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s) {
+  k_visc<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w);
 }
-template <int DIM, typename T> void launch_low(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
-  k_low<DIM, T><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
+template <int DIM, typename T>
+void launch_low(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s) {
+  k_low<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w);
 }
-void launch_tau(const Work &w, int stage, double dt_given, double cfl, cudaStream_t s) {
-  k_tau<<<1, 1024, 0, s>>>(w.blockmin, w.nblocks_rows, w.st, stage, dt_given, cfl);
+void launch_tau(const MeshView &m, const Work &w, int stage, double dt_given, double cfl, bool advance_time,
+                cudaStream_t s) {
+  k_tau<<<nblocks(m.ninst, 256), 256, 0, s>>>(m, w, stage, dt_given, cfl, advance_time ? 1 : 0);
 }
-template <int DIM, typename T> void launch_lim1(const MeshView &m, const Params &p, const Work &w, cudaStream_t s) {
-  k_lim1<DIM, T><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w);
+template <int DIM, typename T>
+void launch_lim1(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s) {
+  k_lim1<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w);
 }
 template <int DIM>
 void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
-                 double *lout, double *lsym_trace, cudaStream_t s) {
-  k_pass<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w, Uin, Uout, lin, lout, lsym_trace);
+                 double *lout, double *lsym_trace, int tpb, cudaStream_t s) {
+  k_pass<DIM><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w, Uin, Uout, lin, lout, lsym_trace);
 }
 template <int DIM>
 void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,
-                  const double *U0, double coef, double *out, double *Upre_trace, cudaStream_t s) {
-  k_final<DIM><<<nblocks(m.n, TPB), TPB, 0, s>>>(m, p, w, Uin, lin, U0, coef, out, Upre_trace);
+                  const double *U0, double coef, double *out, double *Upre_trace, int tpb, cudaStream_t s) {
+  k_final<DIM><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w, Uin, lin, U0, coef, out, Upre_trace);
 }
 template <int DIM> void launch_apply_bc(const MeshView &m, double *U, cudaStream_t s) {
   k_apply_bc<DIM><<<nblocks(m.n, 256), 256, 0, s>>>(m, U);
@@ -749,10 +767,10 @@ template <int DIM> void launch_count_not_admissible(int n, const double *U, DevS
 }
 
 #define EH_INSTANTIATE_T(DIM, T)                                                                                     \
-  template void launch_prep<DIM, T>(const MeshView &, const Params &, const double *, const Work &, cudaStream_t);    \
-  template void launch_visc<DIM, T>(const MeshView &, const Params &, const Work &, cudaStream_t);                    \
-  template void launch_low<DIM, T>(const MeshView &, const Params &, const Work &, cudaStream_t);                     \
-  template void launch_lim1<DIM, T>(const MeshView &, const Params &, const Work &, cudaStream_t);
+  template void launch_prep<DIM, T>(const MeshView &, const Params &, const double *, const Work &, int, cudaStream_t); \
+  template void launch_visc<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);               \
+  template void launch_low<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);                \
+  template void launch_lim1<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);
 
 EH_INSTANTIATE_T(2, double)
 EH_INSTANTIATE_T(3, double)
@@ -761,9 +779,9 @@ EH_INSTANTIATE_T(3, float)
 
 #define EH_INSTANTIATE(DIM)                                                                                          \
   template void launch_pass<DIM>(const MeshView &, const Params &, const Work &, const double *, double *,            \
-                                 const double *, double *, double *, cudaStream_t);                                   \
+                                 const double *, double *, double *, int, cudaStream_t);                              \
   template void launch_final<DIM>(const MeshView &, const Params &, const Work &, const double *, const double *,     \
-                                  const double *, double, double *, double *, cudaStream_t);                          \
+                                  const double *, double, double *, double *, int, cudaStream_t);                     \
   template void launch_apply_bc<DIM>(const MeshView &, double *, cudaStream_t);                                       \
   template void launch_count_not_admissible<DIM>(int, const double *, DevStatus *, cudaStream_t);
 

@@ -66,6 +66,10 @@ struct MeshView {
   const double *bnd_normal;  // [dim][n_bnd]
   const double *bnd_state;   // [S][n_bnd]
   int n_bnd;
+  // independent instances (block-diagonal CSR): rows [inst_row_off[k], inst_row_off[k+1])
+  int ninst;
+  const int32_t *inst;          // instance of every row
+  const int64_t *inst_row_off;  // [ninst + 1]
 };
 
 struct Params {
@@ -91,8 +95,12 @@ struct Work {
   double *P;       // [nnz][SP]
   double *la;      // [nnz]      limiter, ping
   double *lb;      // [nnz]      limiter, pong
-  double *blockmin;
-  int nblocks_rows;
+  unsigned long long *bound_bits;  // [ninst] running minimum of c_cfl m_i / (2 sum_j d_ij) over the
+                                   // instance's rows, as the bit pattern of a positive double (+inf between stages)
+  double *tau_inst; // [ninst]   tau of each instance (fixed at the first stage)
+  double *bound_inst;  // [3][ninst] CFL bound of each stage and instance
+  double *t_inst;   // [ninst]   simulated time of each instance
+  double *tfinal_inst; // [ninst] end time of each instance (+inf: none)
   DevStatus *st;
   // viscosity / flux precision arrays (aliases of rec, w, d, FH in FP64 mode;
   // float arrays in mixed mode)
@@ -109,20 +117,28 @@ struct TraceOut {
 
 // Launchers (all asynchronous on 'stream'). T is the precision of the
 // viscosity / high-order-flux part: double (FP64 mode) or float (mixed mode).
+// 'tpb' is the block size (threads = rows per block): 64, 128 or 256.
+constexpr int TPB_MAX = 256;
 template <int DIM, typename T>
-void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, cudaStream_t s);
-template <int DIM, typename T> void launch_visc(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
-template <int DIM, typename T> void launch_low(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
-void launch_tau(const Work &w, int stage, double dt_given, double cfl, cudaStream_t s);
-template <int DIM, typename T> void launch_lim1(const MeshView &m, const Params &p, const Work &w, cudaStream_t s);
+void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, int tpb, cudaStream_t s);
+template <int DIM, typename T>
+void launch_visc(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s);
+template <int DIM, typename T>
+void launch_low(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s);
+// per-instance minimum of the row bounds; stage 0 fixes tau (dt_given > 0:
+// that step, else the bound), clipped to reach t_final; stage 2 advances t
+void launch_tau(const MeshView &m, const Work &w, int stage, double dt_given, double cfl, bool advance_time,
+                cudaStream_t s);
+template <int DIM, typename T>
+void launch_lim1(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s);
 template <int DIM>
 void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
-                 double *lout, double *lsym_trace, cudaStream_t s);
+                 double *lout, double *lsym_trace, int tpb, cudaStream_t s);
 // out = SSP combination of U0 and BC(Uin + sum lambda l P): coef < 0 -> out = BC(...),
 // else out = U0 + coef (BC(...) - U0). U0 / out are component-major [S][n].
 template <int DIM>
 void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,
-                  const double *U0, double coef, double *out, double *Upre_trace, cudaStream_t s);
+                  const double *U0, double coef, double *out, double *Upre_trace, int tpb, cudaStream_t s);
 template <int DIM> void launch_apply_bc(const MeshView &m, double *U, cudaStream_t s);
 template <int DIM> void launch_count_not_admissible(int n, const double *U, DevStatus *st, cudaStream_t s);
 

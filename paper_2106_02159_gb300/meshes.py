@@ -364,7 +364,7 @@ def _radial_grading(m: int, length: float):
     return t
 
 
-def cylinder_channel_q1(m: int, name: str | None = None) -> Mesh:
+def cylinder_channel_q1(m: int, name: str | None = None, element: str = "q1") -> Mesh:
     """Conforming block-structured Q1 mesh of the channel [0,4]x[0,1] minus the
     disc of radius 0.25 centred at (0.6, 0.5).
 
@@ -462,7 +462,21 @@ def cylinder_channel_q1(m: int, name: str | None = None) -> Mesh:
     faces = np.concatenate(faces)
     fk = np.concatenate(fk)
     fc = np.concatenate(fc)
+    if element == "p1":
+        # every (convex) quad [a, b, c, d] split into [a, b, c] and [a, c, d];
+        # a boundary edge keeps the interior side of its quad
+        tri = np.empty((2 * cells.shape[0], 3), dtype=cells.dtype)
+        tri[0::2] = cells[:, [0, 1, 2]]
+        tri[1::2] = cells[:, [0, 2, 3]]
+        return _finish(name or f"p1-cylinder-m{m}", 2, coords, tri, coords[tri], _local_p1, faces, coords[faces],
+                       fk, 2 * fc)
     return _finish(name or f"q1-cylinder-m{m}", 2, coords, cells, xyz, _local_q1_2d, faces, coords[faces], fk, fc)
+
+
+def cylinder_channel_p1(m: int, name: str | None = None) -> Mesh:
+    """The cylinder channel mesh with every quadrilateral split into two P1
+    triangles (same vertices, boundary and kinds)."""
+    return cylinder_channel_q1(m, name, element="p1")
 
 
 def cylinder_channel_vertices(m: int) -> int:
@@ -531,3 +545,103 @@ def structured_q1_3d(nx: int, ny: int, nz: int, box=((0.0, 1.0), (0.0, 1.0), (0.
             fxyz[:, q] = coords[faces[:, q]]
         return _finish(name or f"q1-3d-{nx}x{ny}x{nz}", 3, coords, cells, xyz, _local_q1_3d, faces, fxyz, fk, fc)
     return _finish(name or f"q1-3d-{nx}x{ny}x{nz}", 3, coords, cells, xyz, _local_q1_3d, None, None, None, None)
+
+
+def concatenate(meshes, bnd_states=None):
+    """Block-diagonal union of independent meshes of one dimension (a batch).
+
+    Returns (mesh, row_offset[k+1], bnd_state or None): instance k owns rows
+    [row_offset[k], row_offset[k+1]); bnd_states (one per mesh, or None) are
+    concatenated along the boundary nodes."""
+    dim = meshes[0].dim
+    assert all(m.dim == dim for m in meshes)
+    noff = np.cumsum([0] + [m.n for m in meshes])
+    eoff = np.cumsum([0] + [m.nnz for m in meshes])
+    row_ptr = np.concatenate([m.row_ptr[:-1] + eoff[k] for k, m in enumerate(meshes)] + [[eoff[-1]]])
+    col = np.concatenate([m.col.astype(np.int64) + noff[k] for k, m in enumerate(meshes)]).astype(np.int32)
+    cat = lambda f, axis=-1: np.ascontiguousarray(np.concatenate([f(m) for m in meshes], axis=axis))  # noqa: E731
+    mesh = Mesh(name=f"batch-{len(meshes)}", dim=dim, coords=cat(lambda m: m.coords, 0), row_ptr=row_ptr.astype(np.int64),
+                col=col, cij=cat(lambda m: m.cij), mij=cat(lambda m: m.mij), mi=cat(lambda m: m.mi),
+                bnd_node=np.concatenate([m.bnd_node.astype(np.int64) + noff[k]
+                                         for k, m in enumerate(meshes)]).astype(np.int32),
+                bnd_kind=cat(lambda m: m.bnd_kind), bnd_normal=cat(lambda m: m.bnd_normal),
+                bnd_mass_full=cat(lambda m: m.bnd_mass_full), bnd_normal_full=cat(lambda m: m.bnd_normal_full))
+    bs = None
+    if bnd_states is not None:
+        S = dim + 2
+        bs = np.ascontiguousarray(np.concatenate(
+            [b if b is not None else np.zeros((S, m.n_bnd)) for m, b in zip(meshes, bnd_states)], axis=1))
+    return mesh, noff.astype(np.int64), bs
+
+
+def extruded_q1(base: Mesh, nz: int, z_len: float = 2.0, name: str | None = None) -> Mesh:
+    """Q1 hexahedra: the 2D Q1 mesh ``base`` extruded over z in [0, z_len)
+    with nz periodic layers (27-point rows for 9-point 2D rows).
+
+    With phi_(a,k)(x, y, z) = phi_a(x, y) psi_k(z) (psi: periodic 1D hat
+    functions, spacing hz) every coefficient is an exact tensor product:
+      c_(a,k),(b,l) = (c2_ab,x m1_kl, c2_ab,y m1_kl, m2_ab c1_kl),
+      m_(a,k),(b,l) = m2_ab m1_kl,  m_(a,k) = m2_a hz,
+    with m1 = hz (1/6, 2/3, 1/6) and c1 = (-1/2, 0, 1/2) on (k-1, k, k+1).
+    Node index a nz + k; boundary faces are the 2D boundary edges times the
+    layers, so n_i = (n2_a, 0) and m^bnd_i = m2^bnd_a hz."""
+    if base.dim != 2:
+        raise ValueError("extrude a 2D mesh")
+    if nz < 3:
+        raise ValueError("need at least 3 periodic layers")
+    hz = z_len / nz
+    n2, nnz2 = base.n, base.nnz
+    k = np.arange(nz, dtype=np.int64)
+    lz = np.stack([(k - 1) % nz, k, (k + 1) % nz], axis=1)   # neighbour layers
+    m1 = np.array([hz / 6.0, 2.0 * hz / 3.0, hz / 6.0])
+    c1 = np.array([-0.5, 0.0, 0.5])
+    order = np.argsort(lz, axis=1, kind="stable")              # sorted column order per layer
+    lz_s = np.take_along_axis(lz, order, axis=1)               # [nz, 3]
+    m1_s = m1[order]
+    c1_s = c1[order]
+    rows2 = base.row_of_entry()
+    cnt2 = np.diff(base.row_ptr)                               # 2D row lengths
+    n = n2 * nz
+    nnz = nnz2 * 3 * nz
+    row_len = np.repeat(cnt2 * 3, nz)                          # row (a, k) has 3 cnt2[a] entries
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum(row_len)
+    # entries of row (a, k): for every 2D entry e of row a, the 3 layers l of k
+    # (columns b nz + l increase with b, then with l: sorted)
+    col = np.empty(nnz, dtype=np.int32)
+    cij = np.empty((3, nnz))
+    mij = np.empty(nnz)
+    # vectorised over (a, k): block of row a has cnt2[a] * 3 entries per layer
+    e_start = base.row_ptr[:-1]
+    for a0 in range(0, n2, 4096):
+        a1 = min(n2, a0 + 4096)
+        for a in range(a0, a1):
+            e0, e1 = int(base.row_ptr[a]), int(base.row_ptr[a + 1])
+            b = base.col[e0:e1].astype(np.int64)               # [c]
+            c = e1 - e0
+            base_pos = row_ptr[a * nz]
+            # [nz, c, 3]
+            colv = b[None, :, None] * nz + lz_s[:, None, :]
+            pos = base_pos + np.arange(nz * c * 3)
+            col[pos] = colv.reshape(-1)
+            cx = base.cij[0, e0:e1][None, :, None] * m1_s[:, None, :]
+            cy = base.cij[1, e0:e1][None, :, None] * m1_s[:, None, :]
+            cz = base.mij[e0:e1][None, :, None] * c1_s[:, None, :]
+            cij[0, pos] = cx.reshape(-1)
+            cij[1, pos] = cy.reshape(-1)
+            cij[2, pos] = cz.reshape(-1)
+            mij[pos] = (base.mij[e0:e1][None, :, None] * m1_s[:, None, :]).reshape(-1)
+    del e_start, rows2
+    mi = np.repeat(base.mi, nz) * hz
+    coords = np.empty((n, 3))
+    coords[:, :2] = np.repeat(base.coords, nz, axis=0)
+    coords[:, 2] = np.tile(k * hz, n2)
+    bn = (base.bnd_node.astype(np.int64)[:, None] * nz + k[None, :]).reshape(-1).astype(np.int32)
+    rep = lambda x: np.repeat(x, nz)  # noqa: E731
+    normal = np.zeros((3, bn.size))
+    normal[:2] = np.repeat(base.bnd_normal, nz, axis=1)
+    nfull = np.zeros((3, bn.size))
+    nfull[:2] = np.repeat(base.bnd_normal_full, nz, axis=1)
+    return Mesh(name=name or f"{base.name}-extruded{nz}", dim=3, coords=coords, row_ptr=row_ptr, col=col,
+                cij=cij, mij=mij, mi=mi, bnd_node=bn, bnd_kind=rep(base.bnd_kind), bnd_normal=normal,
+                bnd_mass_full=rep(base.bnd_mass_full) * hz, bnd_normal_full=nfull)

@@ -166,3 +166,22 @@ def perturbed_state(mesh, seed: int, base=None, amplitude=0.3, n_bumps=12, gamma
         for d in range(mesh.dim):
             vel[d] += amplitude * rng.uniform(-2.0, 2.0) * g
     return conserved(rho, vel[: mesh.dim], p, gamma)
+
+
+def cylinder_instance(m: int, mach: float, gamma=1.4):
+    """Cylinder channel of size m with inflow rho = 1.4, p = 1 (sound speed 1)
+    and u = (mach, 0); returns (mesh, U0, bnd_state)."""
+    mesh = meshes.cylinder_channel_q1(m)
+    U0 = uniform_state(mesh, 1.4, (mach, 0.0), 1.0, gamma)
+    return mesh, U0, np.ascontiguousarray(U0[:, mesh.bnd_node])
+
+
+def batch_sweep(count: int = 256, seed: int = 4, m_range=(8, 256), mach_range=(1.5, 4.0)):
+    """Seeded sweep of independent Q1 cylinder instances: n_y = m cells across
+    the channel, m log-uniform in m_range (cells n_x n_y ~ 4 m^2 log-uniform
+    between 32x8 and 1024x256), inflow Mach uniform in mach_range. Returns a
+    list of (m, mach)."""
+    rng = np.random.default_rng(seed)
+    ms = np.exp(rng.uniform(np.log(m_range[0]), np.log(m_range[1]), count)).round().astype(int)
+    machs = rng.uniform(mach_range[0], mach_range[1], count)
+    return list(zip(ms.tolist(), machs.tolist()))

@@ -137,3 +137,29 @@ def test_vortex_initial_data_is_a_steady_isentropic_vortex():
     assert np.allclose(dpdr, rho * v ** 2 / r, rtol=1e-7, atol=1e-10)
     assert np.allclose(p / rho ** g, 1.0, rtol=1e-14)
     assert np.allclose(u, 0.0, atol=1e-15)
+
+
+def test_extruded_mesh_equals_direct_3d_assembly():
+    """The tensor-product extrusion equals 3x3x3-Gauss assembly of the same
+    hexahedra (structured box, periodic in z): identical CSR, c_ij, m_ij, m_i."""
+    base = M.structured_q1(4, 3, 0.0, 1.0, 0.0, 0.75)
+    ext = M.extruded_q1(base, 5, z_len=1.25)
+    ref = M.structured_q1_3d(4, 3, 5, box=((0.0, 1.0), (0.0, 0.75), (0.0, 1.25)),
+                             periodic=(False, False, True))
+    # both number nodes (x, y) major and z minor
+    assert np.array_equal(ext.row_ptr, ref.row_ptr) and np.array_equal(ext.col, ref.col)
+    assert np.allclose(ext.cij, ref.cij, rtol=0, atol=1e-15)
+    assert np.allclose(ext.mij, ref.mij, rtol=0, atol=1e-16)
+    assert np.allclose(ext.mi, ref.mi, rtol=1e-14)
+    assert np.array_equal(np.sort(ext.bnd_node), np.sort(ref.bnd_node))
+
+
+def test_extruded_cylinder_identities():
+    m = M.extruded_q1(M.cylinder_channel_q1(8), 4)
+    rows = m.row_of_entry()
+    assert np.abs(np.stack([np.bincount(rows, weights=m.cij[d], minlength=m.n) for d in range(3)])).max() < 1e-15
+    cs = np.stack([np.bincount(m.col, weights=m.cij[d], minlength=m.n) for d in range(3)])
+    full = np.zeros((3, m.n))
+    full[:, m.bnd_node] = m.bnd_mass_full * m.bnd_normal_full
+    assert np.abs(cs - full).max() < 1e-14
+    assert np.unique(np.diff(m.row_ptr)).max() == 27
