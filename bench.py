@@ -191,7 +191,8 @@ def algorithmic_fp64_flops(kernel: str, n: int, nnz: int, dim: int) -> float:
     e = nnz - n
     per_entry = {
         "prep": 0,
-        "visc": 3 * S * dim + 4 * dim + 2 * S + 4 + (5 * dim + 15) / 2.0,
+        # k_visc once per unique edge (w_ij, a_ij, lambda_max, d_ij) + k_alpha per entry
+        "visc": (3 * S * dim + 4 * dim + 5 * dim + 15) / 2.0 + 2 * S + 4,
         "low": 7 * S + 12,
         "lim1": 9 * S + 2 * dim + 18,
         "pass": 5 * S + 2 * dim + 16,
@@ -588,8 +589,16 @@ def run_cylinder3d(args, dist):
         stream.synchronize()
         ms = e0.elapsed_time(e1)
         s.synchronize()
+        U = s.get_state()
+        viol = s.diagnostics()["not_admissible"]
+        s.profile(True)
+        s.run(1)
+        prof = s.profile_read()
+        s.profile(False)
+        tot = sum(v[0] for v in prof.values())
+        shares = {k: round(v[0] / tot, 4) for k, v in sorted(prof.items(), key=lambda t: -t[1][0]) if v[1]}
         out[prec] = dict(value=mesh.n * 3 * args.steps / (ms * 1e-3), ms_per_step=ms / args.steps,
-                         U=s.get_state(), violations=s.diagnostics()["not_admissible"])
+                         U=U, violations=viol, shares=shares)
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -609,7 +618,8 @@ def run_cylinder3d(args, dist):
                           "speedup_vs_fp64": out["mixed"]["value"] / out["fp64"]["value"],
                           "l1_rel_error_vs_fp64_run": dict(zip(names, err.tolist())),
                           "after_steps": args.warmup + args.steps},
-                "invariant_violations": {"fp64": out["fp64"]["violations"], "mixed": out["mixed"]["violations"]}}
+                "invariant_violations": {"fp64": out["fp64"]["violations"], "mixed": out["mixed"]["violations"]},
+                "kernel_shares": {"fp64": out["fp64"]["shares"], "mixed": out["mixed"]["shares"]}}
         print(json.dumps(line), flush=True)
 
 

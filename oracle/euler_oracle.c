@@ -39,6 +39,8 @@
  *  - d_ij takes the max of both directions only when i and j are both
  *    boundary nodes (c_ji = -c_ij exactly whenever one of them is interior).
  *  - every limiter pass is symmetrised, l_ij = min(l_j^i, l_i^j).
+ *  - P_ij = 0 (a pass after l_ij = 1, uniform flow): every l gives the same
+ *    state and the line search returns 1, the largest.
  *  - sums over I(i) are written in increment form (differences U_j - U_i,
  *    f(U_j) - f(U_i)), which equals the paper's form because sum_j c_ij = 0
  *    and sum_j d_ij = 0, and makes uniform states exact fixed points; the
@@ -290,6 +292,10 @@ static double dpsi(const double *ub, const double *P, double l, int dim, double 
  * iterations, then the left point is returned. */
 double oracle_line_search(const double *ub, const double *P, double rho_min, double rho_max, double phi_min,
                           int dim, double gamma) {
+  /* P = 0: every l gives the same state; the largest one, 1, is returned */
+  int zero = 1;
+  for (int s = 0; s < dim + 2; ++s) zero &= P[s] == 0.0;
+  if (zero) return 1.0;
   double l = 1.0;
   double rb = ub[0], rp = P[0];
   if (rp > 0.0) {

@@ -184,7 +184,11 @@ void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, con
   const Work &w = c->wk;
   const int *tpb = c->tpb;
   { ProfScope ps(c, EH_KERNEL_PREP); launch_prep<DIM, T>(m, p, Uin, w, tpb[EH_KERNEL_PREP], s); }
-  { ProfScope ps(c, EH_KERNEL_VISC); launch_visc<DIM, T>(m, p, w, tpb[EH_KERNEL_VISC], s); }
+  {
+    ProfScope ps(c, EH_KERNEL_VISC);
+    launch_visc<DIM, T>(m, p, w, tpb[EH_KERNEL_VISC], s);
+    launch_alpha<DIM, T>(m, p, w, tpb[EH_KERNEL_VISC], s);
+  }
   { ProfScope ps(c, EH_KERNEL_LOW); launch_low<DIM, T>(m, p, w, tpb[EH_KERNEL_LOW], s); }
   { ProfScope ps(c, EH_KERNEL_TAU); launch_tau(m, w, stage, dt_given, p.cfl, !trace, s); }
   { ProfScope ps(c, EH_KERNEL_LIM1); launch_lim1<DIM, T>(m, p, w, tpb[EH_KERNEL_LIM1], s); }
@@ -240,6 +244,7 @@ void enqueue_stage_any(eh_ctx *c, double tau) {
 template <int DIM, typename T> void enqueue_cfl(eh_ctx *c) {
   launch_prep<DIM, T>(c->mv, c->prm, c->U, c->wk, c->tpb[EH_KERNEL_PREP], c->stream);
   launch_visc<DIM, T>(c->mv, c->prm, c->wk, c->tpb[EH_KERNEL_VISC], c->stream);
+  launch_alpha<DIM, T>(c->mv, c->prm, c->wk, c->tpb[EH_KERNEL_VISC], c->stream);
   launch_low<DIM, T>(c->mv, c->prm, c->wk, c->tpb[EH_KERNEL_LOW], c->stream);
 }
 
@@ -504,7 +509,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   float *f_cij = nullptr, *f_cn = nullptr, *f_cinv = nullptr;
   if (c->cfg.precision == EH_PRECISION_MIXED) {
     // FP32 c_ij, |c_ij|, 1/|c_ij|, node record, w_ij, d_ij and F^H
-    float *f_rec, *f_w, *f_d, *f_fh;
+    float *f_rec, *f_w, *f_d, *f_fh, *f_a;
     ALLOC(f_cij, (size_t)dim * nnz);
     ALLOC(f_cn, nnz);
     ALLOC(f_cinv, nnz);
@@ -512,6 +517,8 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
     ALLOC(f_w, (size_t)nnz * SP);
     ALLOC(f_d, nnz);
     ALLOC(f_fh, (size_t)n * SP);
+    ALLOC(f_a, nnz);
+    w.va = f_a;
     w.vrec = f_rec;
     w.vw = f_w;
     w.vd = f_d;
@@ -520,6 +527,9 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
     ALLOC(w.w, (size_t)nnz * SP);
     ALLOC(w.d, nnz);
     ALLOC(w.FH, (size_t)n * SP);
+    double *d_a;
+    ALLOC(d_a, nnz);
+    w.va = d_a;
     w.vrec = w.rec;
     w.vw = w.w;
     w.vd = w.d;
@@ -864,8 +874,8 @@ eh_status eh_get_block_sizes(const eh_ctx *c, int32_t *tpb) {
 
 int32_t eh_launches_per_step(const eh_ctx *c) {
   if (!c) return 0;
-  // prep, visc, low, tau, lim1, (passes - 1) x pass, final; three stages
-  return 3 * (6 + (c->cfg.limiter_passes - 1));
+  // prep, visc, alpha, low, tau, lim1, (passes - 1) x pass, final; three stages
+  return 3 * (7 + (c->cfg.limiter_passes - 1));
 }
 
 eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {

@@ -140,6 +140,12 @@ template <int DIM>
 __device__ double line_search(const Params &p, const double *ub, const double *P, double rmin, double rmax,
                               double phimin, double phimin5) {
   constexpr int S = DIM + 2;
+  // P = 0 (every edge whose previous limiter was 1, uniform flow): every l gives
+  // the same state; the largest, 1, is returned without any FP64 work
+  bool zero = true;
+#pragma unroll
+  for (int s = 0; s < S; ++s) zero &= (__double_as_longlong(P[s]) << 1) == 0;
+  if (zero) return 1.0;
   double l = 1.0;
   const double rb = ub[0], rp = P[0];
   // density: the division is needed only when l = 1 leaves [rho_min, rho_max]
@@ -288,52 +294,36 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
   const T *cn = (const T *)m.vcn;
   const T *cinv = (const T *)m.vcinv;
   T *warr = (T *)w.vw;
+  T *aarr = (T *)w.va;
   T *darr = (T *)w.vd;
   const T *Ri = rec + (int64_t)i * R::SIZE;
-  T ui[S], vi[DIM];
-#pragma unroll
-  for (int s = 0; s < S; ++s) ui[s] = Ri[s];
+  T vi[DIM], fi[S][DIM], qi[DIM];
 #pragma unroll
   for (int k = 0; k < DIM; ++k) vi[k] = Ri[R::V + k];
   const T pi = Ri[R::P], ai = Ri[R::A], azi = Ri[R::AZ], ipi = Ri[R::IP], etai = Ri[R::ETA];
-  const T epsi = Ri[R::EPS];
-  T fi[S][DIM];
 #pragma unroll
   for (int s = 0; s < S; ++s)
 #pragma unroll
     for (int q = 0; q < DIM; ++q) fi[s][q] = Ri[R::F + s * DIM + q];
-  // eta'(U_i) (Sec. 3.2 indicator)
-  T deta[S];
-  {
-    const T gm1 = T(p.gm1);
-    T s_i = -etai / ui[0];
-    T g1 = ui[0] / (gm1 * epsi);
-    T v2 = T(0);
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) v2 += vi[k] * vi[k];
-    deta[0] = -s_i - ui[0] / gm1 * (v2 / (T(2) * epsi) - T(p.gamma) / ui[0]);
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) deta[1 + k] = g1 * vi[k];
-    deta[S - 1] = -g1;
-  }
-  T qi[DIM];
 #pragma unroll
   for (int k = 0; k < DIM; ++k) qi[k] = vi[k] * etai;
   const bool bi = m.isb[i] != 0;
-  T N = T(0), D = T(0);
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
   for (int64_t k = k0; k < k1; ++k) {
     const int j = m.col[k];
-    if (j == i) continue;
+    if (j <= i) continue;  // each unique edge once, from the row of min(i, j)
     const T *Rj = rec + (int64_t)j * R::SIZE;
-    T vj[DIM], c[DIM];
+    const int32_t kt = m.tr[k];
+    T vj[DIM], c[DIM], qj[DIM];
+    const T etaj = Rj[R::ETA];
 #pragma unroll
     for (int q = 0; q < DIM; ++q) {
       vj[q] = Rj[R::V + q];
+      qj[q] = vj[q] * etaj;
       c[q] = cij[(int64_t)q * m.nnz + k];
     }
-    const T pj = Rj[R::P], etaj = Rj[R::ETA];
-    T wv[S];
+    // w_ij = (f_j - f_i) c_ij and a_ij = (q_j - q_i) . c_ij
+    T wv[S], a_ = T(0);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       T acc = T(0);
@@ -341,41 +331,100 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
       for (int q = 0; q < DIM; ++q) acc += (Rj[R::F + s * DIM + q] - fi[s][q]) * c[q];
       wv[s] = acc;
     }
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) a_ += (qj[q] - qi[q]) * c[q];
     T *wk = warr + k * SP;
 #pragma unroll
     for (int s = 0; s < S; ++s) wk[s] = wv[s];
-    T a_ = T(0), b_ = T(0);
+    aarr[k] = a_;
+    const bool both = bi && m.isb[j];
+    // the transposed entry: c_ji = -c_ij unless both nodes lie on the boundary
+    // (Sec. 3.1), so w_ji = w_ij and a_ji = a_ij; otherwise evaluate with c_ji
+    T *wt = warr + (int64_t)kt * SP;
+    if (!both) {
 #pragma unroll
-    for (int q = 0; q < DIM; ++q) a_ += (vj[q] * etaj - qi[q]) * c[q];
+      for (int s = 0; s < S; ++s) wt[s] = wv[s];
+      aarr[kt] = a_;
+    } else {
+      T ct[DIM], at = T(0);
 #pragma unroll
-    for (int s = 0; s < S; ++s) b_ += deta[s] * wv[s];
-    N += a_ - b_;
-    D += fabs(a_) + fabs(b_);
-    if (j > i) {
-      const T ci = cinv[k];
-      T unl = T(0), unr = T(0);
+      for (int q = 0; q < DIM; ++q) ct[q] = cij[(int64_t)q * m.nnz + kt];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) acc += (fi[s][q] - Rj[R::F + s * DIM + q]) * ct[q];
+        wt[s] = acc;
+      }
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) at += (qi[q] - qj[q]) * ct[q];
+      aarr[kt] = at;
+    }
+    // d_ij (Sec. 3.1), mirrored
+    const T ci = cinv[k];
+    T unl = T(0), unr = T(0);
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) {
+      unl += vi[q] * (c[q] * ci);
+      unr += vj[q] * (c[q] * ci);
+    }
+    T dij = lambda_max<T>(p, unl, pi, ai, azi, ipi, unr, Rj[R::P], Rj[R::A], Rj[R::AZ], Rj[R::IP]) * cn[k];
+    if (both) {
+      const T cit = cinv[kt];
+      T unj = T(0), uni = T(0);
 #pragma unroll
       for (int q = 0; q < DIM; ++q) {
-        unl += vi[q] * (c[q] * ci);
-        unr += vj[q] * (c[q] * ci);
+        T nq = cij[(int64_t)q * m.nnz + kt] * cit;
+        unj += vj[q] * nq;
+        uni += vi[q] * nq;
       }
-      T dij = lambda_max<T>(p, unl, pi, ai, azi, ipi, unr, pj, Rj[R::A], Rj[R::AZ], Rj[R::IP]) * cn[k];
-      const int32_t kt = m.tr[k];
-      if (bi && m.isb[j]) {
-        const T cit = cinv[kt];
-        T unj = T(0), uni = T(0);
-#pragma unroll
-        for (int q = 0; q < DIM; ++q) {
-          T nq = cij[(int64_t)q * m.nnz + kt] * cit;
-          unj += vj[q] * nq;
-          uni += vi[q] * nq;
-        }
-        T dji = lambda_max<T>(p, unj, pj, Rj[R::A], Rj[R::AZ], Rj[R::IP], uni, pi, ai, azi, ipi) * cn[kt];
-        dij = fmax(dij, dji);
-      }
-      darr[k] = dij;
-      darr[kt] = dij;
+      T dji = lambda_max<T>(p, unj, Rj[R::P], Rj[R::A], Rj[R::AZ], Rj[R::IP], uni, pi, ai, azi, ipi) * cn[kt];
+      dij = fmax(dij, dji);
     }
+    darr[k] = dij;
+    darr[kt] = dij;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_alpha: the indicator alpha_i (Sec. 3.2) from the row's w_ij and a_ij
+// ---------------------------------------------------------------------------
+template <int DIM, typename T>
+__global__ void __launch_bounds__(TPB_MAX) k_alpha(MeshView m, Params p, Work w) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  using R = Rec<DIM>;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.n || w.st->err) return;
+  const T *Ri = (const T *)w.vrec + (int64_t)i * R::SIZE;
+  const T *warr = (const T *)w.vw;
+  const T *aarr = (const T *)w.va;
+  // eta'(U_i)
+  T deta[S];
+  {
+    const T gm1 = T(p.gm1);
+    const T rho = Ri[0], epsi = Ri[R::EPS];
+    T s_i = -Ri[R::ETA] / rho;
+    T g1 = rho / (gm1 * epsi);
+    T v2 = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) v2 += Ri[R::V + k] * Ri[R::V + k];
+    deta[0] = -s_i - rho / gm1 * (v2 / (T(2) * epsi) - T(p.gamma) / rho);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) deta[1 + k] = g1 * Ri[R::V + k];
+    deta[S - 1] = -g1;
+  }
+  T N = T(0), D = T(0);
+  const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
+  for (int64_t k = k0; k < k1; ++k) {
+    if (m.col[k] == i) continue;
+    const T *wk = warr + k * SP;
+    const T a_ = aarr[k];
+    T b_ = T(0);
+#pragma unroll
+    for (int s = 0; s < S; ++s) b_ += deta[s] * wk[s];
+    N += a_ - b_;
+    D += fabs(a_) + fabs(b_);
   }
   w.alpha[i] = D > T(0) ? (double)(fabs(N) / D) : 0.0;
 }
@@ -583,6 +632,13 @@ __global__ void __launch_bounds__(TPB_MAX) k_lim1(MeshView m, Params p, Work w) 
   }
 }
 
+// min of two limiters in [0, 1]: non-negative doubles order like their bit
+// patterns, so an integer min (no FP64 instruction) gives the same value
+__device__ __forceinline__ double lmin(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x < y ? x : y);
+}
+
 // ---------------------------------------------------------------------------
 // k_pass: symmetrise the limiter, update, shrink P and search again
 // ---------------------------------------------------------------------------
@@ -605,7 +661,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_pass(MeshView m, Params p, Work w, 
       if (lsym_trace) lsym_trace[k] = 1.0;
       continue;
     }
-    const double l = fmin(lin[k], lin[m.tr[k]]);
+    const double l = lmin(lin[k], lin[m.tr[k]]);
     if (lsym_trace) lsym_trace[k] = l;
     const double *Pk = w.P + k * SP;
 #pragma unroll
@@ -622,7 +678,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_pass(MeshView m, Params p, Work w, 
       lout[k] = 1.0;
       continue;
     }
-    const double l = fmin(lin[k], lin[m.tr[k]]);
+    const double l = lmin(lin[k], lin[m.tr[k]]);
     double *Pk = w.P + k * SP;
     double P[S];
 #pragma unroll
@@ -679,7 +735,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_final(MeshView m, Params p, Work w,
   for (int s = 0; s < S; ++s) u[s] = Ui[s];
   for (int64_t k = k0; k < k1; ++k) {
     if (m.col[k] == i) continue;
-    const double l = fmin(lin[k], lin[m.tr[k]]);
+    const double l = lmin(lin[k], lin[m.tr[k]]);
     const double *Pk = w.P + k * SP;
 #pragma unroll
     for (int s = 0; s < S; ++s) u[s] += lambda_i * l * Pk[s];
@@ -738,6 +794,10 @@ void launch_visc(const MeshView &m, const Params &p, const Work &w, int tpb, cud
   k_visc<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w);
 }
 template <int DIM, typename T>
+void launch_alpha(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s) {
+  k_alpha<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w);
+}
+template <int DIM, typename T>
 void launch_low(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s) {
   k_low<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w);
 }
@@ -769,6 +829,7 @@ template <int DIM> void launch_count_not_admissible(int n, const double *U, DevS
 #define EH_INSTANTIATE_T(DIM, T)                                                                                     \
   template void launch_prep<DIM, T>(const MeshView &, const Params &, const double *, const Work &, int, cudaStream_t); \
   template void launch_visc<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);               \
+  template void launch_alpha<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);              \
   template void launch_low<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);                \
   template void launch_lim1<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);
 

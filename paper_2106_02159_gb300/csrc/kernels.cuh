@@ -107,6 +107,7 @@ struct Work {
   void *vrec;      // [n][Rec::SIZE] node record in that precision
   void *vw;        // [nnz][SP]
   void *vd;        // [nnz]
+  void *va;        // [nnz]      (q(U_j) - q(U_i)) . c_ij of the indicator
   void *vFH;       // [n][SP]
 };
 
@@ -123,6 +124,8 @@ template <int DIM, typename T>
 void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, int tpb, cudaStream_t s);
 template <int DIM, typename T>
 void launch_visc(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s);
+template <int DIM, typename T>
+void launch_alpha(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s);
 template <int DIM, typename T>
 void launch_low(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s);
 // per-instance minimum of the row bounds; stage 0 fixes tau (dt_given > 0:

@@ -108,7 +108,9 @@ def test_stage_intermediates_match_oracle(case):
     assert np.all((alpha >= 0) & (alpha <= 1))
     for what, key in ((B.EH_TRACE_U_LOW, "UL"), (B.EH_TRACE_F_HIGH, "FH")):
         got = s.trace(what)
-        scale = np.maximum(np.abs(tr[key]).max(axis=1, keepdims=True), 1e-3 * np.abs(tr[key]).max()) + 1e-300
+        # relative to the array's largest entry: F^H sums terms that cancel,
+        # so a component's own maximum can sit near its roundoff
+        scale = np.abs(tr[key]).max() + 1e-300
         assert (np.abs(got - tr[key]) / scale).max() <= 1e-12, key
     bounds = s.trace(B.EH_TRACE_BOUNDS)
     assert np.allclose(bounds, tr["bounds"], rtol=1e-13, atol=0)
