@@ -111,11 +111,6 @@ struct Work {
   void *vFH;       // [n][SP]
 };
 
-struct TraceOut {
-  double *lsym1;   // [nnz] or null
-  double *Upass1;  // [n][SP] or null (written by the last limiting pass when passes == 1)
-};
-
 // Launchers (all asynchronous on 'stream'). T is the precision of the
 // viscosity / high-order-flux part: double (FP64 mode) or float (mixed mode).
 // 'tpb' is the block size (threads = rows per block): 64, 128 or 256.
