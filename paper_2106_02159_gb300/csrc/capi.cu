@@ -392,6 +392,7 @@ eh_status eh_create(const eh_config *cfg, eh_ctx **out) {
   p.z = (cfg->gamma - 1.0) / (2.0 * cfg->gamma);
   p.inv_z = 1.0 / p.z;
   p.kshock = (cfg->gamma + 1.0) / (2.0 * cfg->gamma);
+  p.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
   *out = c;
   return EH_OK;
 }

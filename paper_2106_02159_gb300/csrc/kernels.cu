@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_prep(MeshView m, Params p, const do
     v[k] = u[1 + k] * irho;
     m2 += u[1 + k] * u[1 + k];
   }
-  double eps = u[S - 1] - m2 / (2.0 * rho);
+  double eps = u[S - 1] - 0.5 * m2 * irho;
   double pr = p.gm1 * eps;
   double a = sqrt(p.gamma * pr * irho);
   double az, phi;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_prep(MeshView m, Params p, const do
     az = a * pow(pr, -p.z);
     phi = eps * pow(rho, -p.gamma);
   }
-  double eta = -rho * (log(phi) / p.gm1);
+  double eta = -rho * (log(phi) * p.inv_gm1);
   double *Rr = rec + (int64_t)i * R::SIZE;
 #pragma unroll
   for (int s = 0; s < S; ++s) Rr[s] = u[s];
@@ -264,6 +264,8 @@ __global__ void __launch_bounds__(TPB_MAX) k_prep(MeshView m, Params p, const do
   Rr[R::PHI] = phi;
   Rr[R::ETA] = eta;
   Rr[R::EPS] = eps;
+  Rr[R::IRHO] = irho;
+  Rr[R::IEPS] = 1.0 / eps;
   double f[S][DIM];
   flux<DIM>(u, v, pr, f);
 #pragma unroll
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_prep(MeshView m, Params p, const do
     // the same record in the viscosity precision (mixed mode)
     T *Rv = vrec + (int64_t)i * R::SIZE;
 #pragma unroll
-    for (int q = 0; q < R::F + S * DIM; ++q) Rv[q] = (T)Rr[q];
+    for (int q = 0; q <= R::IEPS; ++q) Rv[q] = (T)Rr[q];
   }
 }
 
@@ -402,14 +404,15 @@ __global__ void __launch_bounds__(TPB_MAX) k_alpha(MeshView m, Params p, Work w)
   // eta'(U_i)
   T deta[S];
   {
-    const T gm1 = T(p.gm1);
-    const T rho = Ri[0], epsi = Ri[R::EPS];
-    T s_i = -Ri[R::ETA] / rho;
-    T g1 = rho / (gm1 * epsi);
+    // eta' = (-s - rho/(gamma-1) (|v|^2/(2 eps) - gamma/rho), g1 v, -g1), g1 = rho/((gamma-1) eps)
+    const T igm1 = T(p.inv_gm1);
+    const T rho = Ri[0], irho = Ri[R::IRHO], ieps = Ri[R::IEPS];
+    T s_i = -Ri[R::ETA] * irho;
+    T g1 = rho * igm1 * ieps;
     T v2 = T(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) v2 += Ri[R::V + k] * Ri[R::V + k];
-    deta[0] = -s_i - rho / gm1 * (v2 / (T(2) * epsi) - T(p.gamma) / rho);
+    deta[0] = -s_i - rho * igm1 * (T(0.5) * v2 * ieps - T(p.gamma) * irho);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) deta[1 + k] = g1 * Ri[R::V + k];
     deta[S - 1] = -g1;
@@ -450,11 +453,12 @@ __global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
     T *darr = (T *)w.vd;
     const T *warr = (const T *)w.vw;
     // U^L increment and the bounds in FP64; F^H in the viscosity precision T
-    double inc[S];
+    double inc[S], wsum[S];  // U^L increment in FP64 (also in mixed mode)
     T fh[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       inc[s] = 0.0;
+      wsum[s] = 0.0;
       fh[s] = T(0);
     }
     // bar-state densities rho_bar = num / den, den = 2 d_ij > 0; the running
@@ -481,8 +485,9 @@ __global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
         const double ws = (double)wsT;
         if (s == 0) w0 = ws;
         const double du = Rj[s] - ui[s];
-        inc[s] += dk * du - ws;
-        fh[s] += -wsT + dH * (T)du;
+        inc[s] += dk * du;  // sum_j d_ij (U_j - U_i); the sum of w_ij is subtracted once
+        fh[s] += dH * (T)du;
+        wsum[s] += ws;
       }
       if (dk > 0.0) {
         const double num = dk * (ui[0] + Rj[0]) - w0;
@@ -496,8 +501,15 @@ __global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
           dmax = den;
         }
       }
-      phimin = fmin(phimin, Rj[R::PHI]);
+      // Phi > 0: the integer order of the bit patterns is the numeric order
+      const long long pj = __double_as_longlong(Rj[R::PHI]), pm = __double_as_longlong(phimin);
+      phimin = __longlong_as_double(pj < pm ? pj : pm);
       dsum += dk;
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      inc[s] -= wsum[s];
+      fh[s] -= (T)wsum[s];
     }
     darr[kd] = (T)(-dsum);
     bound = p.cfl * m.mi[i] / (2.0 * dsum);

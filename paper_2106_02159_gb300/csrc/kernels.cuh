@@ -27,8 +27,10 @@ template <int DIM> struct Rec {
   static constexpr int ETA = 2 * DIM + 7; // eta = -rho s
   static constexpr int EPS = 2 * DIM + 8; // internal energy eps
   static constexpr int F = 2 * DIM + 9;   // flux f(U)[s][q] at F + s * DIM + q
+  static constexpr int IRHO = F + (DIM + 2) * DIM;  // 1/rho
+  static constexpr int IEPS = IRHO + 1;             // 1/eps
   static constexpr int SIZE = DIM == 2 ? 24 : 32;
-  static_assert(F + (DIM + 2) * DIM <= SIZE, "node record too small");
+  static_assert(IEPS < SIZE, "node record too small");
 };
 constexpr int REC_MAX = 32;  // record stride allocated for either dimension
 
@@ -79,6 +81,7 @@ struct Params {
   double z;                  // (gamma-1)/(2 gamma)
   double inv_z;              // 2 gamma/(gamma-1)
   double kshock;             // (gamma+1)/(2 gamma)
+  double inv_gm1;            // 1/(gamma - 1)
 };
 
 struct Work {
