@@ -66,12 +66,14 @@ typedef struct {
 } eh_config;
 
 typedef struct {
-  double t;                   /* simulated time advanced by eh_step/eh_run */
+  double t;                   /* simulated time advanced by eh_step/eh_run (instance 0) */
   int64_t steps;              /* SSPRK(3,3) steps taken */
   double last_dt;             /* dt of the last step */
   double last_stage_bound[3]; /* c_cfl min_i m_i / (2 |d_ii|) of the last step's three stages */
   int64_t cfl_violations;     /* stages 2-3 whose dt exceeded min_i m_i/(2|d_ii|) (c_cfl = 1) */
   int64_t not_admissible;     /* non-admissible nodes found after a step (0 unless an error) */
+  int64_t line_searches_deferred; /* limiter line searches (Sec. 3.3) not settled by the check at
+                                     l = 1 and run in a separate pass, summed over all steps */
 } eh_diagnostics;
 
 /* Fills *cfg with the defaults: dim 2, gamma 1.4, cfl 0.5, 2 limiter passes,
@@ -160,10 +162,12 @@ eh_status eh_trace(eh_ctx *ctx, int what, double *host_out, int64_t count);
  * While enabled, eh_step/eh_stage/eh_run launch eagerly (no graph) and record
  * an event pair around every kernel. eh_profile_read returns, for one kernel
  * kind (EH_KERNEL_*), the summed duration in milliseconds and the number of
- * launches since profiling was enabled (synchronises). */
+ * launches since profiling was enabled (synchronises). EH_KERNEL_VISC covers
+ * the viscosity and indicator kernels; EH_KERNEL_LSEARCH the line searches that
+ * the limiter passes left to a separate kernel (Sec. 3.3). */
 enum {
   EH_KERNEL_PREP = 0, EH_KERNEL_VISC = 1, EH_KERNEL_LOW = 2, EH_KERNEL_TAU = 3, EH_KERNEL_LIM1 = 4,
-  EH_KERNEL_PASS = 5, EH_KERNEL_FINAL = 6, EH_KERNEL_COUNT = 7
+  EH_KERNEL_PASS = 5, EH_KERNEL_FINAL = 6, EH_KERNEL_LSEARCH = 7, EH_KERNEL_COUNT = 8
 };
 eh_status eh_profile_enable(eh_ctx *ctx, int enable);
 eh_status eh_profile_read(eh_ctx *ctx, int kernel, double *total_ms, int64_t *launches);

@@ -36,7 +36,7 @@ EXPORTS = ("eh_config_default", "eh_create", "eh_upload_mesh", "eh_set_state", "
            "eh_last_error", "eh_status_string", "eh_destroy", "eh_cfl_dt_noalloc", "eh_set_instances",
            "eh_get_instances", "eh_autotune", "eh_get_block_sizes")
 CFL_NOALLOC_MAX_ROWS = 1 << 23
-KERNEL_NAMES = ("prep", "visc", "low", "tau", "lim1", "pass", "final")
+KERNEL_NAMES = ("prep", "visc", "low", "tau", "lim1", "pass", "final", "lsearch")
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -64,7 +64,7 @@ class Config(ctypes.Structure):
 class Diagnostics(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_int64), ("last_dt", ctypes.c_double),
                 ("last_stage_bound", ctypes.c_double * 3), ("cfl_violations", ctypes.c_int64),
-                ("not_admissible", ctypes.c_int64)]
+                ("not_admissible", ctypes.c_int64), ("line_searches_deferred", ctypes.c_int64)]
 
 
 _lib = None
@@ -239,7 +239,8 @@ class Solver:
         d = Diagnostics()
         self._check(self.lib.eh_get_diagnostics(self.ctx, ctypes.byref(d)), "eh_get_diagnostics")
         return dict(t=d.t, steps=d.steps, last_dt=d.last_dt, last_stage_bound=list(d.last_stage_bound),
-                    cfl_violations=d.cfl_violations, not_admissible=d.not_admissible)
+                    cfl_violations=d.cfl_violations, not_admissible=d.not_admissible,
+                    line_searches_deferred=d.line_searches_deferred)
 
     def trace(self, what):
         sizes = {EH_TRACE_D_IJ: self.nnz, EH_TRACE_ALPHA: self.n, EH_TRACE_U_LOW: self.S * self.n,

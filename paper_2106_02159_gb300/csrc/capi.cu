@@ -37,7 +37,6 @@ struct eh_ctx {
   DevStatus *st = nullptr;
   DevStatus *st_host = nullptr;  // pinned
   // host bookkeeping
-  double t = 0.0;
   int64_t steps = 0;
   double last_dt = 0.0;
   bool last_stage_traced = false;
@@ -51,7 +50,7 @@ struct eh_ctx {
   double prof_ms[EH_KERNEL_COUNT] = {0};
   int64_t prof_count[EH_KERNEL_COUNT] = {0};
   // block size (rows per block) of every kernel kind
-  int tpb[EH_KERNEL_COUNT] = {128, 128, 128, 1024, 128, 128, 128};
+  int tpb[EH_KERNEL_COUNT] = {128, 128, 128, 1024, 128, 128, 128, 256};
   // independent instances
   int ninst = 1;
   std::vector<void *> inst_allocs;
@@ -191,15 +190,23 @@ void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, con
   }
   { ProfScope ps(c, EH_KERNEL_LOW); launch_low<DIM, T>(m, p, w, tpb[EH_KERNEL_LOW], s); }
   { ProfScope ps(c, EH_KERNEL_TAU); launch_tau(m, w, stage, dt_given, p.cfl, !trace, s); }
-  { ProfScope ps(c, EH_KERNEL_LIM1); launch_lim1<DIM, T>(m, p, w, tpb[EH_KERNEL_LIM1], s); }
+  {
+    ProfScope ps(c, EH_KERNEL_LIM1);
+    launch_lim1<DIM, T>(m, p, w, tpb[EH_KERNEL_LIM1], s);
+  }
+  { ProfScope ps(c, EH_KERNEL_LSEARCH); launch_ls_deferred<DIM>(m, p, w, w.UL, 0, w.la, tpb[EH_KERNEL_LSEARCH], s); }
   const double *ucur = w.UL;
   double *lcur = w.la, *lnext = w.lb;
   double *unext = w.Ua;
   for (int pass = 1; pass < c->cfg.limiter_passes; ++pass) {
     {
       ProfScope ps(c, EH_KERNEL_PASS);
-      launch_pass<DIM>(m, p, w, ucur, unext, lcur, lnext, (trace && pass == 1) ? c->trace_lsym : nullptr,
+      launch_pass<DIM>(m, p, w, ucur, unext, lcur, lnext, (trace && pass == 1) ? c->trace_lsym : nullptr, pass,
                        tpb[EH_KERNEL_PASS], s);
+    }
+    {
+      ProfScope ps(c, EH_KERNEL_LSEARCH);
+      launch_ls_deferred<DIM>(m, p, w, unext, pass, lnext, tpb[EH_KERNEL_LSEARCH], s);
     }
     if (trace && pass == 1) {
       cudaMemcpyAsync(c->trace_upass, unext, sizeof(double) * (size_t)c->n * SP_of(c), cudaMemcpyDeviceToDevice, s);
@@ -543,6 +550,9 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   ALLOC(w.P, (size_t)nnz * SP);
   ALLOC(w.la, nnz);
   ALLOC(w.lb, nnz);
+  ALLOC(w.lsq, nnz);  // every entry can be queued once per pass
+  ALLOC(w.lsq_count, LSQ_SLOTS);
+  w.lsq_cap = (unsigned)nnz;
   ALLOC(c->Usave, (size_t)S * n);
   ALLOC(c->U, (size_t)S * n);
   ALLOC(c->W, (size_t)S * n);
@@ -572,6 +582,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   if (e == cudaSuccess) e = up(d_bkind, bnd_kind, sizeof(int32_t) * n_bnd);
   if (e == cudaSuccess) e = up(d_bnorm, bnd_normal, sizeof(double) * dim * n_bnd);
   if (e == cudaSuccess && bnd_state) e = up(d_bstate, bnd_state, sizeof(double) * S * n_bnd);
+  if (e == cudaSuccess) e = cudaMemset(w.lsq_count, 0, sizeof(unsigned) * LSQ_SLOTS);
   if (e == cudaSuccess && f_cij) {
     std::vector<float> tmp((size_t)dim * nnz);
     for (size_t q = 0; q < tmp.size(); ++q) tmp[q] = (float)cij[q];
@@ -614,7 +625,6 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
     return st;
   }
   c->have_mesh = true;
-  c->t = 0.0;
   c->steps = 0;
   return EH_OK;
 }
@@ -706,7 +716,6 @@ eh_status eh_step(eh_ctx *c, double dt, double *dt_used) {
     if ((st = check_device_error(c))) return st;
     *dt_used = c->st_host->tau;
     c->last_dt = *dt_used;
-    c->t += *dt_used;
   }
   return EH_OK;
 }
@@ -755,12 +764,15 @@ eh_status eh_get_diagnostics(eh_ctx *c, eh_diagnostics *out) {
   CUDA_TRY(c, cudaSetDevice(c->device));
   eh_status st = check_device_error(c);
   memset(out, 0, sizeof(*out));
-  out->t = c->t;
+  double t0 = 0.0;  // simulated time of instance 0, advanced on the device
+  CUDA_TRY(c, cudaMemcpy(&t0, c->wk.t_inst, sizeof(double), cudaMemcpyDeviceToHost));
+  out->t = t0;
   out->steps = c->steps;
   out->last_dt = c->st_host->tau;
   for (int q = 0; q < 3; ++q) out->last_stage_bound[q] = c->st_host->stage_bound[q];
   out->cfl_violations = (int64_t)c->st_host->cfl_violations;
   out->not_admissible = (int64_t)c->st_host->not_admissible;
+  out->line_searches_deferred = (int64_t)c->st_host->line_searches_deferred;
   return st;
 }
 
@@ -876,7 +888,9 @@ eh_status eh_get_block_sizes(const eh_ctx *c, int32_t *tpb) {
 int32_t eh_launches_per_step(const eh_ctx *c) {
   if (!c) return 0;
   // prep, visc, alpha, low, tau, lim1, (passes - 1) x pass, final; three stages
-  return 3 * (7 + (c->cfg.limiter_passes - 1));
+  // per stage: prep, visc, alpha, low, tau, lim1, final, one k_pass per
+  // further pass and one k_ls_deferred per pass
+  return 3 * (7 + (c->cfg.limiter_passes - 1) + c->cfg.limiter_passes);
 }
 
 eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {

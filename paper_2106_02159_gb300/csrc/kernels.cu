@@ -12,6 +12,9 @@
 // k_visc and reused by k_low; the limiter directions P_ij are stored.
 #include "kernels.cuh"
 
+#include <cooperative_groups.h>
+#include <cooperative_groups/scan.h>
+
 #include <cmath>
 #include <type_traits>
 
@@ -21,6 +24,30 @@ namespace eh {
 // (default 128, see eh_autotune), at most TPB_MAX
 
 __host__ __device__ inline unsigned nblocks(int64_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
+
+// ---------------------------------------------------------------------------
+// comparisons and min/max of doubles of known sign, on the bit patterns: a
+// non-negative double orders like its bit pattern read as a signed 64-bit
+// integer, and every negative double reads as a negative integer. An FP64
+// compare or min/max issues on the FP64 pipe (2 lanes per SM and clock on
+// GB300); the integer form runs on the ALUs. No operand is NaN on these paths.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// x > y and x < y for y > 0, x of either sign
+__device__ __forceinline__ bool gt_pos(double x, double y) { return dbits(x) > dbits(y); }
+__device__ __forceinline__ bool lt_pos(double x, double y) { return dbits(x) < dbits(y); }
+// an integer key with the order of the doubles (either sign)
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = dbits(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+// max(x, 0); a > b and max(a, b) for a, b >= 0 (FP32: the plain instructions)
+__device__ __forceinline__ double pos_part(double x) { return dbits(x) > 0 ? x : 0.0; }
+__device__ __forceinline__ float pos_part(float x) { return fmaxf(x, 0.0f); }
+__device__ __forceinline__ bool gt_nonneg(double a, double b) { return dbits(a) > dbits(b); }
+__device__ __forceinline__ bool gt_nonneg(float a, float b) { return a > b; }
+__device__ __forceinline__ double max_nonneg(double a, double b) { return dbits(a) > dbits(b) ? a : b; }
+__device__ __forceinline__ float max_nonneg(float a, float b) { return fmaxf(a, b); }
 
 // ---------------------------------------------------------------------------
 // roots and powers for gamma = 7/5 (division-free Newton iterations from an
@@ -81,7 +108,7 @@ template <typename T>
 __device__ __forceinline__ T lambda_max(const Params &p, T unl, T pl, T al, T azl, T ipl, T unr, T pr, T ar, T azr,
                                         T ipr) {
   T num = al + ar - T(0.5) * T(p.gm1) * (unr - unl);
-  num = fmax(num, T(0));
+  num = pos_part(num);
   T x = num / (azl + azr);
   T ptr;
   if (p.gamma75) {
@@ -92,11 +119,11 @@ __device__ __forceinline__ T lambda_max(const Params &p, T unl, T pl, T al, T az
     ptr = pow(x, T(p.inv_z));
   }
   const T ks = T(p.kshock);
-  T sl = ptr > pl ? sqrt(T(1) + ks * (ptr - pl) * ipl) : T(1);
-  T sr = ptr > pr ? sqrt(T(1) + ks * (ptr - pr) * ipr) : T(1);
+  T sl = gt_nonneg(ptr, pl) ? sqrt(T(1) + ks * (ptr - pl) * ipl) : T(1);
+  T sr = gt_nonneg(ptr, pr) ? sqrt(T(1) + ks * (ptr - pr) * ipr) : T(1);
   T lam1 = unl - al * sl;
   T lam3 = unr + ar * sr;
-  return fmax(fmax(-lam1, T(0)), fmax(lam3, T(0)));
+  return max_nonneg(pos_part(-lam1), pos_part(lam3));
 }
 
 // ---------------------------------------------------------------------------
@@ -200,6 +227,71 @@ __device__ double line_search(const Params &p, const double *ub, const double *P
     }
   }
   return lL;
+}
+
+// The common outcome of the line search, decided with a short branch-free
+// sequence: P = 0, or l = 1 inside the density bounds and (gamma = 7/5) inside
+// the entropy bound. Returns true exactly where line_search returns 1 through
+// one of these exits; false leaves the entry to the full search. (A warp whose
+// lanes took the search's other exits -- density clipping, psi evaluations,
+// the secant/Newton loop -- inline would issue each of them for all 32 lanes.)
+template <int DIM>
+__device__ __forceinline__ bool line_search_at_one(const Params &p, const double *ub, const double *P, double rmin,
+                                                   double rmax, double phimin5) {
+  constexpr int S = DIM + 2;
+  bool zero = true;
+#pragma unroll
+  for (int s = 0; s < S; ++s) zero &= (__double_as_longlong(P[s]) << 1) == 0;
+  if (zero) return true;
+  if (!p.gamma75) return false;
+  // the compares below run on the bit patterns (all thresholds are positive);
+  // rp = -0 may take the density test, which can only send the entry to the
+  // full search
+  const double rb = ub[0], rp = P[0];
+  if (dbits(rp) > 0) {
+    if (gt_pos(rb + rp, rmax)) return false;
+  } else if (dbits(rp) < 0) {
+    if (lt_pos(rb + rp, rmin)) return false;
+  }
+  double u[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) u[s] = ub[s] + P[s];
+  const double rho = u[0];
+  if (!(gt_pos(rho, 1e-6) && lt_pos(rho, 1e6))) return false;
+  double m2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) m2 += u[1 + q] * u[1 + q];
+  const double er = u[S - 1] * rho - 0.5 * m2;
+  if (!(dbits(er) > 0)) return false;
+  const double r2 = rho * rho, r4 = r2 * r2, r12 = r4 * r4 * r4;
+  const double e2 = er * er;
+  const double lhs = e2 * e2 * er, rhs = phimin5 * r12;  // lhs > 0, rhs >= 0
+  return lt_pos(rhs, 1e300) && dbits(lhs) >= dbits(rhs);
+}
+
+// Queues the line searches of row i's entries k0 + b for every bit b of 'mask'
+// for k_ls_deferred: one atomic per group of converged lanes (normally once
+// per warp and kernel). The queue holds nnz entries and a pass queues each
+// entry at most once, so it cannot fill; the bounds check only guards memory
+// (an overflow would be reported as EH_ERR_STATE).
+__device__ __forceinline__ void defer_line_searches(const Work &w, int slot, int i, int64_t k0, uint64_t mask) {
+  namespace cg = cooperative_groups;
+  cg::coalesced_group g = cg::coalesced_threads();
+  const unsigned cnt = (unsigned)__popcll(mask);
+  const unsigned off = cg::exclusive_scan(g, cnt);
+  const unsigned total = g.shfl(off + cnt, g.size() - 1);
+  if (total == 0) return;
+  unsigned base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(&w.lsq_count[slot], total);
+  base = g.shfl(base, 0) + off;
+  while (mask) {
+    const int b = __ffsll((long long)mask) - 1;
+    mask &= mask - 1;
+    if (base < w.lsq_cap)
+      w.lsq[base++] = make_int2(i, (int)(k0 + b));
+    else
+      atomicExch(&w.st->err, 7);  // EH_ERR_STATE
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -381,7 +473,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
         uni += vi[q] * nq;
       }
       T dji = lambda_max<T>(p, unj, Rj[R::P], Rj[R::A], Rj[R::AZ], Rj[R::IP], uni, pi, ai, azi, ipi) * cn[kt];
-      dij = fmax(dij, dji);
+      dij = max_nonneg(dij, dji);
     }
     darr[k] = dij;
     darr[kt] = dij;
@@ -489,14 +581,16 @@ __global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
         fh[s] += dH * (T)du;
         wsum[s] += ws;
       }
-      if (dk > 0.0) {
+      if (dbits(dk) > 0) {  // dk >= 0
         const double num = dk * (ui[0] + Rj[0]) - w0;
         const double den = 2.0 * dk;
-        if (num * dmin < nmin * den) {
+        const long long knew_min = order_key(num * dmin), kmin = order_key(nmin * den);
+        const long long knew_max = order_key(num * dmax), kmax = order_key(nmax * den);
+        if (knew_min < kmin) {
           nmin = num;
           dmin = den;
         }
-        if (num * dmax > nmax * den) {
+        if (knew_max > kmax) {
           nmax = num;
           dmax = den;
         }
@@ -560,6 +654,7 @@ __global__ void __launch_bounds__(256) k_tau(MeshView m, Work w, int stage, doub
                                              int advance_time) {
   DevStatus *st = w.st;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < LSQ_SLOTS) w.lsq_count[k] = 0;  // the stage's deferred line searches start empty
   if (k >= m.ninst || st->err) return;
   const double bound = __longlong_as_double((long long)w.bound_bits[k]);
   w.bound_bits[k] = kInfBits;
@@ -620,6 +715,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_lim1(MeshView m, Params p, Work w) 
   const double alphai = w.alpha[i];
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
   const double coef = tau * (double)(k1 - k0 - 1) * m.inv_mi[i];
+  uint64_t defer = 0;  // entries whose line search goes to k_ls_deferred
   for (int64_t k = k0; k < k1; ++k) {
     const int j = m.col[k];
     double *Pk = w.P + k * SP;
@@ -640,8 +736,14 @@ __global__ void __launch_bounds__(TPB_MAX) k_lim1(MeshView m, Params p, Work w) 
       P[s] = coef * (-b * (double)FHj[s] + bt * fhi[s] + (dH - dk) * (Rj[s] - ui[s]));
       Pk[s] = P[s];
     }
-    w.la[k] = line_search<DIM>(p, ul, P, rmin, rmax, phimin, phimin5);
+    if (line_search_at_one<DIM>(p, ul, P, rmin, rmax, phimin5))
+      w.la[k] = 1.0;
+    else if (k - k0 < 64)
+      defer |= 1ull << (k - k0);
+    else
+      defer_line_searches(w, 0, i, k, 1ull);  // rows longer than 64 entries
   }
+  defer_line_searches(w, 0, i, k0, defer);
 }
 
 // min of two limiters in [0, 1]: non-negative doubles order like their bit
@@ -657,7 +759,7 @@ __device__ __forceinline__ double lmin(double a, double b) {
 template <int DIM>
 __global__ void __launch_bounds__(TPB_MAX) k_pass(MeshView m, Params p, Work w, const double *__restrict__ Uin,
                                               double *__restrict__ Uout, const double *__restrict__ lin,
-                                              double *__restrict__ lout, double *lsym_trace) {
+                                              double *__restrict__ lout, double *lsym_trace, int slot) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -685,6 +787,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_pass(MeshView m, Params p, Work w, 
   const double *bi = w.bounds + (int64_t)i * 4;
   const double rmin = bi[0], rmax = bi[1], phimin = bi[2];
   const double phimin2 = phimin * phimin, phimin5 = phimin2 * phimin2 * phimin;
+  uint64_t defer = 0;
   for (int64_t k = k0; k < k1; ++k) {
     if (m.col[k] == i) {
       lout[k] = 1.0;
@@ -698,7 +801,39 @@ __global__ void __launch_bounds__(TPB_MAX) k_pass(MeshView m, Params p, Work w, 
       P[s] = (1.0 - l) * Pk[s];
       Pk[s] = P[s];
     }
-    lout[k] = line_search<DIM>(p, u, P, rmin, rmax, phimin, phimin5);
+    if (line_search_at_one<DIM>(p, u, P, rmin, rmax, phimin5))
+      lout[k] = 1.0;
+    else if (k - k0 < 64)
+      defer |= 1ull << (k - k0);
+    else
+      defer_line_searches(w, slot, i, k, 1ull);
+  }
+  defer_line_searches(w, slot, i, k0, defer);
+}
+
+// ---------------------------------------------------------------------------
+// k_ls_deferred: the queued line searches of one pass, one per thread, from
+// the pass's start state ub, the stored P_ij and the row's bounds
+// ---------------------------------------------------------------------------
+template <int DIM>
+__global__ void __launch_bounds__(256) k_ls_deferred(MeshView m, Params p, Work w, const double *__restrict__ ub,
+                                                     int slot, double *__restrict__ lout) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  if (w.st->err) return;
+  const unsigned cnt = min(w.lsq_count[slot], w.lsq_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.st->line_searches_deferred, (unsigned long long)cnt);
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+    const int2 it = w.lsq[q];
+    const double *bi = w.bounds + (int64_t)it.x * 4;
+    const double phimin = bi[2], phimin2 = phimin * phimin, phimin5 = phimin2 * phimin2 * phimin;
+    double u[S], P[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      u[s] = ub[(int64_t)it.x * SP + s];
+      P[s] = w.P[(int64_t)it.y * SP + s];
+    }
+    lout[it.y] = line_search<DIM>(p, u, P, bi[0], bi[1], phimin, phimin5);
   }
 }
 
@@ -823,8 +958,15 @@ void launch_lim1(const MeshView &m, const Params &p, const Work &w, int tpb, cud
 }
 template <int DIM>
 void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
-                 double *lout, double *lsym_trace, int tpb, cudaStream_t s) {
-  k_pass<DIM><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w, Uin, Uout, lin, lout, lsym_trace);
+                 double *lout, double *lsym_trace, int slot, int tpb, cudaStream_t s) {
+  k_pass<DIM><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w, Uin, Uout, lin, lout, lsym_trace, slot);
+}
+template <int DIM>
+void launch_ls_deferred(const MeshView &m, const Params &p, const Work &w, const double *ub, int slot, double *lout,
+                        int tpb, cudaStream_t s) {
+  // a fixed grid (1024 threads per SM of a 152-SM GB300) that strides over
+  // however many searches were queued; the count stays on the device
+  k_ls_deferred<DIM><<<152 * 1024 / tpb, tpb, 0, s>>>(m, p, w, ub, slot, lout);
 }
 template <int DIM>
 void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,
@@ -852,7 +994,9 @@ EH_INSTANTIATE_T(3, float)
 
 #define EH_INSTANTIATE(DIM)                                                                                          \
   template void launch_pass<DIM>(const MeshView &, const Params &, const Work &, const double *, double *,            \
-                                 const double *, double *, double *, int, cudaStream_t);                              \
+                                 const double *, double *, double *, int, int, cudaStream_t);                         \
+  template void launch_ls_deferred<DIM>(const MeshView &, const Params &, const Work &, const double *, int, double *, \
+                                        int, cudaStream_t);                                                          \
   template void launch_final<DIM>(const MeshView &, const Params &, const Work &, const double *, const double *,     \
                                   const double *, double, double *, double *, int, cudaStream_t);                     \
   template void launch_apply_bc<DIM>(const MeshView &, double *, cudaStream_t);                                       \

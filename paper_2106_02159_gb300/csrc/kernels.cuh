@@ -41,6 +41,7 @@ struct DevStatus {
   double stage_bound[3];         // c_cfl min_i m_i/(2|d_ii|) of the three stages
   unsigned long long cfl_violations;
   unsigned long long not_admissible;
+  unsigned long long line_searches_deferred;  // searches the l = 1 check left open (cumulative)
 };
 
 struct MeshView {
@@ -112,7 +113,13 @@ struct Work {
   void *vd;        // [nnz]
   void *va;        // [nnz]      (q(U_j) - q(U_i)) . c_ij of the indicator
   void *vFH;       // [n][SP]
+  // line searches that the fast check at l = 1 left open, run by
+  // k_ls_deferred after each limiter pass (one queue, reused by every pass)
+  int2 *lsq;             // [lsq_cap] (row i, entry k)
+  unsigned *lsq_count;   // [LSQ_SLOTS] entries queued by pass 0, 1, ... of the stage (zeroed by k_tau)
+  unsigned lsq_cap;
 };
+constexpr int LSQ_SLOTS = 8;  // limiter passes per stage, at most
 
 // Launchers (all asynchronous on 'stream'). T is the precision of the
 // viscosity / high-order-flux part: double (FP64 mode) or float (mixed mode).
@@ -134,7 +141,12 @@ template <int DIM, typename T>
 void launch_lim1(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s);
 template <int DIM>
 void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
-                 double *lout, double *lsym_trace, int tpb, cudaStream_t s);
+                 double *lout, double *lsym_trace, int slot, int tpb, cudaStream_t s);
+// the queued line searches of pass 'slot' from the states ub ([n][SP]) and the
+// stored P_ij; writes their limiters to lout
+template <int DIM>
+void launch_ls_deferred(const MeshView &m, const Params &p, const Work &w, const double *ub, int slot, double *lout,
+                        int tpb, cudaStream_t s);
 // out = SSP combination of U0 and BC(Uin + sum lambda l P): coef < 0 -> out = BC(...),
 // else out = U0 + coef (BC(...) - U0). U0 / out are component-major [S][n].
 template <int DIM>
