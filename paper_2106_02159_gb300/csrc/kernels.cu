@@ -48,6 +48,11 @@ __device__ __forceinline__ bool gt_nonneg(double a, double b) { return dbits(a) 
 __device__ __forceinline__ bool gt_nonneg(float a, float b) { return a > b; }
 __device__ __forceinline__ double max_nonneg(double a, double b) { return dbits(a) > dbits(b) ? a : b; }
 __device__ __forceinline__ float max_nonneg(float a, float b) { return fmaxf(a, b); }
+// |x| by clearing the sign bit
+__device__ __forceinline__ double abs_bits(double x) {
+  return __longlong_as_double(dbits(x) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ float abs_bits(float x) { return fabsf(x); }
 
 // ---------------------------------------------------------------------------
 // roots and powers for gamma = 7/5 (division-free Newton iterations from an
@@ -162,6 +167,80 @@ __device__ __forceinline__ double dpsi(const Params &p, const double *ub, const 
 
 constexpr int LINE_SEARCH_ITERATIONS = 6;
 
+// gamma = 7/5: psi(l) as psi() above, also returning r = rho(l)^(-1/5), so
+// that psi'(lR) reuses the root of the psi(lR) evaluation (rho^(2/5) = rho r^3);
+// the values are those of psi()/dpsi() bit for bit.
+template <int DIM>
+__device__ __forceinline__ double psi_g75(const double *ub, const double *P, double l, double phimin, double *r_out) {
+  constexpr int S = DIM + 2;
+  double u[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) u[s] = ub[s] + l * P[s];
+  double m2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) m2 += u[1 + k] * u[1 + k];
+  const double eps = u[S - 1] - m2 / (2.0 * u[0]);
+  const double r = rroot5(u[0]);
+  *r_out = r;
+  return eps - phimin * (u[0] * u[0] * (r * r * r));
+}
+
+template <int DIM>
+__device__ __forceinline__ double dpsi_g75(const double *ub, const double *P, double l, double r, double phimin) {
+  constexpr int S = DIM + 2;
+  double u[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) u[s] = ub[s] + l * P[s];
+  const double irho = 1.0 / u[0];
+  double v2 = 0.0, vP = 0.0;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    const double v = u[1 + k] * irho;
+    v2 += v * v;
+    vP += v * P[1 + k];
+  }
+  const double deps = P[S - 1] - vP + 0.5 * v2 * P[0];
+  return deps - phimin * 1.4 * (u[0] * (r * r * r)) * P[0];
+}
+
+// The entropy part of the line search for gamma = 7/5 from l (the density
+// limit): the iteration of line_search below, with the root of rho shared
+// between psi(lR) and psi'(lR), and psi evaluated once when the Newton and
+// secant points coincide.
+template <int DIM>
+__device__ double entropy_search_g75(const double *ub, const double *P, double l, double phimin) {
+  double rR, r0;
+  double pr = psi_g75<DIM>(ub, P, l, phimin, &rR);
+  if (pr >= 0.0) return l;
+  double pl = psi_g75<DIM>(ub, P, 0.0, phimin, &r0);
+  if (pl <= 0.0) return 0.0;
+  double lL = 0.0, lR = l;
+  for (int it = 0; it < LINE_SEARCH_ITERATIONS; ++it) {
+    double ls = lL + pl * (lR - lL) / (pl - pr);
+    double dr = dpsi_g75<DIM>(ub, P, lR, rR, phimin);
+    double ln = dr < 0.0 ? lR - pr / dr : lR;
+    if (ln < ls) ln = ls;
+    double rs, rn;
+    double ps = psi_g75<DIM>(ub, P, ls, phimin, &rs);
+    double pn = ps;
+    rn = rs;
+    if (ln != ls) pn = psi_g75<DIM>(ub, P, ln, phimin, &rn);
+    if (ps >= 0.0) {
+      lL = ls;
+      pl = ps;
+    }
+    if (pn < 0.0) {
+      lR = ln;
+      pr = pn;
+      rR = rn;
+    } else {
+      lL = ln;
+      pl = pn;
+    }
+  }
+  return lL;
+}
+
 // phimin5 = phimin^5 (used by the gamma = 7/5 fast check only).
 template <int DIM>
 __device__ double line_search(const Params &p, const double *ub, const double *P, double rmin, double rmax,
@@ -202,6 +281,7 @@ __device__ double line_search(const Params &p, const double *ub, const double *P
       }
     }
   }
+  if (p.gamma75) return entropy_search_g75<DIM>(ub, P, l, phimin);
   double pr = psi<DIM>(p, ub, P, l, phimin);
   if (pr >= 0.0) return l;
   double pl = psi<DIM>(p, ub, P, 0.0, phimin);
@@ -519,7 +599,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_alpha(MeshView m, Params p, Work w)
 #pragma unroll
     for (int s = 0; s < S; ++s) b_ += deta[s] * wk[s];
     N += a_ - b_;
-    D += fabs(a_) + fabs(b_);
+    D += abs_bits(a_) + abs_bits(b_);
   }
   w.alpha[i] = D > T(0) ? (double)(fabs(N) / D) : 0.0;
 }
