@@ -74,6 +74,7 @@ typedef struct {
   int64_t not_admissible;     /* non-admissible nodes found after a step (0 unless an error) */
   int64_t line_searches_deferred; /* limiter line searches (Sec. 3.3) not settled by the check at
                                      l = 1 and run in a separate pass, summed over all steps */
+  int64_t line_searches_iterated; /* of those, searches that ran the bracketing iteration */
 } eh_diagnostics;
 
 /* Fills *cfg with the defaults: dim 2, gamma 1.4, cfl 0.5, 2 limiter passes,

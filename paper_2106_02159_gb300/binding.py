@@ -64,7 +64,8 @@ class Config(ctypes.Structure):
 class Diagnostics(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_int64), ("last_dt", ctypes.c_double),
                 ("last_stage_bound", ctypes.c_double * 3), ("cfl_violations", ctypes.c_int64),
-                ("not_admissible", ctypes.c_int64), ("line_searches_deferred", ctypes.c_int64)]
+                ("not_admissible", ctypes.c_int64), ("line_searches_deferred", ctypes.c_int64),
+                ("line_searches_iterated", ctypes.c_int64)]
 
 
 _lib = None
@@ -240,7 +241,8 @@ class Solver:
         self._check(self.lib.eh_get_diagnostics(self.ctx, ctypes.byref(d)), "eh_get_diagnostics")
         return dict(t=d.t, steps=d.steps, last_dt=d.last_dt, last_stage_bound=list(d.last_stage_bound),
                     cfl_violations=d.cfl_violations, not_admissible=d.not_admissible,
-                    line_searches_deferred=d.line_searches_deferred)
+                    line_searches_deferred=d.line_searches_deferred,
+                    line_searches_iterated=d.line_searches_iterated)
 
     def trace(self, what):
         sizes = {EH_TRACE_D_IJ: self.nnz, EH_TRACE_ALPHA: self.n, EH_TRACE_U_LOW: self.S * self.n,

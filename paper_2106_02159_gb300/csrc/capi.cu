@@ -553,6 +553,11 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   ALLOC(w.lsq, nnz);  // every entry can be queued once per pass
   ALLOC(w.lsq_count, LSQ_SLOTS);
   w.lsq_cap = (unsigned)nnz;
+  // iterations: a small share of the searches; a full queue falls back to
+  // iterating in k_ls_deferred
+  w.lsq2_cap = (unsigned)std::max<int64_t>(nnz / 8, 4096);
+  ALLOC(w.lsq2, w.lsq2_cap);
+  ALLOC(w.lsq2_count, LSQ_SLOTS);
   ALLOC(c->Usave, (size_t)S * n);
   ALLOC(c->U, (size_t)S * n);
   ALLOC(c->W, (size_t)S * n);
@@ -583,6 +588,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   if (e == cudaSuccess) e = up(d_bnorm, bnd_normal, sizeof(double) * dim * n_bnd);
   if (e == cudaSuccess && bnd_state) e = up(d_bstate, bnd_state, sizeof(double) * S * n_bnd);
   if (e == cudaSuccess) e = cudaMemset(w.lsq_count, 0, sizeof(unsigned) * LSQ_SLOTS);
+  if (e == cudaSuccess) e = cudaMemset(w.lsq2_count, 0, sizeof(unsigned) * LSQ_SLOTS);
   if (e == cudaSuccess && f_cij) {
     std::vector<float> tmp((size_t)dim * nnz);
     for (size_t q = 0; q < tmp.size(); ++q) tmp[q] = (float)cij[q];
@@ -773,6 +779,7 @@ eh_status eh_get_diagnostics(eh_ctx *c, eh_diagnostics *out) {
   out->cfl_violations = (int64_t)c->st_host->cfl_violations;
   out->not_admissible = (int64_t)c->st_host->not_admissible;
   out->line_searches_deferred = (int64_t)c->st_host->line_searches_deferred;
+  out->line_searches_iterated = (int64_t)c->st_host->line_searches_iterated;
   return st;
 }
 
@@ -889,8 +896,8 @@ int32_t eh_launches_per_step(const eh_ctx *c) {
   if (!c) return 0;
   // prep, visc, alpha, low, tau, lim1, (passes - 1) x pass, final; three stages
   // per stage: prep, visc, alpha, low, tau, lim1, final, one k_pass per
-  // further pass and one k_ls_deferred per pass
-  return 3 * (7 + (c->cfg.limiter_passes - 1) + c->cfg.limiter_passes);
+  // further pass and k_ls_deferred + k_ls_iterate per pass
+  return 3 * (7 + (c->cfg.limiter_passes - 1) + 2 * c->cfg.limiter_passes);
 }
 
 eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {

@@ -48,6 +48,11 @@ __device__ __forceinline__ bool gt_nonneg(double a, double b) { return dbits(a) 
 __device__ __forceinline__ bool gt_nonneg(float a, float b) { return a > b; }
 __device__ __forceinline__ double max_nonneg(double a, double b) { return dbits(a) > dbits(b) ? a : b; }
 __device__ __forceinline__ float max_nonneg(float a, float b) { return fmaxf(a, b); }
+// x > 0 and x < 0 (strict: false for both zeros)
+__device__ __forceinline__ bool pos_strict(double x) { return dbits(x) > 0; }
+__device__ __forceinline__ bool neg_strict(double x) { return dbits(x) < 0 && (dbits(x) << 1) != 0; }
+// min(max(x, 0), 1)
+__device__ __forceinline__ double clamp01(double x) { return dbits(x) <= 0 ? 0.0 : (gt_pos(x, 1.0) ? 1.0 : x); }
 // |x| by clearing the sign bit
 __device__ __forceinline__ double abs_bits(double x) {
   return __longlong_as_double(dbits(x) & 0x7FFFFFFFFFFFFFFFLL);
@@ -61,7 +66,7 @@ __device__ __forceinline__ float abs_bits(float x) { return fabsf(x); }
 
 // x^(-1/5): Newton's method on r^-5 = x, r <- r (6 - x r^5) / 5.
 __device__ __forceinline__ double rroot5(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return pow(x, -0.2);
+  if (!(gt_pos(x, 1e-30) && lt_pos(x, 1e30))) return pow(x, -0.2);
   double r = (double)exp2f(-0.2f * log2f((float)x));
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
@@ -74,7 +79,7 @@ __device__ __forceinline__ double rroot5(double x) {
 
 // x^(-1/7): Newton's method on r^-7 = x, r <- r (8 - x r^7) / 7.
 __device__ __forceinline__ double rroot7(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return pow(x, -1.0 / 7.0);
+  if (!(gt_pos(x, 1e-30) && lt_pos(x, 1e30))) return pow(x, -1.0 / 7.0);
   double r = (double)exp2f((-1.0f / 7.0f) * log2f((float)x));
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
@@ -203,104 +208,107 @@ __device__ __forceinline__ double dpsi_g75(const double *ub, const double *P, do
   return deps - phimin * 1.4 * (u[0] * (r * r * r)) * P[0];
 }
 
-// The entropy part of the line search for gamma = 7/5 from l (the density
-// limit): the iteration of line_search below, with the root of rho shared
-// between psi(lR) and psi'(lR), and psi evaluated once when the Newton and
-// secant points coincide.
-template <int DIM>
-__device__ double entropy_search_g75(const double *ub, const double *P, double l, double phimin) {
-  double rR, r0;
-  double pr = psi_g75<DIM>(ub, P, l, phimin, &rR);
-  if (pr >= 0.0) return l;
-  double pl = psi_g75<DIM>(ub, P, 0.0, phimin, &r0);
-  if (pl <= 0.0) return 0.0;
-  double lL = 0.0, lR = l;
-  for (int it = 0; it < LINE_SEARCH_ITERATIONS; ++it) {
-    double ls = lL + pl * (lR - lL) / (pl - pr);
-    double dr = dpsi_g75<DIM>(ub, P, lR, rR, phimin);
-    double ln = dr < 0.0 ? lR - pr / dr : lR;
-    if (ln < ls) ln = ls;
-    double rs, rn;
-    double ps = psi_g75<DIM>(ub, P, ls, phimin, &rs);
-    double pn = ps;
-    rn = rs;
-    if (ln != ls) pn = psi_g75<DIM>(ub, P, ln, phimin, &rn);
-    if (ps >= 0.0) {
-      lL = ls;
-      pl = ps;
-    }
-    if (pn < 0.0) {
-      lR = ln;
-      pr = pn;
-      rR = rn;
-    } else {
-      lL = ln;
-      pl = pn;
-    }
-  }
-  return lL;
-}
+// The line search in two parts. line_search_start takes every exit that needs
+// no iteration (P = 0, the density limit, the entropy bound met at that limit,
+// psi(0) <= 0) and otherwise returns the bracket [0, l] with psi at both ends;
+// line_search_iterate runs the fixed number of secant (feasible side) / Newton
+// (infeasible side) steps on that bracket and returns its feasible end. For
+// gamma = 7/5 the root of rho is shared between psi(lR) and psi'(lR), and psi
+// is evaluated once when the Newton and secant points coincide.
+struct LsBracket {
+  double l;   // the result when done; else the right end of the bracket
+  double pl;  // psi(0) > 0
+  double pr;  // psi(l) < 0
+  double rR;  // rho(l)^(-1/5) (gamma = 7/5)
+  bool done;
+};
 
 // phimin5 = phimin^5 (used by the gamma = 7/5 fast check only).
 template <int DIM>
-__device__ double line_search(const Params &p, const double *ub, const double *P, double rmin, double rmax,
-                              double phimin, double phimin5) {
+__device__ LsBracket line_search_start(const Params &p, const double *ub, const double *P, double rmin, double rmax,
+                                       double phimin, double phimin5) {
   constexpr int S = DIM + 2;
+  LsBracket b{1.0, 0.0, 0.0, 0.0, true};
   // P = 0 (every edge whose previous limiter was 1, uniform flow): every l gives
   // the same state; the largest, 1, is returned without any FP64 work
   bool zero = true;
 #pragma unroll
   for (int s = 0; s < S; ++s) zero &= (__double_as_longlong(P[s]) << 1) == 0;
-  if (zero) return 1.0;
+  if (zero) return b;
+  // (compares on the bit patterns; the density bounds are positive)
   double l = 1.0;
   const double rb = ub[0], rp = P[0];
   // density: the division is needed only when l = 1 leaves [rho_min, rho_max]
-  if (rp > 0.0) {
-    if (rb + rp > rmax) l = fmin(l, (rmax - rb) / rp);
-  } else if (rp < 0.0) {
-    if (rb + rp < rmin) l = fmin(l, (rmin - rb) / rp);
+  if (pos_strict(rp)) {
+    if (gt_pos(rb + rp, rmax)) l = clamp01((rmax - rb) / rp);
+  } else if (neg_strict(rp)) {
+    if (lt_pos(rb + rp, rmin)) l = clamp01((rmin - rb) / rp);
   }
-  l = fmax(0.0, fmin(1.0, l));
-  // entropy at l: for gamma = 7/5, psi(l) >= 0 <=> (eps rho)^5 >= Phi_min^5 rho^12
-  // when eps rho > 0 -- no division and no root on the common path
+  b.l = l;
   if (p.gamma75) {
+    // entropy at l: psi(l) >= 0 <=> (eps rho)^5 >= Phi_min^5 rho^12 when
+    // eps rho > 0 -- no division and no root on the common path
     double u[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) u[s] = ub[s] + l * P[s];
     const double rho = u[0];
-    if (rho > 1e-6 && rho < 1e6) {
+    if (gt_pos(rho, 1e-6) && lt_pos(rho, 1e6)) {
       double m2 = 0.0;
 #pragma unroll
       for (int q = 0; q < DIM; ++q) m2 += u[1 + q] * u[1 + q];
       const double er = u[S - 1] * rho - 0.5 * m2;
-      if (er > 0.0) {
+      if (pos_strict(er)) {
         const double r2 = rho * rho, r4 = r2 * r2, r12 = r4 * r4 * r4;
         const double e2 = er * er;
-        const double lhs = e2 * e2 * er, rhs = phimin5 * r12;
-        if (rhs < 1e300 && lhs >= rhs) return l;
+        const double lhs = e2 * e2 * er, rhs = phimin5 * r12;  // lhs > 0, rhs >= 0
+        if (lt_pos(rhs, 1e300) && dbits(lhs) >= dbits(rhs)) return b;
       }
     }
+    double r0;
+    b.pr = psi_g75<DIM>(ub, P, l, phimin, &b.rR);
+    if (!neg_strict(b.pr)) return b;
+    b.pl = psi_g75<DIM>(ub, P, 0.0, phimin, &r0);
+  } else {
+    b.pr = psi<DIM>(p, ub, P, l, phimin);
+    if (!neg_strict(b.pr)) return b;
+    b.pl = psi<DIM>(p, ub, P, 0.0, phimin);
   }
-  if (p.gamma75) return entropy_search_g75<DIM>(ub, P, l, phimin);
-  double pr = psi<DIM>(p, ub, P, l, phimin);
-  if (pr >= 0.0) return l;
-  double pl = psi<DIM>(p, ub, P, 0.0, phimin);
-  if (pl <= 0.0) return 0.0;
-  double lL = 0.0, lR = l;
+  if (!pos_strict(b.pl)) {
+    b.l = 0.0;
+    return b;
+  }
+  b.done = false;
+  return b;
+}
+
+template <int DIM>
+__device__ double line_search_iterate(const Params &p, const double *ub, const double *P, double phimin,
+                                      const LsBracket &b) {
+  double lL = 0.0, lR = b.l, pl = b.pl, pr = b.pr, rR = b.rR;
   for (int it = 0; it < LINE_SEARCH_ITERATIONS; ++it) {
     double ls = lL + pl * (lR - lL) / (pl - pr);
-    double dr = dpsi<DIM>(p, ub, P, lR, phimin);
-    double ln = dr < 0.0 ? lR - pr / dr : lR;
-    if (ln < ls) ln = ls;
-    double ps = psi<DIM>(p, ub, P, ls, phimin);
-    double pn = psi<DIM>(p, ub, P, ln, phimin);
-    if (ps >= 0.0) {
+    double dr = p.gamma75 ? dpsi_g75<DIM>(ub, P, lR, rR, phimin) : dpsi<DIM>(p, ub, P, lR, phimin);
+    double ln = neg_strict(dr) ? lR - pr / dr : lR;
+    if (order_key(ln) < order_key(ls)) ln = ls;
+    double ps, pn, rs, rn;
+    if (p.gamma75) {
+      ps = psi_g75<DIM>(ub, P, ls, phimin, &rs);
+      pn = ps;
+      rn = rs;
+      if (dbits(ln) != dbits(ls)) pn = psi_g75<DIM>(ub, P, ln, phimin, &rn);
+    } else {
+      ps = psi<DIM>(p, ub, P, ls, phimin);
+      pn = psi<DIM>(p, ub, P, ln, phimin);
+      rn = 0.0;
+    }
+    if (!neg_strict(ps)) {
       lL = ls;
       pl = ps;
     }
-    if (pn < 0.0) {
+    if (neg_strict(pn)) {
       lR = ln;
       pr = pn;
+      rR = rn;
     } else {
       lL = ln;
       pl = pn;
@@ -734,7 +742,10 @@ __global__ void __launch_bounds__(256) k_tau(MeshView m, Work w, int stage, doub
                                              int advance_time) {
   DevStatus *st = w.st;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < LSQ_SLOTS) w.lsq_count[k] = 0;  // the stage's deferred line searches start empty
+  if (k < LSQ_SLOTS) {  // the stage's queued line searches start empty
+    w.lsq_count[k] = 0;
+    w.lsq2_count[k] = 0;
+  }
   if (k >= m.ninst || st->err) return;
   const double bound = __longlong_as_double((long long)w.bound_bits[k]);
   w.bound_bits[k] = kInfBits;
@@ -892,9 +903,22 @@ __global__ void __launch_bounds__(TPB_MAX) k_pass(MeshView m, Params p, Work w, 
 }
 
 // ---------------------------------------------------------------------------
-// k_ls_deferred: the queued line searches of one pass, one per thread, from
-// the pass's start state ub, the stored P_ij and the row's bounds
+// k_ls_deferred / k_ls_iterate: the queued line searches of one pass, one per
+// thread, from the pass's start state ub, the stored P_ij and the row's
+// bounds. The first kernel takes every exit without iteration and queues the
+// rest for the second, whose threads then all run the same iteration count.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ bool queue_iteration(const Work &w, int slot, const LsItem &it) {
+  namespace cg = cooperative_groups;
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(&w.lsq2_count[slot], g.size());
+  base = g.shfl(base, 0) + g.thread_rank();
+  if (base >= w.lsq2_cap) return false;  // full: the caller iterates itself
+  w.lsq2[base] = it;
+  return true;
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(256) k_ls_deferred(MeshView m, Params p, Work w, const double *__restrict__ ub,
                                                      int slot, double *__restrict__ lout) {
@@ -913,7 +937,33 @@ __global__ void __launch_bounds__(256) k_ls_deferred(MeshView m, Params p, Work 
       u[s] = ub[(int64_t)it.x * SP + s];
       P[s] = w.P[(int64_t)it.y * SP + s];
     }
-    lout[it.y] = line_search<DIM>(p, u, P, bi[0], bi[1], phimin, phimin5);
+    const LsBracket b = line_search_start<DIM>(p, u, P, bi[0], bi[1], phimin, phimin5);
+    if (b.done)
+      lout[it.y] = b.l;
+    else if (!queue_iteration(w, slot, LsItem{it.x, it.y, b.l, b.pl, b.pr, b.rR}))
+      lout[it.y] = line_search_iterate<DIM>(p, u, P, phimin, b);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_ls_iterate(MeshView m, Params p, Work w, const double *__restrict__ ub,
+                                                    int slot, double *__restrict__ lout) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  if (w.st->err) return;
+  const unsigned cnt = min(w.lsq2_count[slot], w.lsq2_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&w.st->line_searches_iterated, (unsigned long long)cnt);
+  for (unsigned q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+    const LsItem it = w.lsq2[q];
+    const double phimin = w.bounds[(int64_t)it.i * 4 + 2];
+    double u[S], P[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      u[s] = ub[(int64_t)it.i * SP + s];
+      P[s] = w.P[(int64_t)it.k * SP + s];
+    }
+    const LsBracket b{it.l, it.pl, it.pr, it.rR, false};
+    lout[it.k] = line_search_iterate<DIM>(p, u, P, phimin, b);
   }
 }
 
@@ -1047,6 +1097,7 @@ void launch_ls_deferred(const MeshView &m, const Params &p, const Work &w, const
   // a fixed grid (1024 threads per SM of a 152-SM GB300) that strides over
   // however many searches were queued; the count stays on the device
   k_ls_deferred<DIM><<<152 * 1024 / tpb, tpb, 0, s>>>(m, p, w, ub, slot, lout);
+  k_ls_iterate<DIM><<<152 * 1024 / tpb, tpb, 0, s>>>(m, p, w, ub, slot, lout);
 }
 template <int DIM>
 void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,

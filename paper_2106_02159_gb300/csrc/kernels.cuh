@@ -42,6 +42,7 @@ struct DevStatus {
   unsigned long long cfl_violations;
   unsigned long long not_admissible;
   unsigned long long line_searches_deferred;  // searches the l = 1 check left open (cumulative)
+  unsigned long long line_searches_iterated;  // of those, searches that ran the bracketing iteration
 };
 
 struct MeshView {
@@ -118,6 +119,18 @@ struct Work {
   int2 *lsq;             // [lsq_cap] (row i, entry k)
   unsigned *lsq_count;   // [LSQ_SLOTS] entries queued by pass 0, 1, ... of the stage (zeroed by k_tau)
   unsigned lsq_cap;
+  // the searches among those that need the bracketing iteration, queued by
+  // k_ls_deferred for k_ls_iterate
+  struct LsItem *lsq2;   // [lsq2_cap]
+  unsigned *lsq2_count;  // [LSQ_SLOTS]
+  unsigned lsq2_cap;
+};
+
+// a line search left to the bracketing iteration: row i, entry k, the bracket
+// [0, l] with psi(0) = pl > 0, psi(l) = pr < 0 and rR = rho(l)^(-1/5)
+struct LsItem {
+  int i, k;
+  double l, pl, pr, rR;
 };
 constexpr int LSQ_SLOTS = 8;  // limiter passes per stage, at most
 
