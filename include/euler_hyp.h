@@ -220,15 +220,28 @@ eh_status eh_set_instances(eh_ctx *ctx, int32_t ninst, const int64_t *row_offset
  * NULL). Synchronises. */
 eh_status eh_get_instances(eh_ctx *ctx, double *t, double *last_dt, double *stage_bound);
 
-/* Block-size autotuner: runs 'steps_per_candidate' SSPRK(3,3) steps with 64,
- * 128 and 256 rows per block, times every kernel with CUDA events and keeps
- * the fastest block size per kernel kind. The state and the instance times
+/* Launch-shape autotuner: runs 'steps_per_candidate' SSPRK(3,3) steps for
+ * every candidate -- 64, 128 and 256 rows per block, and for the grid-stride
+ * kernels (EH_KERNEL_LIM1, _PASS, _FINAL) one thread per row or at most 256,
+ * 512 or 768 rows in flight per SM -- times every kernel with CUDA events and
+ * keeps the fastest shape per kernel kind. The state and the instance times
  * are restored afterwards. chosen (may be NULL) receives EH_KERNEL_COUNT
  * block sizes. */
 eh_status eh_autotune(eh_ctx *ctx, int32_t steps_per_candidate, int32_t *chosen);
 
 /* Current block size of every kernel kind (EH_KERNEL_COUNT values). */
 eh_status eh_get_block_sizes(const eh_ctx *ctx, int32_t *tpb);
+
+/* Rows in flight per SM of every kernel kind (EH_KERNEL_COUNT values; 0 = one
+ * thread per row, the grid covering all rows at once). */
+eh_status eh_get_rows_per_sm(const eh_ctx *ctx, int32_t *rows);
+
+/* Sets one kernel kind's launch shape by hand: threads_per_block 64, 128 or
+ * 256; rows_per_sm 0 (one thread per row) or, for EH_KERNEL_LIM1, _PASS and
+ * _FINAL only, a cap of 1..2048 rows in flight per SM (the kernel then loops
+ * over rows with a grid stride). EH_ERR_INVALID_ARG otherwise. Results do not
+ * depend on the shape. */
+eh_status eh_set_launch_shape(eh_ctx *ctx, int32_t kernel, int32_t threads_per_block, int32_t rows_per_sm);
 
 /* Number of kernel launches one eh_step issues (for accounting). */
 int32_t eh_launches_per_step(const eh_ctx *ctx);

@@ -34,7 +34,7 @@ EXPORTS = ("eh_config_default", "eh_create", "eh_upload_mesh", "eh_set_state", "
            "eh_apply_boundary_conditions", "eh_cfl_dt", "eh_stage", "eh_step", "eh_run", "eh_synchronize",
            "eh_get_diagnostics", "eh_trace", "eh_profile_enable", "eh_profile_read", "eh_launches_per_step",
            "eh_last_error", "eh_status_string", "eh_destroy", "eh_cfl_dt_noalloc", "eh_set_instances",
-           "eh_get_instances", "eh_autotune", "eh_get_block_sizes")
+           "eh_get_instances", "eh_autotune", "eh_get_block_sizes", "eh_get_rows_per_sm", "eh_set_launch_shape")
 CFL_NOALLOC_MAX_ROWS = 1 << 23
 KERNEL_NAMES = ("prep", "visc", "low", "tau", "lim1", "pass", "final", "lsearch")
 
@@ -109,6 +109,8 @@ def load(path: str | None = None):
     lib.eh_get_instances.argtypes = [vp, vp, vp, vp]
     lib.eh_autotune.argtypes = [vp, i32, vp]
     lib.eh_get_block_sizes.argtypes = [vp, vp]
+    lib.eh_get_rows_per_sm.argtypes = [vp, vp]
+    lib.eh_set_launch_shape.argtypes = [vp, i32, i32, i32]
     lib.eh_cfl_dt_noalloc.argtypes = [i32, ctypes.c_double, ctypes.c_double, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("eh_config_default", "eh_destroy", "eh_launches_per_step", "eh_last_error",
@@ -294,6 +296,15 @@ class Solver:
         out = np.zeros(len(KERNEL_NAMES), dtype=np.int32)
         self._check(self.lib.eh_get_block_sizes(self.ctx, _p(out)), "eh_get_block_sizes")
         return dict(zip(KERNEL_NAMES, out.tolist()))
+
+    def rows_per_sm(self) -> dict:
+        out = np.zeros(len(KERNEL_NAMES), dtype=np.int32)
+        self._check(self.lib.eh_get_rows_per_sm(self.ctx, _p(out)), "eh_get_rows_per_sm")
+        return dict(zip(KERNEL_NAMES, out.tolist()))
+
+    def set_launch_shape(self, kernel: str, threads_per_block: int, rows_per_sm: int = 0):
+        self._check(self.lib.eh_set_launch_shape(self.ctx, KERNEL_NAMES.index(kernel), int(threads_per_block),
+                                                 int(rows_per_sm)), "eh_set_launch_shape")
 
     def launches_per_step(self) -> int:
         return int(self.lib.eh_launches_per_step(self.ctx))

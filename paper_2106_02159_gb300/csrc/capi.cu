@@ -51,6 +51,10 @@ struct eh_ctx {
   int64_t prof_count[EH_KERNEL_COUNT] = {0};
   // block size (rows per block) of every kernel kind
   int tpb[EH_KERNEL_COUNT] = {128, 128, 128, 1024, 128, 128, 128, 256};
+  // rows in flight per SM of the grid-stride kernels (lim1, pass, final); 0:
+  // one thread per row
+  int rows_per_sm[EH_KERNEL_COUNT] = {0};
+  int nsm = 0;  // multiprocessors of the device
   // independent instances
   int ninst = 1;
   std::vector<void *> inst_allocs;
@@ -174,6 +178,13 @@ void flush_profile(eh_ctx *c) {
 
 // One forward-Euler stage on the component-major state Uin, written as
 // out = BC(FE(Uin)) (coef < 0) or out = U0 + coef (BC(FE(Uin)) - U0).
+// grid cap of a grid-stride kernel kind (0: one thread per row)
+int max_blocks(const eh_ctx *c, int kernel) {
+  const int r = c->rows_per_sm[kernel];
+  if (r <= 0 || c->nsm <= 0) return 0;
+  return c->nsm * std::max(1, r / c->tpb[kernel]);
+}
+
 template <int DIM, typename T>
 void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, const double *U0, double coef, double *out,
                    bool trace) {
@@ -192,7 +203,7 @@ void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, con
   { ProfScope ps(c, EH_KERNEL_TAU); launch_tau(m, w, stage, dt_given, p.cfl, !trace, s); }
   {
     ProfScope ps(c, EH_KERNEL_LIM1);
-    launch_lim1<DIM, T>(m, p, w, tpb[EH_KERNEL_LIM1], s);
+    launch_lim1<DIM, T>(m, p, w, tpb[EH_KERNEL_LIM1], max_blocks(c, EH_KERNEL_LIM1), s);
   }
   { ProfScope ps(c, EH_KERNEL_LSEARCH); launch_ls_deferred<DIM>(m, p, w, w.UL, 0, w.la, tpb[EH_KERNEL_LSEARCH], s); }
   const double *ucur = w.UL;
@@ -202,7 +213,7 @@ void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, con
     {
       ProfScope ps(c, EH_KERNEL_PASS);
       launch_pass<DIM>(m, p, w, ucur, unext, lcur, lnext, (trace && pass == 1) ? c->trace_lsym : nullptr, pass,
-                       tpb[EH_KERNEL_PASS], s);
+                       tpb[EH_KERNEL_PASS], max_blocks(c, EH_KERNEL_PASS), s);
     }
     {
       ProfScope ps(c, EH_KERNEL_LSEARCH);
@@ -217,7 +228,8 @@ void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, con
   }
   {
     ProfScope ps(c, EH_KERNEL_FINAL);
-    launch_final<DIM>(m, p, w, ucur, lcur, U0, coef, out, trace ? c->trace_pre : nullptr, tpb[EH_KERNEL_FINAL], s);
+    launch_final<DIM>(m, p, w, ucur, lcur, U0, coef, out, trace ? c->trace_pre : nullptr, tpb[EH_KERNEL_FINAL],
+                      max_blocks(c, EH_KERNEL_FINAL), s);
   }
 }
 
@@ -391,6 +403,17 @@ eh_status eh_create(const eh_config *cfg, eh_ctx **out) {
     return EH_ERR_OOM;
   }
   cudaMemset(c->st, 0, sizeof(DevStatus));
+  if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) c->nsm = 0;
+  // fewer rows in flight keep each row's cache lines in L1 from one entry to
+  // the next (thread-per-row loops over long rows); the caps are the fastest
+  // of a sweep on GB300 (128 threads per block)
+  if (cfg->dim == 3) {
+    c->rows_per_sm[EH_KERNEL_LIM1] = 384;
+    c->rows_per_sm[EH_KERNEL_PASS] = 512;
+    c->rows_per_sm[EH_KERNEL_FINAL] = 768;
+  } else {
+    c->rows_per_sm[EH_KERNEL_PASS] = 768;
+  }
   Params &p = c->prm;
   p.gamma = cfg->gamma;
   p.cfl = cfg->cfl;
@@ -463,11 +486,12 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
       betat[k] = mij[tr[k]] / mi[i];
     }
   }
-  std::vector<double> inv_mi(n), relax(n, 0.0);
+  std::vector<double> inv_mi(n), relax(n, 0.0), lam(n);
   double area = 0.0;
   for (int i = 0; i < n; ++i) area += mi[i];
   for (int i = 0; i < n; ++i) {
     inv_mi[i] = 1.0 / mi[i];
+    lam[i] = 1.0 / (double)(row_ptr[i + 1] - row_ptr[i] - 1);
     if (c->cfg.bound_relaxation) relax[i] = std::pow(mi[i] / area, 1.5 / dim);
   }
   std::vector<unsigned char> isb(n, 0);
@@ -489,7 +513,8 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   m.n_bnd = n_bnd;
   int64_t *d_row = nullptr;
   int32_t *d_col = nullptr, *d_tr = nullptr, *d_bidx = nullptr, *d_bkind = nullptr;
-  double *d_cij, *d_cn, *d_cinv, *d_beta, *d_betat, *d_mi, *d_imi, *d_relax, *d_bnorm = nullptr, *d_bstate = nullptr;
+  double *d_cij, *d_cn, *d_cinv, *d_beta, *d_betat, *d_mi, *d_imi, *d_relax, *d_lam, *d_bnorm = nullptr,
+      *d_bstate = nullptr;
   unsigned char *d_isb;
 #define ALLOC(ptr, cnt) \
   if ((st = dalloc(c, &ptr, (size_t)(cnt))) != EH_OK) { free_mesh(c); return st; }
@@ -504,6 +529,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   ALLOC(d_mi, n);
   ALLOC(d_imi, n);
   ALLOC(d_relax, n);
+  ALLOC(d_lam, n);
   ALLOC(d_isb, n);
   ALLOC(d_bidx, n);
   ALLOC(d_bkind, n_bnd);
@@ -582,6 +608,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   if (e == cudaSuccess) e = up(d_mi, mi, sizeof(double) * n);
   if (e == cudaSuccess) e = up(d_imi, inv_mi.data(), sizeof(double) * n);
   if (e == cudaSuccess) e = up(d_relax, relax.data(), sizeof(double) * n);
+  if (e == cudaSuccess) e = up(d_lam, lam.data(), sizeof(double) * n);
   if (e == cudaSuccess) e = up(d_isb, isb.data(), n);
   if (e == cudaSuccess) e = up(d_bidx, bidx.data(), sizeof(int32_t) * n);
   if (e == cudaSuccess) e = up(d_bkind, bnd_kind, sizeof(int32_t) * n_bnd);
@@ -614,6 +641,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   m.mi = d_mi;
   m.inv_mi = d_imi;
   m.relax = d_relax;
+  m.lam = d_lam;
   m.isb = d_isb;
   m.vcij = f_cij ? (const void *)f_cij : (const void *)d_cij;
   m.vcn = f_cn ? (const void *)f_cn : (const void *)d_cn;
@@ -828,31 +856,41 @@ eh_status eh_autotune(eh_ctx *c, int32_t steps_per_candidate, int32_t *chosen) {
   std::vector<double> t_saved(c->ninst);
   CUDA_TRY(c, cudaMemcpyAsync(c->Usave, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpy(t_saved.data(), c->wk.t_inst, tb, cudaMemcpyDeviceToHost));
+  // candidates: block sizes 64/128/256, each with the grid-stride kernels
+  // (lim1, pass, final) at one thread per row or 8/16/24 warps in flight per SM
   const int cands[3] = {64, 128, 256};
+  const int caps[4] = {0, 256, 512, 768};
   double best_ms[EH_KERNEL_COUNT];
-  int best[EH_KERNEL_COUNT];
+  int best[EH_KERNEL_COUNT], best_cap[EH_KERNEL_COUNT];
   for (int k = 0; k < EH_KERNEL_COUNT; ++k) {
     best_ms[k] = INFINITY;
     best[k] = c->tpb[k];
+    best_cap[k] = c->rows_per_sm[k];
   }
   const bool was_profiling = c->profiling;
   for (int q = 0; q < 3; ++q) {
-    for (int k = 0; k < EH_KERNEL_COUNT; ++k)
-      if (k != EH_KERNEL_TAU) c->tpb[k] = cands[q];
-    if ((st = eh_profile_enable(c, 1))) return st;
-    CUDA_TRY(c, cudaMemcpyAsync(c->U, c->Usave, bytes, cudaMemcpyDeviceToDevice, c->stream));
-    for (int32_t r = 0; r < steps_per_candidate; ++r) enqueue_step_any(c, 0.0);
-    CUDA_TRY(c, cudaGetLastError());
-    flush_profile(c);
-    for (int k = 0; k < EH_KERNEL_COUNT; ++k)
-      if (k != EH_KERNEL_TAU && c->prof_count[k] && c->prof_ms[k] < best_ms[k]) {
-        best_ms[k] = c->prof_ms[k];
-        best[k] = cands[q];
+    for (int r = 0; r < 4; ++r) {
+      for (int k = 0; k < EH_KERNEL_COUNT; ++k) {
+        if (k != EH_KERNEL_TAU) c->tpb[k] = cands[q];
+        c->rows_per_sm[k] = (k == EH_KERNEL_LIM1 || k == EH_KERNEL_PASS || k == EH_KERNEL_FINAL) ? caps[r] : 0;
       }
+      if ((st = eh_profile_enable(c, 1))) return st;
+      CUDA_TRY(c, cudaMemcpyAsync(c->U, c->Usave, bytes, cudaMemcpyDeviceToDevice, c->stream));
+      for (int32_t it = 0; it < steps_per_candidate; ++it) enqueue_step_any(c, 0.0);
+      CUDA_TRY(c, cudaGetLastError());
+      flush_profile(c);
+      for (int k = 0; k < EH_KERNEL_COUNT; ++k)
+        if (k != EH_KERNEL_TAU && c->prof_count[k] && c->prof_ms[k] < best_ms[k]) {
+          best_ms[k] = c->prof_ms[k];
+          best[k] = cands[q];
+          best_cap[k] = c->rows_per_sm[k];
+        }
+    }
   }
   eh_profile_enable(c, was_profiling ? 1 : 0);
   for (int k = 0; k < EH_KERNEL_COUNT; ++k) {
     c->tpb[k] = best[k];
+    c->rows_per_sm[k] = best_cap[k];
     if (chosen) chosen[k] = best[k];
   }
   // put the state and the instance times back
@@ -889,6 +927,27 @@ eh_status eh_profile_read(eh_ctx *c, int kernel, double *total_ms, int64_t *laun
 eh_status eh_get_block_sizes(const eh_ctx *c, int32_t *tpb) {
   if (!c || !tpb) return EH_ERR_INVALID_ARG;
   for (int k = 0; k < EH_KERNEL_COUNT; ++k) tpb[k] = c->tpb[k];
+  return EH_OK;
+}
+
+eh_status eh_get_rows_per_sm(const eh_ctx *c, int32_t *rows) {
+  if (!c || !rows) return EH_ERR_INVALID_ARG;
+  for (int k = 0; k < EH_KERNEL_COUNT; ++k) rows[k] = c->rows_per_sm[k];
+  return EH_OK;
+}
+
+eh_status eh_set_launch_shape(eh_ctx *c, int32_t kernel, int32_t threads_per_block, int32_t rows_per_sm) {
+  if (!c || kernel < 0 || kernel >= EH_KERNEL_COUNT || kernel == EH_KERNEL_TAU) return EH_ERR_INVALID_ARG;
+  if (threads_per_block != 64 && threads_per_block != 128 && threads_per_block != 256) return EH_ERR_INVALID_ARG;
+  if (rows_per_sm < 0 || rows_per_sm > 2048) return EH_ERR_INVALID_ARG;
+  if (rows_per_sm > 0 && kernel != EH_KERNEL_LIM1 && kernel != EH_KERNEL_PASS && kernel != EH_KERNEL_FINAL)
+    return EH_ERR_INVALID_ARG;
+  c->tpb[kernel] = threads_per_block;
+  c->rows_per_sm[kernel] = rows_per_sm;
+  if (c->graph) {  // the captured graph holds the old launch shapes
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
   return EH_OK;
 }
 

@@ -777,12 +777,10 @@ __global__ void __launch_bounds__(256) k_tau(MeshView m, Work w, int stage, doub
 // k_lim1: Algorithm 1 step 4 -- U^L, P_ij and the first line search
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-__global__ void __launch_bounds__(TPB_MAX) k_lim1(MeshView m, Params p, Work w) {
+__device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, const Work &w, int i) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
   using R = Rec<DIM>;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.n || w.st->err) return;
   const double tau = w.tau_inst[m.inst ? m.inst[i] : 0];
   const double *Ri = w.rec + (int64_t)i * R::SIZE;
   double ui[S], ul[S], fhi[S];
@@ -837,6 +835,16 @@ __global__ void __launch_bounds__(TPB_MAX) k_lim1(MeshView m, Params p, Work w) 
   defer_line_searches(w, 0, i, k0, defer);
 }
 
+// rows i, i + grid size, ... (the grid may be capped to limit the rows in
+// flight; one row per thread otherwise)
+template <int DIM, typename T>
+__global__ void __launch_bounds__(TPB_MAX) k_lim1(MeshView m, Params p, Work w) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.n; i += gridDim.x * blockDim.x) {
+    if (w.st->err) return;
+    lim1_row<DIM, T>(m, p, w, i);
+  }
+}
+
 // min of two limiters in [0, 1]: non-negative doubles order like their bit
 // patterns, so an integer min (no FP64 instruction) gives the same value
 __device__ __forceinline__ double lmin(double a, double b) {
@@ -848,15 +856,13 @@ __device__ __forceinline__ double lmin(double a, double b) {
 // k_pass: symmetrise the limiter, update, shrink P and search again
 // ---------------------------------------------------------------------------
 template <int DIM>
-__global__ void __launch_bounds__(TPB_MAX) k_pass(MeshView m, Params p, Work w, const double *__restrict__ Uin,
-                                              double *__restrict__ Uout, const double *__restrict__ lin,
-                                              double *__restrict__ lout, double *lsym_trace, int slot) {
+__device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, const Work &w, const double *__restrict__ Uin,
+                                         double *__restrict__ Uout, const double *__restrict__ lin,
+                                         double *__restrict__ lout, double *lsym_trace, int slot, int i) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.n || w.st->err) return;
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
-  const double lambda_i = 1.0 / (double)(k1 - k0 - 1);
+  const double lambda_i = m.lam[i];
   double u[S];
   const double *Ui = Uin + (int64_t)i * SP;
 #pragma unroll
@@ -900,6 +906,16 @@ __global__ void __launch_bounds__(TPB_MAX) k_pass(MeshView m, Params p, Work w, 
       defer_line_searches(w, slot, i, k, 1ull);
   }
   defer_line_searches(w, slot, i, k0, defer);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(TPB_MAX) k_pass(MeshView m, Params p, Work w, const double *__restrict__ Uin,
+                                              double *__restrict__ Uout, const double *__restrict__ lin,
+                                              double *__restrict__ lout, double *lsym_trace, int slot) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.n; i += gridDim.x * blockDim.x) {
+    if (w.st->err) return;
+    pass_row<DIM>(m, p, w, Uin, Uout, lin, lout, lsym_trace, slot, i);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -997,15 +1013,13 @@ __device__ __forceinline__ bool admissible(const double *u) {
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(TPB_MAX) k_final(MeshView m, Params p, Work w, const double *__restrict__ Uin,
-                                               const double *__restrict__ lin, const double *U0, double coef,
-                                               double *out, double *Upre_trace) {
+__device__ __forceinline__ void final_row(const MeshView &m, const Params &p, const Work &w, const double *__restrict__ Uin,
+                                          const double *__restrict__ lin, const double *U0, double coef, double *out,
+                                          double *Upre_trace, int i) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m.n || w.st->err) return;
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
-  const double lambda_i = 1.0 / (double)(k1 - k0 - 1);
+  const double lambda_i = m.lam[i];
   double u[S];
   const double *Ui = Uin + (int64_t)i * SP;
 #pragma unroll
@@ -1037,6 +1051,16 @@ __global__ void __launch_bounds__(TPB_MAX) k_final(MeshView m, Params p, Work w,
   }
 #pragma unroll
   for (int s = 0; s < S; ++s) out[(int64_t)s * m.n + i] = u[s];
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(TPB_MAX) k_final(MeshView m, Params p, Work w, const double *__restrict__ Uin,
+                                               const double *__restrict__ lin, const double *U0, double coef,
+                                               double *out, double *Upre_trace) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.n; i += gridDim.x * blockDim.x) {
+    if (w.st->err) return;
+    final_row<DIM>(m, p, w, Uin, lin, U0, coef, out, Upre_trace, i);
+  }
 }
 
 template <int DIM> __global__ void k_apply_bc(MeshView m, double *U) {
@@ -1082,14 +1106,20 @@ void launch_tau(const MeshView &m, const Work &w, int stage, double dt_given, do
                 cudaStream_t s) {
   k_tau<<<nblocks(m.ninst, 256), 256, 0, s>>>(m, w, stage, dt_given, cfl, advance_time ? 1 : 0);
 }
+// grid of the grid-stride row kernels: one thread per row, or at most
+// max_blocks blocks (max_blocks > 0)
+inline unsigned capped_grid(int64_t n, int tpb, int max_blocks) {
+  const unsigned g = nblocks(n, tpb);
+  return (max_blocks > 0 && g > (unsigned)max_blocks) ? (unsigned)max_blocks : g;
+}
 template <int DIM, typename T>
-void launch_lim1(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s) {
-  k_lim1<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w);
+void launch_lim1(const MeshView &m, const Params &p, const Work &w, int tpb, int max_blocks, cudaStream_t s) {
+  k_lim1<DIM, T><<<capped_grid(m.n, tpb, max_blocks), tpb, 0, s>>>(m, p, w);
 }
 template <int DIM>
 void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
-                 double *lout, double *lsym_trace, int slot, int tpb, cudaStream_t s) {
-  k_pass<DIM><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w, Uin, Uout, lin, lout, lsym_trace, slot);
+                 double *lout, double *lsym_trace, int slot, int tpb, int max_blocks, cudaStream_t s) {
+  k_pass<DIM><<<capped_grid(m.n, tpb, max_blocks), tpb, 0, s>>>(m, p, w, Uin, Uout, lin, lout, lsym_trace, slot);
 }
 template <int DIM>
 void launch_ls_deferred(const MeshView &m, const Params &p, const Work &w, const double *ub, int slot, double *lout,
@@ -1101,8 +1131,9 @@ void launch_ls_deferred(const MeshView &m, const Params &p, const Work &w, const
 }
 template <int DIM>
 void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,
-                  const double *U0, double coef, double *out, double *Upre_trace, int tpb, cudaStream_t s) {
-  k_final<DIM><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, w, Uin, lin, U0, coef, out, Upre_trace);
+                  const double *U0, double coef, double *out, double *Upre_trace, int tpb, int max_blocks,
+                  cudaStream_t s) {
+  k_final<DIM><<<capped_grid(m.n, tpb, max_blocks), tpb, 0, s>>>(m, p, w, Uin, lin, U0, coef, out, Upre_trace);
 }
 template <int DIM> void launch_apply_bc(const MeshView &m, double *U, cudaStream_t s) {
   k_apply_bc<DIM><<<nblocks(m.n, 256), 256, 0, s>>>(m, U);
@@ -1116,7 +1147,7 @@ template <int DIM> void launch_count_not_admissible(int n, const double *U, DevS
   template void launch_visc<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);               \
   template void launch_alpha<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);              \
   template void launch_low<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);                \
-  template void launch_lim1<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);
+  template void launch_lim1<DIM, T>(const MeshView &, const Params &, const Work &, int, int, cudaStream_t);
 
 EH_INSTANTIATE_T(2, double)
 EH_INSTANTIATE_T(3, double)
@@ -1125,11 +1156,11 @@ EH_INSTANTIATE_T(3, float)
 
 #define EH_INSTANTIATE(DIM)                                                                                          \
   template void launch_pass<DIM>(const MeshView &, const Params &, const Work &, const double *, double *,            \
-                                 const double *, double *, double *, int, int, cudaStream_t);                         \
+                                 const double *, double *, double *, int, int, int, cudaStream_t);                    \
   template void launch_ls_deferred<DIM>(const MeshView &, const Params &, const Work &, const double *, int, double *, \
                                         int, cudaStream_t);                                                          \
   template void launch_final<DIM>(const MeshView &, const Params &, const Work &, const double *, const double *,     \
-                                  const double *, double, double *, double *, int, cudaStream_t);                     \
+                                  const double *, double, double *, double *, int, int, cudaStream_t);                \
   template void launch_apply_bc<DIM>(const MeshView &, double *, cudaStream_t);                                       \
   template void launch_count_not_admissible<DIM>(int, const double *, DevStatus *, cudaStream_t);
 

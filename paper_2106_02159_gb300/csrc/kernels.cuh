@@ -59,6 +59,7 @@ struct MeshView {
   const double *mi;
   const double *inv_mi;
   const double *relax;       // r_i (0 when the bounds are strict)
+  const double *lam;         // lambda_i = 1 / (card I(i) - 1)
   const unsigned char *isb;  // 1 for boundary nodes
   // arrays in the precision of the viscosity / flux part (double in FP64 mode,
   // float in mixed mode): c_ij [dim][nnz], |c_ij|, 1/|c_ij|
@@ -150,11 +151,14 @@ void launch_low(const MeshView &m, const Params &p, const Work &w, int tpb, cuda
 // that step, else the bound), clipped to reach t_final; stage 2 advances t
 void launch_tau(const MeshView &m, const Work &w, int stage, double dt_given, double cfl, bool advance_time,
                 cudaStream_t s);
+// lim1, pass and final loop over rows with a grid stride; max_blocks > 0 caps
+// their grid (fewer rows in flight: less cache pressure from the gathers of
+// long rows), 0 runs one thread per row
 template <int DIM, typename T>
-void launch_lim1(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s);
+void launch_lim1(const MeshView &m, const Params &p, const Work &w, int tpb, int max_blocks, cudaStream_t s);
 template <int DIM>
 void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
-                 double *lout, double *lsym_trace, int slot, int tpb, cudaStream_t s);
+                 double *lout, double *lsym_trace, int slot, int tpb, int max_blocks, cudaStream_t s);
 // the queued line searches of pass 'slot' from the states ub ([n][SP]) and the
 // stored P_ij; writes their limiters to lout
 template <int DIM>
@@ -164,7 +168,8 @@ void launch_ls_deferred(const MeshView &m, const Params &p, const Work &w, const
 // else out = U0 + coef (BC(...) - U0). U0 / out are component-major [S][n].
 template <int DIM>
 void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,
-                  const double *U0, double coef, double *out, double *Upre_trace, int tpb, cudaStream_t s);
+                  const double *U0, double coef, double *out, double *Upre_trace, int tpb, int max_blocks,
+                  cudaStream_t s);
 template <int DIM> void launch_apply_bc(const MeshView &m, double *U, cudaStream_t s);
 template <int DIM> void launch_count_not_admissible(int n, const double *U, DevStatus *st, cudaStream_t s);
 
