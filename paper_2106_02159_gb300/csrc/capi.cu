@@ -548,21 +548,30 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
     ALLOC(f_cn, nnz);
     ALLOC(f_cinv, nnz);
     ALLOC(f_rec, (size_t)n * REC_MAX);
-    ALLOC(f_w, (size_t)nnz * SP);
-    ALLOC(f_d, nnz);
     ALLOC(f_fh, (size_t)n * SP);
-    ALLOC(f_a, nnz);
+    // packed slots [w (S), a, d, 0...] in both dimensions
+    static_assert(EdgeLayout<2, float>::packed && EdgeLayout<3, float>::packed, "FP32 edge slots are packed");
+    constexpr int spw_f = EdgeLayout<2, float>::SPW;
+    ALLOC(f_w, (size_t)nnz * spw_f);
+    f_d = f_a = nullptr;
     w.va = f_a;
     w.vrec = f_rec;
     w.vw = f_w;
     w.vd = f_d;
     w.vFH = f_fh;
   } else {
-    ALLOC(w.w, (size_t)nnz * SP);
-    ALLOC(w.d, nnz);
     ALLOC(w.FH, (size_t)n * SP);
-    double *d_a;
-    ALLOC(d_a, nnz);
+    double *d_a = nullptr;
+    if (dim == 3) {  // packed slots [w (5), a, d, 0]
+      constexpr int spw3 = EdgeLayout<3, double>::SPW;
+      ALLOC(w.w, (size_t)nnz * spw3);
+      w.d = nullptr;
+    } else {
+      constexpr int spw2 = EdgeLayout<2, double>::SPW;
+      ALLOC(w.w, (size_t)nnz * spw2);
+      ALLOC(w.d, nnz);
+      ALLOC(d_a, nnz);
+    }
     w.va = d_a;
     w.vrec = w.rec;
     w.vw = w.w;
@@ -997,6 +1006,12 @@ eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {
   switch (what) {
     case EH_TRACE_D_IJ:
       if (count != nnz) return fail(c, EH_ERR_INVALID_ARG, "count must be %lld", (long long)nnz);
+      if (c->cfg.dim == 3 || mixed(c)) {  // packed slots [w (S), a, d, 0...]
+        const int spw = 8, dpos = c->cfg.dim + 3;
+        if ((st = vcopy(c->wk.vw, nnz * spw, buf))) return st;
+        for (int64_t k = 0; k < nnz; ++k) host_out[k] = buf[k * spw + dpos];
+        return EH_OK;
+      }
       if ((st = vcopy(c->wk.vd, nnz, buf))) return st;
       std::copy(buf.begin(), buf.end(), host_out);
       return EH_OK;

@@ -59,6 +59,38 @@ __device__ __forceinline__ double abs_bits(double x) {
 }
 __device__ __forceinline__ float abs_bits(float x) { return fabsf(x); }
 
+// the per-entry viscosity quantities (layout: EdgeLayout)
+template <int DIM, typename T> __device__ __forceinline__ T *w_slot(const Work &w, int64_t k) {
+  return (T *)w.vw + k * EdgeLayout<DIM, T>::SPW;
+}
+template <int DIM, typename T> __device__ __forceinline__ T *d_ptr(const Work &w, int64_t k) {
+  return EdgeLayout<DIM, T>::packed ? w_slot<DIM, T>(w, k) + EdgeLayout<DIM, T>::D : (T *)w.vd + k;
+}
+template <int DIM, typename T> __device__ __forceinline__ T *a_ptr(const Work &w, int64_t k) {
+  return EdgeLayout<DIM, T>::packed ? w_slot<DIM, T>(w, k) + EdgeLayout<DIM, T>::A : (T *)w.va + k;
+}
+// one packed slot [w (S), a, d, 0...] of 8 values in whole-sector vector stores
+template <int S> __device__ __forceinline__ void store_slot(double *p, const double *wv, double a, double d) {
+  double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int s = 0; s < S; ++s) v[s] = wv[s];
+  v[S] = a;
+  v[S + 1] = d;
+  double2 *q = reinterpret_cast<double2 *>(p);
+#pragma unroll
+  for (int h = 0; h < 4; ++h) q[h] = make_double2(v[2 * h], v[2 * h + 1]);
+}
+template <int S> __device__ __forceinline__ void store_slot(float *p, const float *wv, float a, float d) {
+  float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int s = 0; s < S; ++s) v[s] = wv[s];
+  v[S] = a;
+  v[S + 1] = d;
+  float4 *q = reinterpret_cast<float4 *>(p);
+  q[0] = make_float4(v[0], v[1], v[2], v[3]);
+  q[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
 // ---------------------------------------------------------------------------
 // roots and powers for gamma = 7/5 (division-free Newton iterations from an
 // FP32 seed; two steps take the ~2^-21 seed error below double rounding)
@@ -467,7 +499,6 @@ __global__ void __launch_bounds__(TPB_MAX) k_prep(MeshView m, Params p, const do
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) {
   constexpr int S = DIM + 2;
-  constexpr int SP = Layout<DIM>::SP;
   using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || w.st->err) return;
@@ -475,9 +506,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
   const T *cij = (const T *)m.vcij;
   const T *cn = (const T *)m.vcn;
   const T *cinv = (const T *)m.vcinv;
-  T *warr = (T *)w.vw;
-  T *aarr = (T *)w.va;
-  T *darr = (T *)w.vd;
+  constexpr bool packed = EdgeLayout<DIM, T>::packed;
   const T *Ri = rec + (int64_t)i * R::SIZE;
   T vi[DIM], fi[S][DIM], qi[DIM];
 #pragma unroll
@@ -515,20 +544,15 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
     }
 #pragma unroll
     for (int q = 0; q < DIM; ++q) a_ += (qj[q] - qi[q]) * c[q];
-    T *wk = warr + k * SP;
-#pragma unroll
-    for (int s = 0; s < S; ++s) wk[s] = wv[s];
-    aarr[k] = a_;
     const bool both = bi && m.isb[j];
     // the transposed entry: c_ji = -c_ij unless both nodes lie on the boundary
     // (Sec. 3.1), so w_ji = w_ij and a_ji = a_ij; otherwise evaluate with c_ji
-    T *wt = warr + (int64_t)kt * SP;
-    if (!both) {
+    T wt[S], at = a_;
 #pragma unroll
-      for (int s = 0; s < S; ++s) wt[s] = wv[s];
-      aarr[kt] = a_;
-    } else {
-      T ct[DIM], at = T(0);
+    for (int s = 0; s < S; ++s) wt[s] = wv[s];
+    if (both) {
+      T ct[DIM];
+      at = T(0);
 #pragma unroll
       for (int q = 0; q < DIM; ++q) ct[q] = cij[(int64_t)q * m.nnz + kt];
 #pragma unroll
@@ -540,7 +564,16 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
       }
 #pragma unroll
       for (int q = 0; q < DIM; ++q) at += (qi[q] - qj[q]) * ct[q];
-      aarr[kt] = at;
+    }
+    if constexpr (!packed) {
+      T *wk = w_slot<DIM, T>(w, k), *wtk = w_slot<DIM, T>(w, kt);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        wk[s] = wv[s];
+        wtk[s] = wt[s];
+      }
+      *a_ptr<DIM, T>(w, k) = a_;
+      *a_ptr<DIM, T>(w, kt) = at;
     }
     // d_ij (Sec. 3.1), mirrored
     const T ci = cinv[k];
@@ -563,8 +596,13 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
       T dji = lambda_max<T>(p, unj, Rj[R::P], Rj[R::A], Rj[R::AZ], Rj[R::IP], uni, pi, ai, azi, ipi) * cn[kt];
       dij = max_nonneg(dij, dji);
     }
-    darr[k] = dij;
-    darr[kt] = dij;
+    if constexpr (packed) {
+      store_slot<S>(w_slot<DIM, T>(w, k), wv, a_, dij);
+      store_slot<S>(w_slot<DIM, T>(w, kt), wt, at, dij);
+    } else {
+      *d_ptr<DIM, T>(w, k) = dij;
+      *d_ptr<DIM, T>(w, kt) = dij;
+    }
   }
 }
 
@@ -574,13 +612,10 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB_MAX) k_alpha(MeshView m, Params p, Work w) {
   constexpr int S = DIM + 2;
-  constexpr int SP = Layout<DIM>::SP;
   using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || w.st->err) return;
   const T *Ri = (const T *)w.vrec + (int64_t)i * R::SIZE;
-  const T *warr = (const T *)w.vw;
-  const T *aarr = (const T *)w.va;
   // eta'(U_i)
   T deta[S];
   {
@@ -601,8 +636,8 @@ __global__ void __launch_bounds__(TPB_MAX) k_alpha(MeshView m, Params p, Work w)
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
   for (int64_t k = k0; k < k1; ++k) {
     if (m.col[k] == i) continue;
-    const T *wk = warr + k * SP;
-    const T a_ = aarr[k];
+    const T *wk = w_slot<DIM, T>(w, k);
+    const T a_ = *a_ptr<DIM, T>(w, k);
     T b_ = T(0);
 #pragma unroll
     for (int s = 0; s < S; ++s) b_ += deta[s] * wk[s];
@@ -630,8 +665,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
 #pragma unroll
     for (int s = 0; s < S; ++s) ui[s] = Ri[s];
     const double alphai = w.alpha[i];
-    T *darr = (T *)w.vd;
-    const T *warr = (const T *)w.vw;
+
     // U^L increment and the bounds in FP64; F^H in the viscosity precision T
     double inc[S], wsum[S];  // U^L increment in FP64 (also in mixed mode)
     T fh[S];
@@ -654,9 +688,9 @@ __global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
         continue;
       }
       const double *Rj = w.rec + (int64_t)j * R::SIZE;
-      const T dkT = darr[k];
+      const T *wk = w_slot<DIM, T>(w, k);
+      const T dkT = *d_ptr<DIM, T>(w, k);
       const double dk = (double)dkT;
-      const T *wk = warr + k * SP;
       const T dH = T(0.5 * (alphai + w.alpha[j])) * dkT;
       double w0 = 0.0;
 #pragma unroll
@@ -693,7 +727,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
       inc[s] -= wsum[s];
       fh[s] -= (T)wsum[s];
     }
-    darr[kd] = (T)(-dsum);
+    *d_ptr<DIM, T>(w, kd) = (T)(-dsum);
     bound = p.cfl * m.mi[i] / (2.0 * dsum);
     double *inci = w.inc + (int64_t)i * SP;
     T *fhi = (T *)w.vFH + (int64_t)i * SP;
@@ -786,7 +820,7 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
   double ui[S], ul[S], fhi[S];
   const double *inci = w.inc + (int64_t)i * SP;
   const T *FHarr = (const T *)w.vFH;
-  const T *darr = (const T *)w.vd;
+
   const T *FHi = FHarr + (int64_t)i * SP;
   const double tm = tau * m.inv_mi[i];
 #pragma unroll
@@ -816,7 +850,7 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
     }
     const double *Rj = w.rec + (int64_t)j * R::SIZE;
     const T *FHj = FHarr + (int64_t)j * SP;
-    const double dk = (double)darr[k];
+    const double dk = (double)*d_ptr<DIM, T>(w, k);
     const double dH = 0.5 * (alphai + w.alpha[j]) * dk;
     const double b = m.beta[k], bt = m.betat[k];
     double P[S];

@@ -14,6 +14,19 @@ template <int DIM> struct Layout {
   static constexpr int SP = DIM == 2 ? 4 : 6;
 };
 
+// Per-entry quantities of the viscosity kernel: w_ij (S values), a_ij, d_ij,
+// in precision T. FP64 2D: w_ij in a 4-value slot (one 32-byte sector), a_ij
+// and d_ij in arrays of their own. Otherwise (3D, and FP32 2D) one 8-value
+// slot [w_ij (S), a_ij, d_ij, 0...] per entry, so that the write of an edge
+// and its mirrored copy cover whole 32-byte sectors (partial slots and
+// separate a/d writes left partial sectors that the L2 completed from DRAM).
+template <int DIM, typename T> struct EdgeLayout {
+  static constexpr bool packed = DIM == 3 || sizeof(T) == 4;
+  static constexpr int SPW = packed ? 8 : 4;
+  static constexpr int A = DIM + 2;  // packed: slot index of a_ij
+  static constexpr int D = DIM + 3;  // packed: slot index of d_ij
+};
+
 // Node record written once per stage by k_prep and gathered by the edge loops:
 // [0..S) state, then the primitive and derived quantities below, then the
 // flux f(U) (S x DIM, row-major).
@@ -111,9 +124,9 @@ struct Work {
   // viscosity / flux precision arrays (aliases of rec, w, d, FH in FP64 mode;
   // float arrays in mixed mode)
   void *vrec;      // [n][Rec::SIZE] node record in that precision
-  void *vw;        // [nnz][SP]
-  void *vd;        // [nnz]
-  void *va;        // [nnz]      (q(U_j) - q(U_i)) . c_ij of the indicator
+  void *vw;        // [nnz][EdgeLayout::SPW] w_ij (and, packed, a_ij and d_ij)
+  void *vd;        // [nnz]      d_ij (not packed)
+  void *va;        // [nnz]      (q(U_j) - q(U_i)) . c_ij of the indicator (not packed)
   void *vFH;       // [n][SP]
   // line searches that the fast check at l = 1 left open, run by
   // k_ls_deferred after each limiter pass (one queue, reused by every pass)
