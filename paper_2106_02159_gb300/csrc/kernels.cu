@@ -80,6 +80,12 @@ template <int S> __device__ __forceinline__ void store_slot(double *p, const dou
 #pragma unroll
   for (int h = 0; h < 4; ++h) q[h] = make_double2(v[2 * h], v[2 * h + 1]);
 }
+// one 32-byte sector of FP64 values
+__device__ __forceinline__ void store_sector(double *p, double x0, double x1, double x2, double x3) {
+  double2 *q = reinterpret_cast<double2 *>(p);
+  q[0] = make_double2(x0, x1);
+  q[1] = make_double2(x2, x3);
+}
 template <int S> __device__ __forceinline__ void store_slot(float *p, const float *wv, float a, float d) {
   float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -546,11 +552,25 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
     for (int q = 0; q < DIM; ++q) a_ += (qj[q] - qi[q]) * c[q];
     const bool both = bi && m.isb[j];
     // the transposed entry: c_ji = -c_ij unless both nodes lie on the boundary
-    // (Sec. 3.1), so w_ji = w_ij and a_ji = a_ij; otherwise evaluate with c_ji
+    // (Sec. 3.1), so w_ji = w_ij and a_ji = a_ij; otherwise evaluate with c_ji.
+    // Packed slots are stored whole once d_ij is known; otherwise each value
+    // is stored as soon as it is computed (fewer live registers).
+    // FP64 3D slots are two sectors: [w0..w3] stored at once, [w4, a, d, 0]
+    // once d_ij is known
+    constexpr bool two_sectors = packed && sizeof(T) == 8;
     T wt[S], at = a_;
+    if constexpr (!packed) {
+      T *wk = w_slot<DIM, T>(w, k);
 #pragma unroll
-    for (int s = 0; s < S; ++s) wt[s] = wv[s];
-    if (both) {
+      for (int s = 0; s < S; ++s) wk[s] = wv[s];
+      *a_ptr<DIM, T>(w, k) = a_;
+    } else if constexpr (two_sectors) {
+      store_sector((double *)w_slot<DIM, T>(w, k), wv[0], wv[1], wv[2], wv[3]);
+    }
+    if (!both) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) wt[s] = wv[s];
+    } else {
       T ct[DIM];
       at = T(0);
 #pragma unroll
@@ -566,14 +586,12 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
       for (int q = 0; q < DIM; ++q) at += (qi[q] - qj[q]) * ct[q];
     }
     if constexpr (!packed) {
-      T *wk = w_slot<DIM, T>(w, k), *wtk = w_slot<DIM, T>(w, kt);
+      T *wtk = w_slot<DIM, T>(w, kt);
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        wk[s] = wv[s];
-        wtk[s] = wt[s];
-      }
-      *a_ptr<DIM, T>(w, k) = a_;
+      for (int s = 0; s < S; ++s) wtk[s] = wt[s];
       *a_ptr<DIM, T>(w, kt) = at;
+    } else if constexpr (two_sectors) {
+      store_sector((double *)w_slot<DIM, T>(w, kt), wt[0], wt[1], wt[2], wt[3]);
     }
     // d_ij (Sec. 3.1), mirrored
     const T ci = cinv[k];
@@ -596,7 +614,21 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
       T dji = lambda_max<T>(p, unj, Rj[R::P], Rj[R::A], Rj[R::AZ], Rj[R::IP], uni, pi, ai, azi, ipi) * cn[kt];
       dij = max_nonneg(dij, dji);
     }
-    if constexpr (packed) {
+    if constexpr (two_sectors) {
+      // values 4..7 of [w (S), a, d, 0...]
+      double hi[4] = {0.0, 0.0, 0.0, 0.0}, hit[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int s = 4; s < S; ++s) {
+        hi[s - 4] = wv[s];
+        hit[s - 4] = wt[s];
+      }
+      hi[S - 4] = a_;
+      hi[S - 3] = dij;
+      hit[S - 4] = at;
+      hit[S - 3] = dij;
+      store_sector((double *)w_slot<DIM, T>(w, k) + 4, hi[0], hi[1], hi[2], hi[3]);
+      store_sector((double *)w_slot<DIM, T>(w, kt) + 4, hit[0], hit[1], hit[2], hit[3]);
+    } else if constexpr (packed) {
       store_slot<S>(w_slot<DIM, T>(w, k), wv, a_, dij);
       store_slot<S>(w_slot<DIM, T>(w, kt), wt, at, dij);
     } else {
