@@ -173,7 +173,9 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
     rec = 8 * (2 * dim + 9)            # node record fields written by prep
     per = {
         "prep": (8 * S + rec, 0),
-        "visc": (8 + rec + 8 + 1, 4 + 8 * dim + 8 + 8 * S + 8 + 4 / 2),
+        # k_visc (c_ij, |c_ij|, 1/|c_ij| and the transpose index of the j > i half;
+        # w_ij, a_ij, d_ij written once per entry) + k_alpha (w_ij, a_ij read; alpha written)
+        "visc": (8 + rec + 1 + 8 * (S + 4) + 8, 4 + (4 + 8 * dim + 16) / 2 + 8 * S + 16 + 4 + 8 * S + 8),
         "low": (8 + 8 * (S + 1) + 8 * 3 + 8 * SP * 2 + 8 * 4, 4 + 8 + 8 * S),
         "lim1": (8 + 8 * S + 8 * SP * 2 + 8 + 8 * 4 + 8 + 8 * SP, 4 + 8 * 3 + 8 * SP + 8),
         "pass": (8 + 8 * SP * 2 + 8 * 4, 4 + 4 + 8 + 8 * SP * 2 + 8),
@@ -182,6 +184,15 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
         "lsearch": (0, 0),  # data dependent: the queued searches only
     }[kernel]
     return per[0] * n + per[1] * nnz
+
+
+# DRAM bytes (read + write) per CSR entry of each kernel kind, from the ncu
+# capture in profiles/all_kernels_cylinder500k.md (2D Q1 cylinder, FP64,
+# developed flow); a launch moves about this times nnz. Only valid for the
+# kernels as captured there, and only for the 2D FP64 cylinder workload.
+NCU_DRAM_BYTES_PER_ENTRY_2D_FP64 = {
+    "prep": 18.8, "visc": 198.1, "low": 85.3, "lim1": 126.4, "pass": 87.5, "final": 59.3,
+}
 
 
 def algorithmic_fp64_flops(kernel: str, n: int, nnz: int, dim: int) -> float:
@@ -396,8 +407,13 @@ def run_ours(args, dist):
     hbm_achieved = bytes_top / (top_ms * 1e-3) / 1e9
     # every kernel of the step is bound by FP64 issue on GB300 (ncu: FP64 pipe
     # 83-86% of peak, DRAM <= 1 TB/s), so the roofline is the FP64 ALU one
+    traffic = None
+    if mesh.dim == 2 and args.precision == "fp64" and top in NCU_DRAM_BYTES_PER_ENTRY_2D_FP64:
+        traffic = NCU_DRAM_BYTES_PER_ENTRY_2D_FP64[top] * mesh.nnz
     roofline = {"bound": "alu", "kernel": f"k_{top}", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per entry on the 500k-vertex "
+                                  "capture, scaled by nnz" if traffic else None,
                 "peak_source": "nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz); probe-measured FMA rate 1.01",
                 "algorithmic_fp64_flops_per_launch": flops_top, "mean_launch_ms": top_ms,
                 "hbm": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
@@ -471,6 +487,7 @@ def run_batch(args, dist):
     s.set_state(U0)
     s.apply_boundary_conditions()
     chosen = s.autotune(1)
+    rows_cap = s.rows_per_sm()
     s.run(args.warmup)
     s.synchronize()
     clocks = Clocks(dist.local_rank)
@@ -520,6 +537,7 @@ def run_batch(args, dist):
                                    f"{args.precision}, one launch per kernel for all instances (CUDA graph)",
                        "instances": len(inst), "vertices": mesh.n, "nnz": mesh.nnz,
                        "cells_min_max": [min(cells), max(cells)], "block_sizes": chosen,
+                       "rows_per_sm": rows_cap,
                        "invariant_violations": diag["not_admissible"]},
             "clocks": clk,
             "per_instance_loop": {"value": loop_value, "unit": UNIT, "steps": loop_steps,
