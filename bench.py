@@ -193,6 +193,12 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
 NCU_DRAM_BYTES_PER_ENTRY_2D_FP64 = {
     "prep": 18.8, "visc": 198.1, "low": 85.3, "lim1": 126.4, "pass": 87.5, "final": 59.3,
 }
+# FP64 pipe activity (sm__pipe_fp64_cycles_active, % of peak) on the same capture:
+# how busy the issue-bound kernels keep the FP64 units (k_visc and k_alpha
+# time-weighted as "visc")
+NCU_FP64_PIPE_ACTIVE_2D_FP64 = {
+    "prep": 0.814, "visc": 0.822, "low": 0.857, "lim1": 0.834, "pass": 0.577, "final": 0.722,
+}
 
 
 def algorithmic_fp64_flops(kernel: str, n: int, nnz: int, dim: int) -> float:
@@ -414,6 +420,7 @@ def run_ours(args, dist):
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per entry on the 500k-vertex "
                                   "capture, scaled by nnz" if traffic else None,
+                "fp64_pipe_active_ncu": NCU_FP64_PIPE_ACTIVE_2D_FP64.get(top) if traffic else None,
                 "peak_source": "nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz); probe-measured FMA rate 1.01",
                 "algorithmic_fp64_flops_per_launch": flops_top, "mean_launch_ms": top_ms,
                 "hbm": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,

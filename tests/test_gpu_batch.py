@@ -94,3 +94,51 @@ def test_autotune_keeps_state_and_results():
         s.step(sync=False)
     ref, _ = _solve(mesh, U0, bs, 3, B.EH_PRECISION_FP64)
     assert np.array_equal(s.get_state(), ref)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_launch_shapes_do_not_change_results(dim):
+    """Rows per block and the cap on rows in flight per SM (grid-stride limiter
+    kernels) change the schedule, never the arithmetic: bitwise equal states."""
+    if dim == 2:
+        mesh, U0, bs = W.cylinder_problem(14)
+        U0 = W.perturbed_state(mesh, 8)
+    else:
+        mesh = M.structured_q1_3d(7, 6, 5, periodic=(True, True, True))
+        U0 = W.perturbed_state(mesh, 9, base=dict(rho=1.0, vel=(0.4, 0.1, -0.2), p=1.0))
+        bs = None
+    ref, s = _solve(mesh, U0, bs, 3, B.EH_PRECISION_FP64)
+    for tpb, cap in ((64, 0), (256, 0), (64, 256), (128, 512), (256, 2048)):
+        q = B.Solver(dim=mesh.dim)
+        q.upload_mesh(mesh, bs)
+        for k in ("lim1", "pass", "final"):
+            q.set_launch_shape(k, tpb, cap)
+        q.set_launch_shape("visc", tpb)
+        assert q.rows_per_sm()["pass"] == cap and q.block_sizes()["lim1"] == tpb
+        q.set_state(U0)
+        q.apply_boundary_conditions()
+        for _ in range(3):
+            q.step(sync=False)
+        assert np.array_equal(q.get_state(), ref), (tpb, cap)
+        q.close()
+
+
+def test_launch_shape_rejects_bad_arguments():
+    s = B.Solver(dim=2)
+    for args in (("lim1", 96, 0), ("pass", 128, -1), ("pass", 128, 4096), ("visc", 128, 256), ("tau", 128, 0)):
+        with pytest.raises(B.EulerError):
+            s.set_launch_shape(*args)
+    s.close()
+
+
+def test_queued_line_searches_are_counted():
+    """The limiter's line searches that the l = 1 check leaves open run in the
+    queued kernels; the diagnostics count them (a flow with active limiting
+    queues some; every iterated search was queued first)."""
+    mesh, U0, bs = W.cylinder_problem(14)
+    U0 = W.perturbed_state(mesh, 8)
+    _, s = _solve(mesh, U0, bs, 4, B.EH_PRECISION_FP64)
+    d = s.diagnostics()
+    assert d["line_searches_deferred"] > 0
+    assert 0 <= d["line_searches_iterated"] <= d["line_searches_deferred"]
+    s.close()
