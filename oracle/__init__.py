@@ -21,7 +21,7 @@ _SRC = os.path.join(_HERE, "euler_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libeuler_oracle.so")
 
-BC_SLIP, BC_DIRICHLET, BC_DO_NOTHING = 1, 2, 3
+BC_SLIP, BC_DIRICHLET, BC_DO_NOTHING, BC_CHARACTERISTIC, BC_GODUNOV = 1, 2, 3, 4, 5
 
 _lib = None
 
@@ -95,6 +95,10 @@ def _bind(lib):
     lib.oracle_line_search.restype = ctypes.c_double
     lib.oracle_line_search.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_double]
+    lib.oracle_bc_characteristic.restype = None
+    lib.oracle_bc_characteristic.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_double]
+    lib.oracle_bc_godunov.restype = None
+    lib.oracle_bc_godunov.argtypes = [dp, dp, dp, ctypes.c_int, ctypes.c_double]
     lib.oracle_set_threads.restype = ctypes.c_int
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
     lib.oracle_count_not_admissible.restype = ctypes.c_int64
@@ -185,6 +189,26 @@ def line_search(ub, P, rho_min, rho_max, phi_min, gamma=1.4, lib=None) -> float:
     ub = np.ascontiguousarray(ub, dtype=np.float64)
     P = np.ascontiguousarray(P, dtype=np.float64)
     return lib.oracle_line_search(_dptr(ub), _dptr(P), rho_min, rho_max, phi_min, ub.size - 2, gamma)
+
+
+def bc_characteristic(u, normal, ud, gamma=1.4, lib=None) -> np.ndarray:
+    """Characteristic non-reflecting post-processing of one state (Sec. 4.2.2)."""
+    lib = lib or load()
+    out = np.array(u, dtype=np.float64, copy=True)
+    nrm = np.ascontiguousarray(normal, dtype=np.float64)
+    ud = np.ascontiguousarray(ud, dtype=np.float64)
+    lib.oracle_bc_characteristic(_dptr(out), _dptr(nrm), _dptr(ud), out.size - 2, gamma)
+    return out
+
+
+def bc_godunov(u, normal, ud, gamma=1.4, lib=None) -> np.ndarray:
+    """Godunov non-reflecting post-processing of one state (Sec. 4.2.1)."""
+    lib = lib or load()
+    out = np.array(u, dtype=np.float64, copy=True)
+    nrm = np.ascontiguousarray(normal, dtype=np.float64)
+    ud = np.ascontiguousarray(ud, dtype=np.float64)
+    lib.oracle_bc_godunov(_dptr(out), _dptr(nrm), _dptr(ud), out.size - 2, gamma)
+    return out
 
 
 class OracleError(RuntimeError):

@@ -64,7 +64,7 @@
 /* fixed number of bracketing iterations of the entropy line search */
 #define LINE_SEARCH_ITERATIONS 6
 
-enum { BC_SLIP = 1, BC_DIRICHLET = 2, BC_DO_NOTHING = 3 };
+enum { BC_SLIP = 1, BC_DIRICHLET = 2, BC_DO_NOTHING = 3, BC_CHARACTERISTIC = 4, BC_GODUNOV = 5 };
 
 enum {
   ORACLE_OK = 0,
@@ -398,8 +398,8 @@ oracle_ctx *oracle_create(const oracle_problem *prob, int *status) {
   for (int b = 0; b < p->n_bnd; ++b) {
     int i = p->bnd_node[b];
     int kind = p->bnd_kind[b];
-    if (i < 0 || i >= n || kind < BC_SLIP || kind > BC_DO_NOTHING) { oracle_destroy(c); return NULL; }
-    if (kind == BC_DIRICHLET && !p->bnd_state) { oracle_destroy(c); return NULL; }
+    if (i < 0 || i >= n || kind < BC_SLIP || kind > BC_GODUNOV) { oracle_destroy(c); return NULL; }
+    if (kind != BC_SLIP && kind != BC_DO_NOTHING && !p->bnd_state) { oracle_destroy(c); return NULL; }
     c->is_bnd[i] = 1;
   }
   int passes = p->limiter_passes;
@@ -658,20 +658,216 @@ int oracle_forward_euler(oracle_ctx *c, const double *U, double tau, double *Uou
 /* Sec. 4: boundary post-processing                                          */
 /* ------------------------------------------------------------------------- */
 
+/* Primitive quantities of a state along the unit normal nrm: rho, the normal
+ * velocity vn, the tangential velocity vt = v - vn n, p and a (Sec. 4.2.2). */
+typedef struct {
+  double rho, vn, vt[MAXD], p, a;
+} nprim;
+
+static nprim normal_primitives(const double *u, const double *nrm, int dim, double gamma) {
+  nprim w;
+  w.rho = u[0];
+  w.vn = 0.0;
+  for (int d = 0; d < dim; ++d) w.vn += u[1 + d] / u[0] * nrm[d];
+  for (int d = 0; d < dim; ++d) w.vt[d] = u[1 + d] / u[0] - w.vn * nrm[d];
+  w.p = pressure(u, dim, gamma);
+  w.a = sqrt(gamma * w.p / w.rho);
+  return w;
+}
+
+/* The conserved state with density rho, velocity vn n + vt and pressure p. */
+static void conserved_from(double rho, double vn, const double *vt, double p, const double *nrm, int dim, double gamma,
+                           double *out) {
+  double v2 = 0.0;
+  out[0] = rho;
+  for (int d = 0; d < dim; ++d) {
+    double v = vn * nrm[d] + vt[d];
+    out[1 + d] = rho * v;
+    v2 += v * v;
+  }
+  out[dim + 1] = p / (gamma - 1.0) + 0.5 * rho * v2;
+}
+
+/* Sec. 4.2.2, characteristic variables: C_1 = v_n - 2a/(gamma-1) and
+ * C_3 = v_n + 2a/(gamma-1) with speeds v_n -/+ a, S = p rho^-gamma and v^perp
+ * with speed v_n. Incoming characteristics (negative speed along the outward
+ * normal) take the Dirichlet state's values, outgoing ones keep U's; the four
+ * cases give eqs. Supersonic_inflow, Subsonic_inflow, Subsonic_outflow and
+ * Supersonic_outflow. u is replaced by the post-processed state. */
+void oracle_bc_characteristic(double *u, const double *nrm, const double *ud, int dim, double gamma) {
+  nprim w = normal_primitives(u, nrm, dim, gamma);
+  if (w.vn < 0.0 && w.a < -w.vn) { /* supersonic inflow */
+    for (int s = 0; s < dim + 2; ++s) u[s] = ud[s];
+    return;
+  }
+  if (w.vn >= 0.0 && w.a <= w.vn) return; /* supersonic outflow */
+  nprim wd = normal_primitives(ud, nrm, dim, gamma);
+  double c3 = w.vn + 2.0 * w.a / (gamma - 1.0);   /* outgoing in both subsonic cases */
+  double c1d = wd.vn - 2.0 * wd.a / (gamma - 1.0); /* incoming in both subsonic cases */
+  /* subsonic inflow: entropy and tangential velocity come in; outflow: they go out */
+  const nprim *src = w.vn < 0.0 ? &wd : &w;
+  double s_ent = src->p * pow(src->rho, -gamma);
+  double a_p = 0.25 * (gamma - 1.0) * (c3 - c1d);
+  double vn_p = 0.5 * (c1d + c3);
+  double rho_p = pow(a_p * a_p / (gamma * s_ent), 1.0 / (gamma - 1.0));
+  double p_p = s_ent * pow(rho_p, gamma);
+  conserved_from(rho_p, vn_p, src->vt, p_p, nrm, dim, gamma, u);
+}
+
+/* Toro's pressure function of side K and its derivative (Riemann problem of
+ * the Euler equations along a line): shock branch for p > p_K, rarefaction
+ * branch otherwise. */
+static void toro_f(double p, const nprim *k, double gamma, double *f, double *df) {
+  if (p > k->p) {
+    double A = 2.0 / ((gamma + 1.0) * k->rho), B = (gamma - 1.0) / (gamma + 1.0) * k->p;
+    double q = sqrt(A / (p + B));
+    *f = (p - k->p) * q;
+    *df = q * (1.0 - 0.5 * (p - k->p) / (p + B));
+  } else {
+    double z = (gamma - 1.0) / (2.0 * gamma);
+    *f = 2.0 * k->a / (gamma - 1.0) * (pow(p / k->p, z) - 1.0);
+    *df = pow(p / k->p, -(gamma + 1.0) / (2.0 * gamma)) / (k->rho * k->a);
+  }
+}
+
+/* State at x/t = 0 of the exact solution of the Riemann problem with left
+ * state l and right state r (normal velocities vn, tangential velocities
+ * carried by the contact): rho, vn, vt, p. */
+static void riemann_at_zero(const nprim *l, const nprim *r, int dim, double gamma, nprim *out) {
+  const double g1 = (gamma - 1.0) / (2.0 * gamma), g2 = (gamma + 1.0) / (2.0 * gamma);
+  const double g4 = 2.0 / (gamma - 1.0), g5 = 2.0 / (gamma + 1.0), g6 = (gamma - 1.0) / (gamma + 1.0);
+  const double g7 = 0.5 * (gamma - 1.0);
+  const double du = r->vn - l->vn;
+  if (g4 * (l->a + r->a) <= du) { /* the two rarefactions leave a vacuum between them */
+    double sl = l->vn + g4 * l->a, sr = r->vn - g4 * r->a;
+    if (l->vn - l->a >= 0.0) { *out = *l; return; }
+    if (sl > 0.0) { /* inside the left fan */
+      double c = g5 * (l->a + g7 * l->vn);
+      out->rho = l->rho * pow(c / l->a, g4);
+      out->vn = g5 * (l->a + g7 * l->vn);
+      out->p = l->p * pow(c / l->a, 1.0 / g1);
+      for (int d = 0; d < dim; ++d) out->vt[d] = l->vt[d];
+      return;
+    }
+    if (sr >= 0.0) { /* vacuum */
+      out->rho = 0.0;
+      out->vn = 0.0;
+      out->p = 0.0;
+      for (int d = 0; d < dim; ++d) out->vt[d] = 0.0;
+      return;
+    }
+    if (r->vn + r->a > 0.0) { /* inside the right fan */
+      double c = g5 * (r->a - g7 * r->vn);
+      out->rho = r->rho * pow(c / r->a, g4);
+      out->vn = g5 * (-r->a + g7 * r->vn);
+      out->p = r->p * pow(c / r->a, 1.0 / g1);
+      for (int d = 0; d < dim; ++d) out->vt[d] = r->vt[d];
+      return;
+    }
+    *out = *r;
+    return;
+  }
+  /* p*: Newton's method on f_L(p) + f_R(p) + (v_R - v_L) = 0 from the
+   * two-rarefaction pressure, kept positive, to a relative change of 1e-15 */
+  double p = pow((l->a + r->a - g7 * du) / (l->a / pow(l->p, g1) + r->a / pow(r->p, g1)), 1.0 / g1);
+  for (int it = 0; it < 100; ++it) {
+    double fl, dfl, fr, dfr;
+    toro_f(p, l, gamma, &fl, &dfl);
+    toro_f(p, r, gamma, &fr, &dfr);
+    double pn = p - (fl + fr + du) / (dfl + dfr);
+    if (pn <= 0.0) pn = 0.5 * p;
+    double change = fabs(pn - p) / (0.5 * (pn + p));
+    p = pn;
+    if (change < 1e-15) break;
+  }
+  double fl, dfl, fr, dfr;
+  toro_f(p, l, gamma, &fl, &dfl);
+  toro_f(p, r, gamma, &fr, &dfr);
+  const double vs = 0.5 * (l->vn + r->vn) + 0.5 * (fr - fl); /* contact speed */
+  if (vs >= 0.0) { /* x = 0 lies left of the contact */
+    for (int d = 0; d < dim; ++d) out->vt[d] = l->vt[d];
+    if (p > l->p) { /* left shock */
+      double s = l->vn - l->a * sqrt(g2 * p / l->p + g1);
+      if (s >= 0.0) { *out = *l; return; }
+      out->rho = l->rho * (p / l->p + g6) / (g6 * p / l->p + 1.0);
+      out->vn = vs;
+      out->p = p;
+      return;
+    }
+    if (l->vn - l->a >= 0.0) { *out = *l; return; } /* left rarefaction ahead of x = 0 */
+    double cs = l->a * pow(p / l->p, g1);
+    if (vs - cs < 0.0) { /* x = 0 in the left star region */
+      out->rho = l->rho * pow(p / l->p, 1.0 / gamma);
+      out->vn = vs;
+      out->p = p;
+      return;
+    }
+    double c = g5 * (l->a + g7 * l->vn); /* inside the left fan */
+    out->rho = l->rho * pow(c / l->a, g4);
+    out->vn = c;
+    out->p = l->p * pow(c / l->a, 1.0 / g1);
+    return;
+  }
+  for (int d = 0; d < dim; ++d) out->vt[d] = r->vt[d];
+  if (p > r->p) { /* right shock */
+    double s = r->vn + r->a * sqrt(g2 * p / r->p + g1);
+    if (s <= 0.0) { *out = *r; return; }
+    out->rho = r->rho * (p / r->p + g6) / (g6 * p / r->p + 1.0);
+    out->vn = vs;
+    out->p = p;
+    return;
+  }
+  if (r->vn + r->a <= 0.0) { *out = *r; return; } /* right rarefaction behind x = 0 */
+  double cs = r->a * pow(p / r->p, g1);
+  if (vs + cs > 0.0) { /* x = 0 in the right star region */
+    out->rho = r->rho * pow(p / r->p, 1.0 / gamma);
+    out->vn = vs;
+    out->p = p;
+    return;
+  }
+  double c = g5 * (r->a - g7 * r->vn); /* inside the right fan */
+  out->rho = r->rho * pow(c / r->a, g4);
+  out->vn = -c;
+  out->p = r->p * pow(c / r->a, 1.0 / g1);
+}
+
+/* Sec. 4.2.1, eq. Godunov_bc: U^P = the value at x = 0 of the exact solution
+ * of the Riemann problem along the outward normal with left state U and
+ * right state U^D. u is replaced by it. */
+void oracle_bc_godunov(double *u, const double *nrm, const double *ud, int dim, double gamma) {
+  nprim l = normal_primitives(u, nrm, dim, gamma), r = normal_primitives(ud, nrm, dim, gamma), z;
+  riemann_at_zero(&l, &r, dim, gamma, &z);
+  conserved_from(z.rho, z.vn, z.vt, z.p, nrm, dim, gamma, u);
+}
+
 /* Slip (eq. slip_bc): M <- M - (M . n^s) n^s. Supersonic inflow (eq.
  * Supersonic_inflow): U <- U^D. Supersonic outflow (eq. Supersonic_outflow):
- * nothing. */
+ * nothing. Non-reflecting nodes: the characteristic post-processing or the
+ * Godunov one (Sec. 4.2), with the node's normal and Dirichlet state. */
 void oracle_apply_bc(const oracle_ctx *c, double *U) {
   const oracle_problem *p = &c->p;
   int n = p->n, dim = p->dim, S = c->S;
   for (int b = 0; b < p->n_bnd; ++b) {
     int i = p->bnd_node[b];
-    if (p->bnd_kind[b] == BC_SLIP) {
+    int kind = p->bnd_kind[b];
+    if (kind == BC_SLIP) {
       double mn = 0.0;
       for (int d = 0; d < dim; ++d) mn += U[(1 + d) * n + i] * p->bnd_normal[(int64_t)d * p->n_bnd + b];
       for (int d = 0; d < dim; ++d) U[(1 + d) * n + i] -= mn * p->bnd_normal[(int64_t)d * p->n_bnd + b];
-    } else if (p->bnd_kind[b] == BC_DIRICHLET) {
+    } else if (kind == BC_DIRICHLET) {
       for (int s = 0; s < S; ++s) U[s * n + i] = p->bnd_state[(int64_t)s * p->n_bnd + b];
+    } else if (kind == BC_CHARACTERISTIC || kind == BC_GODUNOV) {
+      double u[MAXS], ud[MAXS], nrm[MAXD];
+      for (int s = 0; s < S; ++s) {
+        u[s] = U[s * n + i];
+        ud[s] = p->bnd_state[(int64_t)s * p->n_bnd + b];
+      }
+      for (int d = 0; d < dim; ++d) nrm[d] = p->bnd_normal[(int64_t)d * p->n_bnd + b];
+      if (kind == BC_CHARACTERISTIC)
+        oracle_bc_characteristic(u, nrm, ud, dim, p->gamma);
+      else
+        oracle_bc_godunov(u, nrm, ud, dim, p->gamma);
+      for (int s = 0; s < S; ++s) U[s * n + i] = u[s];
     }
   }
 }

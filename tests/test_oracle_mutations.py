@@ -169,6 +169,42 @@ def pin_vortex_second_order(lib):
     return math.log2(errs[0] / errs[1]) >= 1.8
 
 
+@_safe
+def pin_characteristic_invariants(lib):
+    from .test_oracle_bc import _invariants, _random_pair
+    rng = np.random.default_rng(31)
+    for inflow in (True, False):
+        for _ in range(100):
+            n, u, ud = _random_pair(rng, 2, (-0.95, -0.01) if inflow else (0.0, 0.95))
+            up = oracle.bc_characteristic(u, n, ud, lib=lib)
+            iu, idd, ip = _invariants(u, n), _invariants(ud, n), _invariants(up, n)
+            src = idd if inflow else iu
+            if not (np.isclose(ip["C1"], idd["C1"], rtol=1e-12, atol=1e-12)
+                    and np.isclose(ip["C3"], iu["C3"], rtol=1e-12, atol=1e-12)
+                    and np.isclose(ip["S"], src["S"], rtol=1e-11)
+                    and np.allclose(ip["vt"], src["vt"], rtol=1e-12, atol=1e-12)):
+                return False
+    return True
+
+
+@_safe
+def pin_godunov_exact(lib):
+    from .test_oracle_bc import G, _cons, _prim, _random_pair
+    rng = np.random.default_rng(51)
+    for _ in range(400):
+        n, u, ud = _random_pair(rng, 2, (-2.5, 2.5), data_condition=False)
+        rl, _, pl, al, ul, tl = _prim(u, n)
+        rr, _, pr, ar, ur, tr = _prim(ud, n)
+        if 2 * (al + ar) / (G - 1) <= ur - ul:
+            continue
+        rho, un, p = RE.sample(np.array([0.5]), 1.0, rl, ul, pl, rr, ur, pr, gamma=G, x0=0.5)
+        _, us = RE.star_pressure(rl, ul, pl, rr, ur, pr, gamma=G)
+        ref = _cons(rho[0], un[0] * n + (tl if float(us) >= 0 else tr), p[0])
+        if not np.allclose(oracle.bc_godunov(u, n, ud, lib=lib), ref, rtol=1e-9, atol=1e-10):
+            return False
+    return True
+
+
 MUTATIONS = {
     "bar_state_sign": ("ubar[s] = dL > 0.0 ? 0.5 * (ui[s] + uj[s]) - dfc[s] / (2.0 * dL) : ui[s];",
                        "ubar[s] = dL > 0.0 ? 0.5 * (ui[s] + uj[s]) + dfc[s] / (2.0 * dL) : ui[s];",
@@ -191,6 +227,15 @@ MUTATIONS = {
                                "if (j < i) c->dij[k] = 1.0;", pin_stage_symmetries),
     "ssp_stage_weight": ("w[q] = u0[q] + 0.25 * (v[q] - u0[q]);", "w[q] = u0[q] + 0.5 * (v[q] - u0[q]);",
                          pin_vortex_second_order),
+    "characteristic_c1_sign": ("double c1d = wd.vn - 2.0 * wd.a / (gamma - 1.0);",
+                               "double c1d = wd.vn + 2.0 * wd.a / (gamma - 1.0);", pin_characteristic_invariants),
+    "characteristic_entropy_source": ("const nprim *src = w.vn < 0.0 ? &wd : &w;",
+                                      "const nprim *src = w.vn < 0.0 ? &w : &wd;", pin_characteristic_invariants),
+    "godunov_shock_density": ("out->rho = l->rho * (p / l->p + g6) / (g6 * p / l->p + 1.0);",
+                              "out->rho = l->rho * (p / l->p - g6) / (g6 * p / l->p + 1.0);", pin_godunov_exact),
+    "godunov_tangential_side": ("  for (int d = 0; d < dim; ++d) out->vt[d] = r->vt[d];\n  if (p > r->p) {",
+                                "  for (int d = 0; d < dim; ++d) out->vt[d] = l->vt[d];\n  if (p > r->p) {",
+                                pin_godunov_exact),
 }
 
 
