@@ -46,7 +46,15 @@ typedef enum {
 /* Boundary kinds (Sec. 4): slip (eq. slip_bc), supersonic inflow = Dirichlet
  * state (eq. Supersonic_inflow), supersonic outflow = do nothing
  * (eq. Supersonic_outflow). */
-enum { EH_BC_SLIP = 1, EH_BC_DIRICHLET = 2, EH_BC_DO_NOTHING = 3 };
+/* Boundary kinds (Sec. 4): slip (eq. slip_bc), Dirichlet / supersonic inflow
+ * (eq. Supersonic_inflow), do nothing (supersonic outflow, eq.
+ * Supersonic_outflow), and the two non-reflecting post-processings of
+ * Sec. 4.2 with the node's outward normal and its Dirichlet (far-field)
+ * state: by characteristic variables (eqs. Supersonic_inflow, Subsonic_inflow,
+ * Subsonic_outflow, Supersonic_outflow, chosen by the node's normal velocity
+ * and sound speed) and by the exact Riemann value at the boundary (eq.
+ * Godunov_bc). */
+enum { EH_BC_SLIP = 1, EH_BC_DIRICHLET = 2, EH_BC_DO_NOTHING = 3, EH_BC_CHARACTERISTIC = 4, EH_BC_GODUNOV = 5 };
 
 /* Arithmetic of the step. FP64: everything in IEEE double. MIXED: c_ij,
  * lambda_max, d_ij and the high-order fluxes in FP32; state, bounds, limiter
@@ -93,9 +101,12 @@ eh_status eh_create(const eh_config *cfg, eh_ctx **out);
  *   mij[nnz]      : consistent mass m_ij; mi[n]: lumped mass m_i > 0
  *   n_bnd, bnd_node[n_bnd], bnd_kind[n_bnd] (EH_BC_*): every node on the
  *                   boundary, once (nodes not listed are interior)
- *   bnd_normal[dim][n_bnd] : unit slip normal n^s_i of eq. def_ns_nio (read for slip nodes)
- *   bnd_state[S][n_bnd]    : Dirichlet states (read for Dirichlet nodes; may be
- *                            NULL if there are none)
+ *   bnd_normal[dim][n_bnd] : unit normal of the node's kind: n^s_i of eq.
+ *                            def_ns_nio for slip nodes, n^nr_i (the normalised
+ *                            integral of phi_i n over the non-reflecting faces)
+ *                            for non-reflecting nodes
+ *   bnd_state[S][n_bnd]    : Dirichlet / far-field states (read for Dirichlet and
+ *                            non-reflecting nodes; may be NULL if there are none)
  * The library builds the transpose index itself. Errors: EH_ERR_BAD_MESH for
  * an invalid pattern or boundary list, EH_ERR_OOM. A second call replaces the
  * mesh and invalidates the state. */

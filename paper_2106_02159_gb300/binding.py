@@ -24,7 +24,7 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", 
 
 EH_OK, EH_ERR_INVALID_ARG, EH_ERR_OOM, EH_ERR_BAD_MESH = 0, 1, 2, 3
 EH_ERR_NOT_ADMISSIBLE, EH_ERR_CFL, EH_ERR_CUDA, EH_ERR_STATE = 4, 5, 6, 7
-EH_BC_SLIP, EH_BC_DIRICHLET, EH_BC_DO_NOTHING = 1, 2, 3
+EH_BC_SLIP, EH_BC_DIRICHLET, EH_BC_DO_NOTHING, EH_BC_CHARACTERISTIC, EH_BC_GODUNOV = 1, 2, 3, 4, 5
 EH_PRECISION_FP64, EH_PRECISION_MIXED = 0, 1
 (EH_TRACE_D_IJ, EH_TRACE_ALPHA, EH_TRACE_U_LOW, EH_TRACE_F_HIGH, EH_TRACE_BOUNDS, EH_TRACE_L_PASS1,
  EH_TRACE_U_PASS1, EH_TRACE_TAU, EH_TRACE_TAU_BOUND) = range(9)

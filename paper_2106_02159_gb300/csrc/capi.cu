@@ -499,9 +499,10 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   for (int b = 0; b < n_bnd; ++b) {
     const int i = bnd_node[b];
     if (i < 0 || i >= n || bidx[i] >= 0) return fail(c, EH_ERR_BAD_MESH, "boundary node %d invalid or repeated", i);
-    if (bnd_kind[b] < EH_BC_SLIP || bnd_kind[b] > EH_BC_DO_NOTHING)
+    if (bnd_kind[b] < EH_BC_SLIP || bnd_kind[b] > EH_BC_GODUNOV)
       return fail(c, EH_ERR_BAD_MESH, "boundary kind %d invalid", bnd_kind[b]);
-    if (bnd_kind[b] == EH_BC_DIRICHLET && !bnd_state) return fail(c, EH_ERR_BAD_MESH, "Dirichlet node without state");
+    if (bnd_kind[b] != EH_BC_SLIP && bnd_kind[b] != EH_BC_DO_NOTHING && !bnd_state)
+      return fail(c, EH_ERR_BAD_MESH, "boundary kind %d needs a Dirichlet state", bnd_kind[b]);
     isb[i] = 1;
     bidx[i] = b;
   }
@@ -712,8 +713,8 @@ eh_status eh_apply_boundary_conditions(eh_ctx *c) {
   eh_status st = require_ready(c);
   if (st) return st;
   CUDA_TRY(c, cudaSetDevice(c->device));
-  if (c->cfg.dim == 2) launch_apply_bc<2>(c->mv, c->U, c->stream);
-  else launch_apply_bc<3>(c->mv, c->U, c->stream);
+  if (c->cfg.dim == 2) launch_apply_bc<2>(c->mv, c->prm, c->U, c->stream);
+  else launch_apply_bc<3>(c->mv, c->prm, c->U, c->stream);
   CUDA_TRY(c, cudaGetLastError());
   return EH_OK;
 }

@@ -1053,8 +1053,166 @@ __global__ void __launch_bounds__(256) k_ls_iterate(MeshView m, Params p, Work w
 // k_final: last limited update, boundary post-processing (Sec. 4), SSP
 // combination (Sec. 4.1) and admissibility check
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Sec. 4.2: non-reflecting post-processing of one state along the unit
+// outward normal nv with the far-field (Dirichlet) state ud
+// ---------------------------------------------------------------------------
+template <int DIM> struct NormalState {
+  double rho, un, ut[DIM], p, c;  // density, normal and tangential velocity, pressure, sound speed
+};
+
 template <int DIM>
-__device__ __forceinline__ void apply_bc_node(const MeshView &m, int i, double *u) {
+__device__ NormalState<DIM> split_normal(const double *u, const double *nv, double gamma) {
+  NormalState<DIM> w;
+  w.rho = u[0];
+  const double ir = 1.0 / u[0];
+  double un = 0.0, v2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) {
+    const double v = u[1 + q] * ir;
+    un += v * nv[q];
+    v2 += v * v;
+  }
+  w.un = un;
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) w.ut[q] = u[1 + q] * ir - un * nv[q];
+  w.p = (gamma - 1.0) * (u[DIM + 1] - 0.5 * u[0] * v2);
+  w.c = sqrt(gamma * w.p * ir);
+  return w;
+}
+
+template <int DIM>
+__device__ void join_normal(double rho, double un, const double *ut, double pr, const double *nv, double gamma,
+                            double *u) {
+  u[0] = rho;
+  double v2 = 0.0;
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) {
+    const double v = ut[q] + un * nv[q];
+    u[1 + q] = rho * v;
+    v2 += v * v;
+  }
+  u[DIM + 1] = pr / (gamma - 1.0) + 0.5 * rho * v2;
+}
+
+// Sec. 4.2.2: incoming characteristics (C_1 = u_n - 2c/(gamma-1) at speed
+// u_n - c; entropy p rho^-gamma and tangential velocity at u_n; C_3 = u_n +
+// 2c/(gamma-1) at u_n + c) take the far-field values, outgoing ones keep the
+// node's: eqs. Supersonic_inflow, Subsonic_inflow, Subsonic_outflow,
+// Supersonic_outflow.
+template <int DIM>
+__device__ void bc_characteristic(double *u, const double *nv, const double *ud, double gamma) {
+  const NormalState<DIM> in = split_normal<DIM>(u, nv, gamma);
+  if (in.un < 0.0 && -in.un > in.c) {  // every wave enters
+#pragma unroll
+    for (int s = 0; s < DIM + 2; ++s) u[s] = ud[s];
+    return;
+  }
+  if (in.un >= 0.0 && in.un >= in.c) return;  // every wave leaves
+  const NormalState<DIM> far = split_normal<DIM>(ud, nv, gamma);
+  const double k = 2.0 / (gamma - 1.0);
+  const double c3 = in.un + k * in.c, c1 = far.un - k * far.c;
+  const NormalState<DIM> &up = in.un < 0.0 ? far : in;  // source of entropy and tangential velocity
+  const double ent = up.p * pow(up.rho, -gamma);
+  const double cp = 0.25 * (gamma - 1.0) * (c3 - c1);
+  const double rho = pow(cp * cp / (gamma * ent), 1.0 / (gamma - 1.0));
+  join_normal<DIM>(rho, 0.5 * (c1 + c3), up.ut, ent * pow(rho, gamma), nv, gamma, u);
+}
+
+// wave curve of side w through its state: the jump in normal velocity across
+// a 1- or 3-wave that leads to pressure p, and its derivative in p
+template <int DIM>
+__device__ void wave_curve(double p, const NormalState<DIM> &w, double gamma, double *f, double *df) {
+  if (p > w.p) {  // shock (Rankine-Hugoniot)
+    const double A = 2.0 / ((gamma + 1.0) * w.rho), B = w.p * (gamma - 1.0) / (gamma + 1.0);
+    const double r = sqrt(A / (B + p));
+    *f = (p - w.p) * r;
+    *df = r * (1.0 - 0.5 * (p - w.p) / (B + p));
+  } else {  // rarefaction (isentropic)
+    const double e = 0.5 * (gamma - 1.0) / gamma;
+    const double q = pow(p / w.p, e);
+    *f = 2.0 * w.c / (gamma - 1.0) * (q - 1.0);
+    *df = q * w.c / (gamma * p);
+  }
+}
+
+// Sec. 4.2.1, eq. Godunov_bc: the exact solution at x/t = 0 of the Riemann
+// problem along nv with the node's state on the inside (left) and the far
+// field outside (right)
+template <int DIM>
+__device__ void bc_godunov(double *u, const double *nv, const double *ud, double gamma) {
+  const NormalState<DIM> L = split_normal<DIM>(u, nv, gamma), R = split_normal<DIM>(ud, nv, gamma);
+  const double gm = gamma - 1.0, gp = gamma + 1.0, e = 0.5 * gm / gamma;
+  const double jump = R.un - L.un;
+  double rho, un, pr;
+  const double *ut;
+  if (2.0 * (L.c + R.c) / gm <= jump) {  // vacuum between two rarefactions
+    const double head_l = L.un - L.c, edge_l = L.un + 2.0 * L.c / gm;
+    const double edge_r = R.un - 2.0 * R.c / gm, head_r = R.un + R.c;
+    if (head_l >= 0.0) {
+      rho = L.rho; un = L.un; pr = L.p; ut = L.ut;
+    } else if (edge_l > 0.0) {
+      const double c = 2.0 / gp * (L.c + 0.5 * gm * L.un);
+      rho = L.rho * pow(c / L.c, 2.0 / gm); un = c; pr = L.p * pow(c / L.c, 1.0 / e); ut = L.ut;
+    } else if (edge_r >= 0.0) {
+      rho = 0.0; un = 0.0; pr = 0.0; ut = L.ut;
+    } else if (head_r > 0.0) {
+      const double c = 2.0 / gp * (R.c - 0.5 * gm * R.un);
+      rho = R.rho * pow(c / R.c, 2.0 / gm); un = -c; pr = R.p * pow(c / R.c, 1.0 / e); ut = R.ut;
+    } else {
+      rho = R.rho; un = R.un; pr = R.p; ut = R.ut;
+    }
+    join_normal<DIM>(rho, un, ut, pr, nv, gamma, u);
+    if (rho == 0.0) {
+#pragma unroll
+      for (int s = 0; s < DIM + 2; ++s) u[s] = 0.0;
+    }
+    return;
+  }
+  // star pressure: Newton from the two-rarefaction value to a relative change of 1e-15
+  double ps = pow((L.c + R.c - 0.5 * gm * jump) / (L.c * pow(L.p, -e) + R.c * pow(R.p, -e)), 1.0 / e);
+  for (int it = 0; it < 100; ++it) {
+    double fl, dl, fr, dr;
+    wave_curve<DIM>(ps, L, gamma, &fl, &dl);
+    wave_curve<DIM>(ps, R, gamma, &fr, &dr);
+    double pn = ps - (fl + fr + jump) / (dl + dr);
+    if (!(pn > 0.0)) pn = 0.5 * ps;
+    const double rel = fabs(pn - ps) / (0.5 * (pn + ps));
+    ps = pn;
+    if (rel < 1e-15) break;
+  }
+  double fl, dl, fr, dr;
+  wave_curve<DIM>(ps, L, gamma, &fl, &dl);
+  wave_curve<DIM>(ps, R, gamma, &fr, &dr);
+  const double us = 0.5 * (L.un + R.un + fr - fl);  // contact speed
+  const bool left = us >= 0.0;
+  const NormalState<DIM> &K = left ? L : R;
+  const double sgn = left ? 1.0 : -1.0;  // mirror the right side onto the left
+  ut = K.ut;
+  const double uk = sgn * K.un, ustar = sgn * us;
+  if (ps > K.p) {  // shock moving away from the contact
+    const double speed = uk - K.c * sqrt(0.5 * gp / gamma * ps / K.p + e);
+    if (speed >= 0.0) {
+      rho = K.rho; un = K.un; pr = K.p;
+    } else {
+      const double r = ps / K.p, g6 = gm / gp;
+      rho = K.rho * (r + g6) / (g6 * r + 1.0); un = us; pr = ps;
+    }
+  } else if (uk - K.c >= 0.0) {  // rarefaction entirely on the far side of x = 0
+    rho = K.rho; un = K.un; pr = K.p;
+  } else if (ustar - K.c * pow(ps / K.p, e) < 0.0) {  // x = 0 in the star region
+    rho = K.rho * pow(ps / K.p, 1.0 / gamma); un = us; pr = ps;
+  } else {  // x = 0 inside the rarefaction fan
+    const double c = 2.0 / gp * (K.c + 0.5 * gm * uk);
+    rho = K.rho * pow(c / K.c, 2.0 / gm); un = sgn * c; pr = K.p * pow(c / K.c, 1.0 / e);
+  }
+  join_normal<DIM>(rho, un, ut, pr, nv, gamma, u);
+}
+
+// Sec. 4: slip (M <- M - (M . n^s) n^s), Dirichlet / supersonic inflow
+// (U <- U^D), do nothing, and the two non-reflecting post-processings
+template <int DIM>
+__device__ __forceinline__ void apply_bc_node(const MeshView &m, const Params &p, int i, double *u) {
   const int b = m.bnd_index[i];
   if (b < 0) return;
   const int kind = m.bnd_kind[b];
@@ -1067,6 +1225,16 @@ __device__ __forceinline__ void apply_bc_node(const MeshView &m, int i, double *
   } else if (kind == 2) {  // supersonic inflow: U <- U^D
 #pragma unroll
     for (int s = 0; s < DIM + 2; ++s) u[s] = m.bnd_state[(int64_t)s * m.n_bnd + b];
+  } else if (kind == 4 || kind == 5) {
+    double nv[DIM], ud[DIM + 2];
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) nv[q] = m.bnd_normal[(int64_t)q * m.n_bnd + b];
+#pragma unroll
+    for (int s = 0; s < DIM + 2; ++s) ud[s] = m.bnd_state[(int64_t)s * m.n_bnd + b];
+    if (kind == 4)
+      bc_characteristic<DIM>(u, nv, ud, p.gamma);
+    else
+      bc_godunov<DIM>(u, nv, ud, p.gamma);
   }
 }
 
@@ -1103,7 +1271,7 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
   }
   // a finished instance (tau = 0) keeps its state bit for bit: the stage is
   // the identity there, and re-applying the post-processing would not be
-  if (w.tau_inst[m.inst ? m.inst[i] : 0] != 0.0) apply_bc_node<DIM>(m, i, u);
+  if (w.tau_inst[m.inst ? m.inst[i] : 0] != 0.0) apply_bc_node<DIM>(m, p, i, u);
   if (coef >= 0.0) {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -1129,13 +1297,13 @@ __global__ void __launch_bounds__(TPB_MAX) k_final(MeshView m, Params p, Work w,
   }
 }
 
-template <int DIM> __global__ void k_apply_bc(MeshView m, double *U) {
+template <int DIM> __global__ void k_apply_bc(MeshView m, Params p, double *U) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || m.bnd_index[i] < 0) return;
   double u[DIM + 2];
 #pragma unroll
   for (int s = 0; s < DIM + 2; ++s) u[s] = U[(int64_t)s * m.n + i];
-  apply_bc_node<DIM>(m, i, u);
+  apply_bc_node<DIM>(m, p, i, u);
 #pragma unroll
   for (int s = 0; s < DIM + 2; ++s) U[(int64_t)s * m.n + i] = u[s];
 }
@@ -1201,8 +1369,8 @@ void launch_final(const MeshView &m, const Params &p, const Work &w, const doubl
                   cudaStream_t s) {
   k_final<DIM><<<capped_grid(m.n, tpb, max_blocks), tpb, 0, s>>>(m, p, w, Uin, lin, U0, coef, out, Upre_trace);
 }
-template <int DIM> void launch_apply_bc(const MeshView &m, double *U, cudaStream_t s) {
-  k_apply_bc<DIM><<<nblocks(m.n, 256), 256, 0, s>>>(m, U);
+template <int DIM> void launch_apply_bc(const MeshView &m, const Params &p, double *U, cudaStream_t s) {
+  k_apply_bc<DIM><<<nblocks(m.n, 256), 256, 0, s>>>(m, p, U);
 }
 template <int DIM> void launch_count_not_admissible(int n, const double *U, DevStatus *st, cudaStream_t s) {
   k_count_not_admissible<DIM><<<nblocks(n, 256), 256, 0, s>>>(n, U, st);
@@ -1227,7 +1395,7 @@ EH_INSTANTIATE_T(3, float)
                                         int, cudaStream_t);                                                          \
   template void launch_final<DIM>(const MeshView &, const Params &, const Work &, const double *, const double *,     \
                                   const double *, double, double *, double *, int, int, cudaStream_t);                \
-  template void launch_apply_bc<DIM>(const MeshView &, double *, cudaStream_t);                                       \
+  template void launch_apply_bc<DIM>(const MeshView &, const Params &, double *, cudaStream_t);                       \
   template void launch_count_not_admissible<DIM>(int, const double *, DevStatus *, cudaStream_t);
 
 EH_INSTANTIATE(2)

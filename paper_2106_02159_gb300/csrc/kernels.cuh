@@ -183,7 +183,7 @@ template <int DIM>
 void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,
                   const double *U0, double coef, double *out, double *Upre_trace, int tpb, int max_blocks,
                   cudaStream_t s);
-template <int DIM> void launch_apply_bc(const MeshView &m, double *U, cudaStream_t s);
+template <int DIM> void launch_apply_bc(const MeshView &m, const Params &p, double *U, cudaStream_t s);
 template <int DIM> void launch_count_not_admissible(int n, const double *U, DevStatus *st, cudaStream_t s);
 
 }  // namespace eh

@@ -26,6 +26,8 @@ import numpy as np
 BC_SLIP = 1
 BC_DIRICHLET = 2
 BC_DO_NOTHING = 3
+BC_CHARACTERISTIC = 4  # non-reflecting, by characteristic variables (Sec. 4.2.2)
+BC_GODUNOV = 5         # non-reflecting, by the exact Riemann value (Sec. 4.2.1)
 
 
 @dataclasses.dataclass
@@ -241,16 +243,18 @@ def _boundary(n, dim, faces, face_xyz, face_kind, cell_centroid):
     full = np.zeros((n, dim))
     slip = np.zeros((n, dim))
     nonslip = np.zeros((n, dim))
-    touch = np.zeros((n, 4), dtype=bool)
+    touch = np.zeros((n, 6), dtype=bool)
     for d in range(dim):
         full[:, d] = np.bincount(nodes, weights=vec[:, d], minlength=n)
         slip[:, d] = np.bincount(nodes[kinds == BC_SLIP], weights=vec[kinds == BC_SLIP, d], minlength=n)
         nonslip[:, d] = np.bincount(nodes[kinds != BC_SLIP], weights=vec[kinds != BC_SLIP, d], minlength=n)
-    for kd in (BC_SLIP, BC_DIRICHLET, BC_DO_NOTHING):
+    for kd in (BC_SLIP, BC_DIRICHLET, BC_DO_NOTHING, BC_CHARACTERISTIC, BC_GODUNOV):
         touch[np.unique(nodes[kinds == kd]), kd] = True
     bnodes = np.unique(nodes)
-    # kind priority: inflow (Dirichlet) > slip > do-nothing
+    # kind priority: inflow (Dirichlet) > slip > non-reflecting > do-nothing
     kind = np.full(bnodes.size, BC_DO_NOTHING, dtype=np.int32)
+    kind[touch[bnodes, BC_CHARACTERISTIC]] = BC_CHARACTERISTIC
+    kind[touch[bnodes, BC_GODUNOV]] = BC_GODUNOV
     kind[touch[bnodes, BC_SLIP]] = BC_SLIP
     kind[touch[bnodes, BC_DIRICHLET]] = BC_DIRICHLET
     vs = slip[bnodes]

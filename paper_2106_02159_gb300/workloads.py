@@ -121,6 +121,44 @@ def cylinder_problem(m: int, gamma=1.4):
     return mesh, U0, bnd_state
 
 
+# --------------------------------------------------------------------------
+# non-reflecting boundary tests (Sec. 6: vortex leaving [-1,1]^2)
+# --------------------------------------------------------------------------
+
+# case: (Mach number of the free stream, velocity perturbation of the vortex)
+NRBC_CASES = {"i": (0.5, 0.75), "ii": (0.5, 0.25), "iii": (0.05, 0.75), "iv": (0.05, 0.25)}
+
+
+def nrbc_vortex_state(x, mach, vbar, r0=0.1, gamma=1.4, center=(0.0, 0.0)):
+    """rho = 1, v = (1, 0) + vbar/r0 psi(r) (-(y - y0), x - x0), p = p_inf -
+    vbar^2 psi(r)^2 / 2 with psi(r) = exp((1 - r^2/r0^2)/2) and p_inf =
+    a_inf^2/gamma, a_inf = 1/mach. The paper leaves r0 and the centre to the
+    cited test suite; here r0 = 0.1 and the centre is the origin (so the centre
+    crosses x = 1 at t = 1)."""
+    dx = x[:, 0] - center[0]
+    dy = x[:, 1] - center[1]
+    psi = np.exp(0.5 * (1.0 - (dx * dx + dy * dy) / (r0 * r0)))
+    p_inf = (1.0 / mach) ** 2 / gamma
+    vx = 1.0 - vbar / r0 * psi * dy
+    vy = vbar / r0 * psi * dx
+    return conserved(np.ones(x.shape[0]), [vx, vy], p_inf - 0.5 * vbar * vbar * psi * psi, gamma)
+
+
+def nrbc_vortex_problem(n_cells=80, case="i", kind=None, r0=0.1, gamma=1.4):
+    """The vortex of ``nrbc_vortex_state`` on an n_cells x n_cells Q1 mesh of
+    [-1,1]^2 with a non-reflecting kind (default: characteristic) on all four
+    sides and the free stream as far-field state. Returns (mesh, U0, bnd_state)."""
+    kind = meshes.BC_CHARACTERISTIC if kind is None else kind
+    mach, vbar = NRBC_CASES[case]
+    mesh = meshes.structured_q1(n_cells, n_cells, -1.0, 1.0, -1.0, 1.0, kinds=(kind,) * 4,
+                                name=f"nrbc-q1-{n_cells}-{case}-k{kind}")
+    U0 = nrbc_vortex_state(mesh.coords, mach, vbar, r0, gamma)
+    p_inf = (1.0 / mach) ** 2 / gamma
+    far = conserved(np.ones(mesh.bnd_node.size), [np.ones(mesh.bnd_node.size), np.zeros(mesh.bnd_node.size)],
+                    np.full(mesh.bnd_node.size, p_inf), gamma)
+    return mesh, U0, np.ascontiguousarray(far)
+
+
 @dataclasses.dataclass
 class Workload:
     name: str
