@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("cylinder", "vortex", "batch", "serve", "cylinder3d"),
+    ap.add_argument("--workload", choices=("cylinder", "vortex", "batch", "serve", "cylinder3d", "nrbc"),
                     default="cylinder")
     ap.add_argument("--requests", type=int, default=48, help="serve workload: requests in the trace")
     ap.add_argument("--instances", type=int, default=256, help="batch workload: number of instances")
@@ -678,6 +678,83 @@ def run_cylinder3d(args, dist):
         print(json.dumps(line), flush=True)
 
 
+def nrbc_deltas(mesh, U, curl0_max):
+    """delta_1 = max |v - v_inf| / |v_inf| and delta_2 = max |curl v| / max |curl v_0|
+    over the nodes (Sec. 6, non-reflecting conditions), with v_inf = (1, 0) and
+    the nodal curl of the lumped Galerkin projection, (curl v)_i = (1/m_i)
+    sum_j (c_ij,x v_j,y - c_ij,y v_j,x)."""
+    v = U[1:3] / U[0]
+    d1 = float(np.sqrt((v[0] - 1.0) ** 2 + v[1] ** 2).max())
+    rows = mesh.row_of_entry()
+    cv = mesh.cij[0] * v[1, mesh.col] - mesh.cij[1] * v[0, mesh.col]
+    curl = np.bincount(rows, weights=cv, minlength=mesh.n) / mesh.mi
+    cmax = float(np.abs(curl).max())
+    return d1, (cmax / curl0_max if curl0_max else cmax)
+
+
+def run_nrbc(args, dist):
+    """The non-reflecting boundary tests of Sec. 6: a vortex (r0 = 0.1) carried
+    by a unit free stream out of [-1,1]^2 on an 80 x 80 Q1 mesh, CFL 0.75,
+    strict bounds, to t = 4, for the four (Mach, perturbation) cases, with the
+    characteristic and the Godunov post-processing on all four sides (and
+    do-nothing as a reflecting reference): delta_1(t), delta_2(t)."""
+    import torch
+    from paper_2106_02159_gb300 import binding, meshes, workloads
+    torch.cuda.set_device(dist.local_rank)
+    binding.build()
+    if dist.rank != 0:
+        return
+    kinds = {"characteristic": meshes.BC_CHARACTERISTIC, "godunov": meshes.BC_GODUNOV,
+             "do_nothing": meshes.BC_DO_NOTHING}
+    samples = (0.5, 1.0, 1.5, 2.0, 3.0, 4.0)
+    results, total_dof, total_ms = {}, 0.0, 0.0
+    for case in sorted(workloads.NRBC_CASES):
+        for kname, kind in kinds.items():
+            mesh, U0, bs = workloads.nrbc_vortex_problem(80, case, kind)
+            v0 = U0[1:3] / U0[0]
+            rows = mesh.row_of_entry()
+            c0 = np.bincount(rows, weights=mesh.cij[0] * v0[1, mesh.col] - mesh.cij[1] * v0[0, mesh.col],
+                             minlength=mesh.n) / mesh.mi
+            c0max = float(np.abs(c0).max())
+            stream = torch.cuda.Stream()
+            s = binding.Solver(dim=2, cfl=0.75, stream=stream.cuda_stream)
+            s.upload_mesh(mesh, bs)
+            s.set_instances([0, mesh.n], [4.0])
+            s.set_state(U0)
+            s.apply_boundary_conditions()
+            series, steps, k = [], 0, 0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            while True:
+                e0.record(stream)
+                s.run(20)
+                e1.record(stream)
+                stream.synchronize()
+                total_ms += e0.elapsed_time(e1)
+                steps += 20
+                t = float(s.instances()["t"][0])
+                while k < len(samples) and t >= samples[k] - 1e-12:
+                    d1, d2 = nrbc_deltas(mesh, s.get_state(), c0max)
+                    series.append({"t": round(t, 4), "delta_1": d1, "delta_2": d2})
+                    k += 1
+                if t >= 4.0 or k >= len(samples):
+                    break
+            total_dof += mesh.n * 3 * steps
+            results[f"{case}/{kname}"] = {"mach": workloads.NRBC_CASES[case][0],
+                                          "vbar": workloads.NRBC_CASES[case][1], "steps": steps,
+                                          "violations": s.diagnostics()["not_admissible"], "deltas": series}
+            s.close()
+    line = {"metric": "delta_1(t), delta_2(t) of the vortex leaving the box (non-reflecting conditions)",
+            "value": None, "unit": "1", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+            "dtype": "f64",
+            "config": {"workload": "Sec. 6 non-reflecting tests: [-1,1]^2, 80x80 Q1, rho=1, v_inf=(1,0), "
+                                   "r0=0.1, CFL 0.75, strict bounds, t in [0, 4]",
+                       "cases": {k: list(v) for k, v in workloads.NRBC_CASES.items()}},
+            "throughput": {"value": total_dof / (total_ms * 1e-3), "unit": UNIT,
+                           "what": "all 12 runs, device time of the steps (6561-vertex meshes: launch-bound)"},
+            "results": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     dist = Dist()
@@ -690,6 +767,8 @@ def main():
             run_serve(args, dist)
         elif args.workload == "cylinder3d":
             run_cylinder3d(args, dist)
+        elif args.workload == "nrbc":
+            run_nrbc(args, dist)
         else:
             run_ours(args, dist)
     finally:
