@@ -722,16 +722,21 @@ def run_nrbc(args, dist):
             s.set_instances([0, mesh.n], [4.0])
             s.set_state(U0)
             s.apply_boundary_conditions()
-            series, steps, k = [], 0, 0
+            series, steps, k, failure, t = [], 0, 0, None, 0.0
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             while True:
                 e0.record(stream)
                 s.run(20)
                 e1.record(stream)
                 stream.synchronize()
+                try:
+                    t_now = float(s.instances()["t"][0])
+                except binding.EulerError as e:  # e.g. a non-admissible state: record it and stop this run
+                    failure = {"after_steps": steps + 20, "last_t": t, "error": str(e)}
+                    break
                 total_ms += e0.elapsed_time(e1)
                 steps += 20
-                t = float(s.instances()["t"][0])
+                t = t_now
                 while k < len(samples) and t >= samples[k] - 1e-12:
                     d1, d2 = nrbc_deltas(mesh, s.get_state(), c0max)
                     series.append({"t": round(t, 4), "delta_1": d1, "delta_2": d2})
@@ -741,7 +746,7 @@ def run_nrbc(args, dist):
             total_dof += mesh.n * 3 * steps
             results[f"{case}/{kname}"] = {"mach": workloads.NRBC_CASES[case][0],
                                           "vbar": workloads.NRBC_CASES[case][1], "steps": steps,
-                                          "violations": s.diagnostics()["not_admissible"], "deltas": series}
+                                          "failure": failure, "deltas": series}
             s.close()
     line = {"metric": "delta_1(t), delta_2(t) of the vortex leaving the box (non-reflecting conditions)",
             "value": None, "unit": "1", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
