@@ -110,6 +110,9 @@ def _bind(lib):
     lib.oracle_apply_bc.argtypes = [ctypes.c_void_p, dp]
     lib.oracle_ssprk3_step.restype = ctypes.c_int
     lib.oracle_ssprk3_step.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, dp, dp]
+    lib.oracle_ssprk3_step_adaptive.restype = ctypes.c_int
+    lib.oracle_ssprk3_step_adaptive.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, dp, dp,
+                                                ctypes.POINTER(ctypes.c_int)]
     lib.oracle_run.restype = ctypes.c_int
     lib.oracle_run.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, ctypes.c_double, dp]
     lib.oracle_run_to.restype = ctypes.c_int
@@ -309,6 +312,18 @@ class Oracle:
         if st:
             raise OracleError(f"oracle_ssprk3_step failed with status {st}")
         return U, used.value, bounds
+
+    def ssprk3_step_adaptive(self, U, cfl_max):
+        """One SSPRK(3,3) step with the CFL number adapted above 1 (restart with
+        half the CFL number while a low-order state leaves the admissible set);
+        returns (U_new, dt_used, cfl_used, restarts)."""
+        U = np.array(self._state(U), copy=True)
+        dt, cfl, r = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int(0)
+        st = self.lib.oracle_ssprk3_step_adaptive(self._ctx, _dptr(U), float(cfl_max), ctypes.byref(dt),
+                                                  ctypes.byref(cfl), ctypes.byref(r))
+        if st:
+            raise OracleError(f"oracle_ssprk3_step_adaptive failed with status {st}")
+        return U, dt.value, cfl.value, r.value
 
     def run(self, U, nsteps, dt=0.0):
         U = np.array(self._state(U), copy=True)

@@ -118,6 +118,9 @@ typedef struct {
   double *relax;         /* [n] r_i, or 0 */
   /* work arrays */
   double *dij, *alpha, *UL, *FH, *bounds, *P, *lij, *lraw, *Ucur, *Unext;
+  /* nodes whose low-order update U^L left the admissible set, summed over
+   * the stages since the last reset (the check of the adaptive CFL step) */
+  int64_t low_not_admissible;
 } oracle_ctx;
 
 /* ------------------------------------------------------------------------- */
@@ -568,6 +571,14 @@ int oracle_forward_euler(oracle_ctx *c, const double *U, double tau, double *Uou
       c->UL[s * n + i] = ui[s] + 2.0 * tau / p->mi[i] * inc[s];
       c->FH[s * n + i] = fh[s];
     }
+    {
+      double ul[MAXS];
+      for (int s = 0; s < S; ++s) ul[s] = c->UL[s * n + i];
+      if (!(ul[0] > 0.0 && internal_energy(ul, dim) > 0.0)) {
+#pragma omp atomic
+        c->low_not_admissible += 1;
+      }
+    }
     /* optional relaxation of the local bounds (off by default) */
     double r = c->relax[i];
     c->bounds[0 * n + i] = (1.0 - r) * rho_min;
@@ -879,6 +890,50 @@ void oracle_apply_bc(const oracle_ctx *c, double *U) {
 /* U is advanced in place. dt > 0: use it; dt <= 0: the CFL step of the first
  * stage, reused by the other two stages (Sec. 3.1). stage_tau_bound (may be
  * NULL) receives the three stages' own CFL bounds. */
+/* Remark "High aspect-ratio meshes" (Sec. 3.1): one SSPRK(3,3) step with a
+ * CFL number above 1. The step is tried with c_cfl = cfl_max; if the
+ * low-order update U^L of any stage, or the result, leaves the admissible set,
+ * the step restarts from U with c_cfl halved, until it passes (c_cfl <= 1
+ * always passes: U^L is then a convex combination of admissible bar states).
+ * U is advanced in place; dt_used, cfl_used and restarts (may be NULL)
+ * receive the accepted step, its CFL number and the number of restarts. */
+int oracle_ssprk3_step(oracle_ctx *c, double *U, double dt, double *dt_used, double *stage_tau_bound);
+
+int oracle_ssprk3_step_adaptive(oracle_ctx *c, double *U, double cfl_max, double *dt_used, double *cfl_used,
+                                int *restarts) {
+  if (!(cfl_max > 0.0)) return ORACLE_ERR_ARG;
+  size_t bytes = sizeof(double) * c->S * c->p.n;
+  double *u_in = (double *)malloc(bytes);
+  if (!u_in) return ORACLE_ERR_OOM;
+  memcpy(u_in, U, bytes);
+  const double cfl_saved = c->p.cfl;
+  double cfl = cfl_max, dt = 0.0;
+  int r = 0, st;
+  for (;;) {
+    c->p.cfl = cfl;
+    c->low_not_admissible = 0;
+    memcpy(U, u_in, bytes);
+    st = oracle_ssprk3_step(c, U, 0.0, &dt, NULL);
+    int failed = st == ORACLE_ERR_NOT_ADMISSIBLE || (st == ORACLE_OK && (c->low_not_admissible > 0 ||
+                                                                          oracle_count_not_admissible(c, U) > 0));
+    if (st != ORACLE_OK && st != ORACLE_ERR_NOT_ADMISSIBLE) break;
+    if (!failed) break;
+    if (cfl <= 1.0) {
+      st = ORACLE_ERR_NOT_ADMISSIBLE;
+      break;
+    }
+    cfl *= 0.5;
+    ++r;
+  }
+  c->p.cfl = cfl_saved;
+  if (st != ORACLE_OK) memcpy(U, u_in, bytes);
+  free(u_in);
+  if (dt_used) *dt_used = dt;
+  if (cfl_used) *cfl_used = cfl;
+  if (restarts) *restarts = r;
+  return st;
+}
+
 int oracle_ssprk3_step(oracle_ctx *c, double *U, double dt, double *dt_used, double *stage_tau_bound) {
   const oracle_problem *p = &c->p;
   int n = p->n, S = c->S;

@@ -205,6 +205,21 @@ def pin_godunov_exact(lib):
     return True
 
 
+@_safe
+def pin_adaptive_cfl_accepts_admissible_low_order(lib):
+    mesh = W.riemann_strip(120)
+    U0 = W.riemann_initial(mesh, "strong_shock")
+    U, dt, c, r = oracle.Oracle(mesh, cfl=0.5, lib=lib).ssprk3_step_adaptive(U0, 16.0)
+    if not (r >= 1 and c == 16.0 / 2 ** r):
+        return False
+    _, _, stages = H.ssprk3_with_traces(oracle.Oracle(mesh, cfl=c, lib=lib), U0)
+    for _, _, tr in stages:
+        ul = tr["UL"]
+        if not ((ul[0] > 0).all() and (ul[-1] - 0.5 * (ul[1:-1] ** 2).sum(0) / ul[0] > 0).all()):
+            return False
+    return True
+
+
 MUTATIONS = {
     "bar_state_sign": ("ubar[s] = dL > 0.0 ? 0.5 * (ui[s] + uj[s]) - dfc[s] / (2.0 * dL) : ui[s];",
                        "ubar[s] = dL > 0.0 ? 0.5 * (ui[s] + uj[s]) + dfc[s] / (2.0 * dL) : ui[s];",
@@ -233,6 +248,8 @@ MUTATIONS = {
                                       "const nprim *src = w.vn < 0.0 ? &w : &wd;", pin_characteristic_invariants),
     "godunov_shock_density": ("out->rho = l->rho * (p / l->p + g6) / (g6 * p / l->p + 1.0);",
                               "out->rho = l->rho * (p / l->p - g6) / (g6 * p / l->p + 1.0);", pin_godunov_exact),
+    "adaptive_cfl_ignores_low_order_states": ("(st == ORACLE_OK && (c->low_not_admissible > 0 ||",
+                                              "(st == ORACLE_OK && (0 ||", pin_adaptive_cfl_accepts_admissible_low_order),
     "godunov_tangential_side": ("  for (int d = 0; d < dim; ++d) out->vt[d] = r->vt[d];\n  if (p > r->p) {",
                                 "  for (int d = 0; d < dim; ++d) out->vt[d] = l->vt[d];\n  if (p > r->p) {",
                                 pin_godunov_exact),
