@@ -83,6 +83,8 @@ typedef struct {
   int64_t line_searches_deferred; /* limiter line searches (Sec. 3.3) not settled by the check at
                                      l = 1 and run in a separate pass, summed over all steps */
   int64_t line_searches_iterated; /* of those, searches that ran the bracketing iteration */
+  int64_t low_order_not_admissible; /* rows whose low-order update U^L left the admissible set
+                                       (always 0 with c_cfl <= 1; see eh_step_adaptive) */
 } eh_diagnostics;
 
 /* Fills *cfg with the defaults: dim 2, gamma 1.4, cfl 0.5, 2 limiter passes,
@@ -146,6 +148,16 @@ eh_status eh_step(eh_ctx *ctx, double dt, double *dt_used);
 /* nsteps SSPRK(3,3) steps with the same dt rule as eh_step, replayed from a
  * CUDA graph, without synchronising. */
 eh_status eh_run(eh_ctx *ctx, int32_t nsteps, double dt);
+
+/* One SSPRK(3,3) step with a CFL number above 1 (Sec. 3.1, remark on high
+ * aspect-ratio meshes): the step is tried with c_cfl = cfl_max (0 < cfl_max
+ * <= 64) in place of the context's CFL number; while the low-order update U^L
+ * of a stage, or the result, leaves the admissible set, the state and time
+ * are put back and the step restarts with c_cfl halved (c_cfl <= 1 always
+ * passes). Synchronises after every attempt. Outputs (may be NULL): the
+ * accepted dt, its CFL number and the number of restarts. One instance only
+ * (EH_ERR_STATE after eh_set_instances with more than one). */
+eh_status eh_step_adaptive(eh_ctx *ctx, double cfl_max, double *dt_used, double *cfl_used, int32_t *restarts);
 
 /* Waits for queued work and reports a pending device-side error. */
 eh_status eh_synchronize(eh_ctx *ctx);

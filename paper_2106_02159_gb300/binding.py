@@ -34,7 +34,8 @@ EXPORTS = ("eh_config_default", "eh_create", "eh_upload_mesh", "eh_set_state", "
            "eh_apply_boundary_conditions", "eh_cfl_dt", "eh_stage", "eh_step", "eh_run", "eh_synchronize",
            "eh_get_diagnostics", "eh_trace", "eh_profile_enable", "eh_profile_read", "eh_launches_per_step",
            "eh_last_error", "eh_status_string", "eh_destroy", "eh_cfl_dt_noalloc", "eh_set_instances",
-           "eh_get_instances", "eh_autotune", "eh_get_block_sizes", "eh_get_rows_per_sm", "eh_set_launch_shape")
+           "eh_get_instances", "eh_autotune", "eh_get_block_sizes", "eh_get_rows_per_sm", "eh_set_launch_shape",
+           "eh_step_adaptive")
 CFL_NOALLOC_MAX_ROWS = 1 << 23
 KERNEL_NAMES = ("prep", "visc", "low", "tau", "lim1", "pass", "final", "lsearch")
 
@@ -65,7 +66,7 @@ class Diagnostics(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_int64), ("last_dt", ctypes.c_double),
                 ("last_stage_bound", ctypes.c_double * 3), ("cfl_violations", ctypes.c_int64),
                 ("not_admissible", ctypes.c_int64), ("line_searches_deferred", ctypes.c_int64),
-                ("line_searches_iterated", ctypes.c_int64)]
+                ("line_searches_iterated", ctypes.c_int64), ("low_order_not_admissible", ctypes.c_int64)]
 
 
 _lib = None
@@ -111,6 +112,7 @@ def load(path: str | None = None):
     lib.eh_get_block_sizes.argtypes = [vp, vp]
     lib.eh_get_rows_per_sm.argtypes = [vp, vp]
     lib.eh_set_launch_shape.argtypes = [vp, i32, i32, i32]
+    lib.eh_step_adaptive.argtypes = [vp, ctypes.c_double, dp, dp, ctypes.POINTER(i32)]
     lib.eh_cfl_dt_noalloc.argtypes = [i32, ctypes.c_double, ctypes.c_double, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("eh_config_default", "eh_destroy", "eh_launches_per_step", "eh_last_error",
@@ -235,6 +237,13 @@ class Solver:
     def run(self, nsteps, dt=0.0):
         self._check(self.lib.eh_run(self.ctx, int(nsteps), float(dt)), "eh_run")
 
+    def step_adaptive(self, cfl_max):
+        """One step with the CFL number adapted above 1; returns (dt, cfl, restarts)."""
+        dt, cfl, r = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int32(0)
+        self._check(self.lib.eh_step_adaptive(self.ctx, float(cfl_max), ctypes.byref(dt), ctypes.byref(cfl),
+                                              ctypes.byref(r)), "eh_step_adaptive")
+        return dt.value, cfl.value, r.value
+
     def synchronize(self):
         self._check(self.lib.eh_synchronize(self.ctx), "eh_synchronize")
 
@@ -244,7 +253,8 @@ class Solver:
         return dict(t=d.t, steps=d.steps, last_dt=d.last_dt, last_stage_bound=list(d.last_stage_bound),
                     cfl_violations=d.cfl_violations, not_admissible=d.not_admissible,
                     line_searches_deferred=d.line_searches_deferred,
-                    line_searches_iterated=d.line_searches_iterated)
+                    line_searches_iterated=d.line_searches_iterated,
+                    low_order_not_admissible=d.low_order_not_admissible)
 
     def trace(self, what):
         sizes = {EH_TRACE_D_IJ: self.nnz, EH_TRACE_ALPHA: self.n, EH_TRACE_U_LOW: self.S * self.n,

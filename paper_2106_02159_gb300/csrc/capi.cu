@@ -797,6 +797,56 @@ eh_status eh_run(eh_ctx *c, int32_t nsteps, double dt) {
   return EH_OK;
 }
 
+eh_status eh_step_adaptive(eh_ctx *c, double cfl_max, double *dt_used, double *cfl_used, int32_t *restarts) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  if (!(cfl_max > 0.0 && cfl_max <= 64.0)) return EH_ERR_INVALID_ARG;
+  if (c->ninst != 1) return fail(c, EH_ERR_STATE, "eh_step_adaptive runs one instance");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if ((st = check_device_error(c))) return st;
+  const size_t bytes = sizeof(double) * S_of(c) * c->n;
+  double t0 = 0.0;
+  CUDA_TRY(c, cudaMemcpyAsync(c->Usave, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpy(&t0, c->wk.t_inst, sizeof(double), cudaMemcpyDeviceToHost));
+  double cfl = cfl_max;
+  int32_t r = 0;
+  for (;;) {
+    c->prm.cfl = cfl;
+    CUDA_TRY(c, cudaMemsetAsync(&c->st->err, 0, sizeof(int), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(&c->st->low_not_admissible, 0, sizeof(unsigned long long), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(&c->st->not_admissible, 0, sizeof(unsigned long long), c->stream));
+    enqueue_step_any(c, 0.0);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaMemcpy(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost));
+    const int e = c->st_host->err;
+    const bool failed = e == EH_ERR_NOT_ADMISSIBLE || c->st_host->low_not_admissible > 0;
+    if (e && !failed) {
+      c->prm.cfl = c->cfg.cfl;
+      return check_device_error(c);
+    }
+    if (!failed) break;
+    // put the state and the time back; clear the failure
+    CUDA_TRY(c, cudaMemcpyAsync(c->U, c->Usave, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->wk.t_inst, &t0, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(&c->st->err, 0, sizeof(int), c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (cfl <= 1.0) {  // cannot happen for an admissible state: U^L is then invariant-domain preserving
+      c->prm.cfl = c->cfg.cfl;
+      return fail(c, EH_ERR_NOT_ADMISSIBLE, "no admissible step down to c_cfl = %g", cfl);
+    }
+    cfl *= 0.5;
+    ++r;
+  }
+  c->prm.cfl = c->cfg.cfl;
+  c->steps += 1;
+  c->last_stage_traced = false;
+  if (dt_used) *dt_used = c->st_host->tau;
+  if (cfl_used) *cfl_used = cfl;
+  if (restarts) *restarts = r;
+  return EH_OK;
+}
+
 eh_status eh_synchronize(eh_ctx *c) {
   if (!c) return EH_ERR_INVALID_ARG;
   CUDA_TRY(c, cudaSetDevice(c->device));
@@ -818,6 +868,7 @@ eh_status eh_get_diagnostics(eh_ctx *c, eh_diagnostics *out) {
   out->not_admissible = (int64_t)c->st_host->not_admissible;
   out->line_searches_deferred = (int64_t)c->st_host->line_searches_deferred;
   out->line_searches_iterated = (int64_t)c->st_host->line_searches_iterated;
+  out->low_order_not_admissible = (int64_t)c->st_host->low_not_admissible;
   return st;
 }
 

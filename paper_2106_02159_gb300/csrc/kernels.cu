@@ -864,6 +864,16 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
   double *ULi = w.UL + (int64_t)i * SP;
 #pragma unroll
   for (int s = 0; s < S; ++s) ULi[s] = ul[s];
+  {
+    // U^L admissible: rho > 0 and rho E - |M|^2/2 > 0 (no division); with
+    // c_cfl <= 1 it always is (invariant-domain property), above 1 the
+    // adaptive step restarts on it
+    double m2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) m2 += ul[1 + q] * ul[1 + q];
+    if (!(pos_strict(ul[0]) && pos_strict(ul[S - 1] * ul[0] - 0.5 * m2)))
+      atomicAdd(&w.st->low_not_admissible, 1ull);
+  }
   const double *bi = w.bounds + (int64_t)i * 4;
   const double rmin = bi[0], rmax = bi[1], phimin = bi[2];
   const double phimin2 = phimin * phimin, phimin5 = phimin2 * phimin2 * phimin;

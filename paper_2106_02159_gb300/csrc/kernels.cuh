@@ -56,6 +56,7 @@ struct DevStatus {
   unsigned long long not_admissible;
   unsigned long long line_searches_deferred;  // searches the l = 1 check left open (cumulative)
   unsigned long long line_searches_iterated;  // of those, searches that ran the bracketing iteration
+  unsigned long long low_not_admissible;      // rows whose low-order update U^L left the admissible set
 };
 
 struct MeshView {
