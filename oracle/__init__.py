@@ -73,6 +73,21 @@ class _Problem(ctypes.Structure):
     ]
 
 
+class _Parabolic(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_void_p), ("G", ctypes.c_void_p), ("n_cells", ctypes.c_int), ("nv", ctypes.c_int),
+        ("nq", ctypes.c_int), ("cells", ctypes.c_void_p), ("qw", ctypes.c_void_p), ("qphi", ctypes.c_void_p),
+        ("qgrad", ctypes.c_void_p), ("n_wall", ctypes.c_int), ("wall", ctypes.c_void_p), ("mu", ctypes.c_double),
+        ("lam", ctypes.c_double), ("kappa_cv", ctypes.c_double), ("cg_tol", ctypes.c_double),
+        ("cg_max_iter", ctypes.c_int),
+    ]
+
+
+class _ParabolicInfo(ctypes.Structure):
+    _fields_ = [("cg_iter_velocity", ctypes.c_int), ("cg_iter_energy", ctypes.c_int), ("cg_iter_low", ctypes.c_int),
+                ("limited", ctypes.c_int), ("min_e", ctypes.c_double)]
+
+
 class _Trace(ctypes.Structure):
     _fields_ = [
         ("dij", ctypes.c_void_p), ("alpha", ctypes.c_void_p), ("UL", ctypes.c_void_p),
@@ -113,6 +128,12 @@ def _bind(lib):
     lib.oracle_ssprk3_step_adaptive.restype = ctypes.c_int
     lib.oracle_ssprk3_step_adaptive.argtypes = [ctypes.c_void_p, dp, ctypes.c_double, dp, dp,
                                                 ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_parabolic_step.restype = ctypes.c_int
+    lib.oracle_parabolic_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Parabolic), dp, ctypes.c_double,
+                                          ctypes.POINTER(_ParabolicInfo)]
+    lib.oracle_ns_step.restype = ctypes.c_int
+    lib.oracle_ns_step.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Parabolic), dp, ctypes.c_double, dp,
+                                   ctypes.POINTER(_ParabolicInfo)]
     lib.oracle_run.restype = ctypes.c_int
     lib.oracle_run.argtypes = [ctypes.c_void_p, dp, ctypes.c_int, ctypes.c_double, dp]
     lib.oracle_run_to.restype = ctypes.c_int
@@ -324,6 +345,44 @@ class Oracle:
         if st:
             raise OracleError(f"oracle_ssprk3_step_adaptive failed with status {st}")
         return U, dt.value, cfl.value, r.value
+
+    def set_viscosity(self, pdata, mu, lam=0.0, kappa_cv=0.0, wall=None, cg_tol=1e-13, cg_max_iter=2000):
+        """The finite-element data of meshes.parabolic_data and the constants of
+        the parabolic sub-step (Sec. 5); wall: no-slip node ids."""
+        keep = dict(L=np.ascontiguousarray(pdata["L"], dtype=np.float64),
+                    G=np.ascontiguousarray(pdata["G"], dtype=np.float64),
+                    cells=np.ascontiguousarray(pdata["cells"], dtype=np.int32),
+                    qw=np.ascontiguousarray(pdata["qw"], dtype=np.float64),
+                    qphi=np.ascontiguousarray(pdata["qphi"], dtype=np.float64),
+                    qgrad=np.ascontiguousarray(pdata["qgrad"], dtype=np.float64),
+                    wall=np.ascontiguousarray(np.zeros(0) if wall is None else wall, dtype=np.int32))
+        nc, nq, nv = keep["qphi"].shape
+        self._par_keep = keep
+        self._par = _Parabolic(L=_ptr(keep["L"]), G=_ptr(keep["G"]), n_cells=nc, nv=nv, nq=nq,
+                               cells=_ptr(keep["cells"]), qw=_ptr(keep["qw"]), qphi=_ptr(keep["qphi"]),
+                               qgrad=_ptr(keep["qgrad"]), n_wall=int(keep["wall"].size), wall=_ptr(keep["wall"]),
+                               mu=float(mu), lam=float(lam), kappa_cv=float(kappa_cv), cg_tol=float(cg_tol),
+                               cg_max_iter=int(cg_max_iter))
+
+    def parabolic_step(self, U, dt):
+        """U <- S_P(dt) U (Sec. 5); returns (U_new, info dict)."""
+        U = np.array(self._state(U), copy=True)
+        info = _ParabolicInfo()
+        st = self.lib.oracle_parabolic_step(self._ctx, ctypes.byref(self._par), _dptr(U), float(dt), ctypes.byref(info))
+        if st:
+            raise OracleError(f"oracle_parabolic_step failed with status {st}")
+        return U, {f: getattr(info, f) for f, _ in _ParabolicInfo._fields_}
+
+    def ns_step(self, U, dt=0.0):
+        """Strang step H(tau) P(2 tau) H(tau); returns (U_new, tau, info dict)."""
+        U = np.array(self._state(U), copy=True)
+        info = _ParabolicInfo()
+        tau = ctypes.c_double(0.0)
+        st = self.lib.oracle_ns_step(self._ctx, ctypes.byref(self._par), _dptr(U), float(dt), ctypes.byref(tau),
+                                     ctypes.byref(info))
+        if st:
+            raise OracleError(f"oracle_ns_step failed with status {st}")
+        return U, tau.value, {f: getattr(info, f) for f, _ in _ParabolicInfo._fields_}
 
     def run(self, U, nsteps, dt=0.0):
         U = np.array(self._state(U), copy=True)

@@ -994,3 +994,290 @@ int oracle_run_to(oracle_ctx *c, double *U, double t_final, int max_steps, doubl
   if (steps_out) *steps_out = steps;
   return ORACLE_OK;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 5: the parabolic sub-step S_P and the Strang-split Navier-Stokes step */
+/* ------------------------------------------------------------------------- */
+
+/* Finite-element data of the viscous and Fourier terms (2D P1/Q1) and the
+ * physical constants. L_ij = int grad phi_i . grad phi_j;
+ * G_ij[k][m] = int d_k phi_i d_m phi_j; quadrature data of the cells for the
+ * viscous energy source K_i. Velocity: no slip (v = 0) at the wall nodes,
+ * homogeneous Neumann elsewhere; internal energy: homogeneous Neumann. */
+typedef struct {
+  const double *L;      /* [nnz] */
+  const double *G;      /* [2][2][nnz] */
+  int n_cells, nv, nq;
+  const int32_t *cells; /* [n_cells][nv] */
+  const double *qw;     /* [n_cells][nq] weights x |det J| */
+  const double *qphi;   /* [n_cells][nq][nv] */
+  const double *qgrad;  /* [n_cells][nq][2][nv] */
+  int n_wall;
+  const int32_t *wall;  /* no-slip nodes */
+  double mu, lambda, kappa_cv; /* shear and bulk viscosity, kappa / c_v */
+  double cg_tol;        /* relative residual of the CG solves */
+  int cg_max_iter;
+} oracle_parabolic;
+
+typedef struct {
+  int cg_iter_velocity, cg_iter_energy, cg_iter_low; /* iterations (low: 0 if not needed) */
+  int limited;          /* 1 if the high-order internal energy had a non-positive value */
+  double min_e;         /* min_i e_i^{n+1} */
+} oracle_parabolic_info;
+
+/* The operator y = D x + c A x of the velocity system: D = diag(rho_i m_i),
+ * A_ij[k][m] = mu delta_km L_ij + mu G_ij[m][k] + (lambda - 2 mu/3) G_ij[k][m]
+ * (eq. mt_parabolic_discrete: a(phi_j e_m, phi_i e_k) with
+ * sigma(v) = 2 mu eps(v) + (lambda - 2 mu/3) div v I). Wall rows are the
+ * identity and wall columns drop out (zero Dirichlet values). x, y: [n][2]. */
+static void velocity_apply(const oracle_ctx *c, const oracle_parabolic *pp, const double *D, const unsigned char *wall,
+                           double coef, const double *x, double *y) {
+  const oracle_problem *p = &c->p;
+  const int n = p->n;
+  const int64_t nnz = p->nnz;
+  const double lm = pp->lambda - 2.0 * pp->mu / 3.0;
+  for (int i = 0; i < n; ++i) {
+    if (wall[i]) {
+      y[2 * i] = x[2 * i];
+      y[2 * i + 1] = x[2 * i + 1];
+      continue;
+    }
+    double acc[2] = {0.0, 0.0};
+    for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) {
+      const int j = p->col[k];
+      if (wall[j]) continue;
+      for (int a = 0; a < 2; ++a)
+        for (int m = 0; m < 2; ++m) {
+          double Aam = (a == m ? pp->mu * pp->L[k] : 0.0) + pp->mu * pp->G[(m * 2 + a) * nnz + k] +
+                       lm * pp->G[(a * 2 + m) * nnz + k];
+          acc[a] += Aam * x[2 * j + m];
+        }
+    }
+    for (int a = 0; a < 2; ++a) y[2 * i + a] = D[i] * x[2 * i + a] + coef * acc[a];
+  }
+}
+
+/* y = D x + coef L x (scalar, energy systems). */
+static void energy_apply(const oracle_ctx *c, const oracle_parabolic *pp, const double *D, double coef, const double *x,
+                         double *y) {
+  const oracle_problem *p = &c->p;
+  for (int i = 0; i < p->n; ++i) {
+    double acc = 0.0;
+    for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) acc += pp->L[k] * x[p->col[k]];
+    y[i] = D[i] * x[i] + coef * acc;
+  }
+}
+
+static double dotv(const double *a, const double *b, int64_t m) {
+  double s = 0.0;
+  for (int64_t q = 0; q < m; ++q) s += a[q] * b[q];
+  return s;
+}
+
+/* Preconditioned conjugate gradients (diagonal preconditioner Pd) for the
+ * symmetric positive definite system of size m applied by apply(x, y);
+ * x holds the initial guess and receives the solution; stops when
+ * ||r|| <= tol ||b||. Returns the iteration count, or -1 without convergence. */
+static int pcg(const oracle_ctx *c, const oracle_parabolic *pp, const double *D, const unsigned char *wall, double coef,
+               int scalar, const double *Pd, const double *b, double *x, int64_t m) {
+  double *r = (double *)malloc(sizeof(double) * m), *z = (double *)malloc(sizeof(double) * m);
+  double *d = (double *)malloc(sizeof(double) * m), *q = (double *)malloc(sizeof(double) * m);
+  int it = -1;
+  if (!r || !z || !d || !q) goto out;
+  if (scalar) energy_apply(c, pp, D, coef, x, q); else velocity_apply(c, pp, D, wall, coef, x, q);
+  for (int64_t s = 0; s < m; ++s) r[s] = b[s] - q[s];
+  const double bn = sqrt(dotv(b, b, m));
+  if (sqrt(dotv(r, r, m)) <= pp->cg_tol * bn) { it = 0; goto out; }
+  for (int64_t s = 0; s < m; ++s) { z[s] = r[s] / Pd[s]; d[s] = z[s]; }
+  double rz = dotv(r, z, m);
+  for (int k = 1; k <= pp->cg_max_iter; ++k) {
+    if (scalar) energy_apply(c, pp, D, coef, d, q); else velocity_apply(c, pp, D, wall, coef, d, q);
+    const double alpha = rz / dotv(d, q, m);
+    for (int64_t s = 0; s < m; ++s) { x[s] += alpha * d[s]; r[s] -= alpha * q[s]; }
+    if (sqrt(dotv(r, r, m)) <= pp->cg_tol * bn) { it = k; goto out; }
+    for (int64_t s = 0; s < m; ++s) z[s] = r[s] / Pd[s];
+    const double rz_new = dotv(r, z, m);
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    for (int64_t s = 0; s < m; ++s) d[s] = z[s] + beta * d[s];
+  }
+out:
+  free(r); free(z); free(d); free(q);
+  return it;
+}
+
+/* eq. def_Ki_nplusone: K_i = (1/m_i) int sigma(v):eps(v) phi_i, with the
+ * cells' quadrature. v: [n][2]. */
+static void viscous_source(const oracle_ctx *c, const oracle_parabolic *pp, const double *v, double *K) {
+  const oracle_problem *p = &c->p;
+  const double lm = pp->lambda - 2.0 * pp->mu / 3.0;
+  for (int i = 0; i < p->n; ++i) K[i] = 0.0;
+  for (int e = 0; e < pp->n_cells; ++e) {
+    const int32_t *cn = pp->cells + (int64_t)e * pp->nv;
+    for (int q = 0; q < pp->nq; ++q) {
+      const double *gr = pp->qgrad + ((int64_t)e * pp->nq + q) * 2 * pp->nv;
+      double Dv[2][2] = {{0.0, 0.0}, {0.0, 0.0}}; /* Dv[k][m] = d_m v_k */
+      for (int a = 0; a < pp->nv; ++a)
+        for (int k = 0; k < 2; ++k)
+          for (int m = 0; m < 2; ++m) Dv[k][m] += v[2 * cn[a] + k] * gr[m * pp->nv + a];
+      double ee = 0.0;
+      for (int k = 0; k < 2; ++k)
+        for (int m = 0; m < 2; ++m) {
+          double eps = 0.5 * (Dv[k][m] + Dv[m][k]);
+          ee += eps * eps;
+        }
+      const double div = Dv[0][0] + Dv[1][1];
+      const double se = 2.0 * pp->mu * ee + lm * div * div; /* sigma(v):eps(v) */
+      const double w = pp->qw[(int64_t)e * pp->nq + q];
+      for (int a = 0; a < pp->nv; ++a) K[cn[a]] += w * pp->qphi[((int64_t)e * pp->nq + q) * pp->nv + a] * se;
+    }
+  }
+  for (int i = 0; i < p->n; ++i) K[i] /= p->mi[i];
+}
+
+/* One parabolic sub-step over dt (2 tau in the Strang splitting), U in place:
+ * rho unchanged; velocity by Crank-Nicolson (eqs. mt_parabolic_discrete,
+ * vel_parabolic_discrete); internal energy by Crank-Nicolson with the viscous
+ * source K (eqs. def_Ki_nplusone, high_int_energy_CN); if some e_i^{n+1} <= 0,
+ * the low-order backward-Euler update (eq. low_order_update_internal_energy)
+ * and FCT limiting of A_ij (eq. Aij_for_internal_energy); total energy by
+ * eq. energy_parabolic_discrete. */
+int oracle_parabolic_step(oracle_ctx *c, const oracle_parabolic *pp, double *U, double dt,
+                          oracle_parabolic_info *info) {
+  const oracle_problem *p = &c->p;
+  if (p->dim != 2 || !pp || !(dt > 0.0)) return ORACLE_ERR_ARG;
+  const int n = p->n;
+  const int64_t nnz = p->nnz;
+  int st = ORACLE_OK;
+  double *D = malloc(sizeof(double) * n), *V = malloc(sizeof(double) * 2 * n), *Vh = malloc(sizeof(double) * 2 * n);
+  double *bv = malloc(sizeof(double) * 2 * n), *Pd = malloc(sizeof(double) * 2 * n);
+  double *en = malloc(sizeof(double) * n), *eh = malloc(sizeof(double) * n), *eH = malloc(sizeof(double) * n);
+  double *eL = malloc(sizeof(double) * n), *K = malloc(sizeof(double) * n), *be = malloc(sizeof(double) * n);
+  double *Pe = malloc(sizeof(double) * n);
+  unsigned char *wall = calloc(n, 1);
+  if (!D || !V || !Vh || !bv || !Pd || !en || !eh || !eH || !eL || !K || !be || !Pe || !wall) {
+    st = ORACLE_ERR_OOM;
+    goto done;
+  }
+  for (int w = 0; w < pp->n_wall; ++w) wall[pp->wall[w]] = 1;
+  if (info) memset(info, 0, sizeof(*info));
+  const double lm = pp->lambda - 2.0 * pp->mu / 3.0;
+  for (int i = 0; i < n; ++i) {
+    const double rho = U[i];
+    D[i] = rho * p->mi[i];
+    V[2 * i] = U[n + i] / rho;
+    V[2 * i + 1] = U[2 * n + i] / rho;
+    en[i] = U[3 * n + i] / rho - 0.5 * (V[2 * i] * V[2 * i] + V[2 * i + 1] * V[2 * i + 1]);
+  }
+  /* velocity: (D + dt/2 A) V^{n+1/2} = D V^n (m_i M_i = rho_i m_i V_i), wall rows 0 */
+  for (int i = 0; i < n; ++i) {
+    int64_t kd = -1;
+    for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k)
+      if (p->col[k] == i) kd = k;
+    for (int a = 0; a < 2; ++a) {
+      bv[2 * i + a] = wall[i] ? 0.0 : D[i] * V[2 * i + a];
+      Vh[2 * i + a] = wall[i] ? 0.0 : V[2 * i + a];
+      Pd[2 * i + a] = wall[i] ? 1.0
+                              : D[i] + 0.5 * dt * (pp->mu * pp->L[kd] + pp->mu * pp->G[(a * 2 + a) * nnz + kd] +
+                                                   lm * pp->G[(a * 2 + a) * nnz + kd]);
+    }
+  }
+  int it = pcg(c, pp, D, wall, 0.5 * dt, 0, Pd, bv, Vh, 2 * (int64_t)n);
+  if (it < 0) { st = ORACLE_ERR_ARG; goto done; }
+  if (info) info->cg_iter_velocity = it;
+  /* internal energy: (D + dt/2 b) e^{n+1/2} = D e^n + dt/2 m K */
+  viscous_source(c, pp, Vh, K);
+  for (int i = 0; i < n; ++i) {
+    int64_t kd = -1;
+    for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k)
+      if (p->col[k] == i) kd = k;
+    be[i] = D[i] * en[i] + 0.5 * dt * p->mi[i] * K[i];
+    eh[i] = en[i];
+    Pe[i] = D[i] + 0.5 * dt * pp->kappa_cv * pp->L[kd];
+  }
+  it = pcg(c, pp, D, wall, 0.5 * dt * pp->kappa_cv, 1, Pe, be, eh, n);
+  if (it < 0) { st = ORACLE_ERR_ARG; goto done; }
+  if (info) info->cg_iter_energy = it;
+  int negative = 0;
+  for (int i = 0; i < n; ++i) {
+    eH[i] = 2.0 * eh[i] - en[i];
+    if (!(eH[i] > 0.0)) negative = 1;
+  }
+  if (negative) {
+    /* low order: (D + dt b) e^L = D e^n + dt m K (the source over the whole
+     * step; with it m_i rho_i (e^H_i - e^L_i) = sum_j A_ij holds) */
+    for (int i = 0; i < n; ++i) {
+      int64_t kd = -1;
+      for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k)
+        if (p->col[k] == i) kd = k;
+      be[i] = D[i] * en[i] + dt * p->mi[i] * K[i];
+      eL[i] = en[i];
+      Pe[i] = D[i] + dt * pp->kappa_cv * pp->L[kd];
+    }
+    it = pcg(c, pp, D, wall, dt * pp->kappa_cv, 1, Pe, be, eL, n);
+    if (it < 0) { st = ORACLE_ERR_ARG; goto done; }
+    if (info) { info->cg_iter_low = it; info->limited = 1; }
+    /* FCT (Zalesak) with the local bounds of the low-order solution */
+    double *Rp = malloc(sizeof(double) * n), *Rm = malloc(sizeof(double) * n);
+    if (!Rp || !Rm) { free(Rp); free(Rm); st = ORACLE_ERR_OOM; goto done; }
+    for (int i = 0; i < n; ++i) {
+      double emin = eL[i], emax = eL[i], pp_ = 0.0, pm = 0.0;
+      const double xi = eH[i] + en[i] - 2.0 * eL[i];
+      for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) {
+        const int j = p->col[k];
+        if (j == i) continue;
+        emin = fmin(emin, eL[j]);
+        emax = fmax(emax, eL[j]);
+        const double A = -0.5 * dt * pp->kappa_cv * pp->L[k] * ((eH[j] + en[j] - 2.0 * eL[j]) - xi);
+        if (A > 0.0) pp_ += A; else pm += A;
+      }
+      const double qp = D[i] * (emax - eL[i]), qm = D[i] * (emin - eL[i]);
+      Rp[i] = pp_ > 0.0 ? fmin(1.0, qp / pp_) : 1.0;
+      Rm[i] = pm < 0.0 ? fmin(1.0, qm / pm) : 1.0;
+    }
+    for (int i = 0; i < n; ++i) {
+      double acc = 0.0;
+      const double xi = eH[i] + en[i] - 2.0 * eL[i];
+      for (int64_t k = p->row_ptr[i]; k < p->row_ptr[i + 1]; ++k) {
+        const int j = p->col[k];
+        if (j == i) continue;
+        const double A = -0.5 * dt * pp->kappa_cv * pp->L[k] * ((eH[j] + en[j] - 2.0 * eL[j]) - xi);
+        const double l = A > 0.0 ? fmin(Rp[i], Rm[j]) : fmin(Rm[i], Rp[j]);
+        acc += l * A;
+      }
+      eh[i] = eL[i] + acc / D[i]; /* limited e^{n+1} (eh reused) */
+    }
+    free(Rp);
+    free(Rm);
+    for (int i = 0; i < n; ++i) eH[i] = eh[i];
+  }
+  double emin = INFINITY;
+  for (int i = 0; i < n; ++i) {
+    const double rho = U[i];
+    const double v0 = 2.0 * Vh[2 * i] - V[2 * i], v1 = 2.0 * Vh[2 * i + 1] - V[2 * i + 1];
+    U[n + i] = rho * v0;
+    U[2 * n + i] = rho * v1;
+    U[3 * n + i] = rho * eH[i] + 0.5 * rho * (v0 * v0 + v1 * v1);
+    emin = fmin(emin, eH[i]);
+  }
+  if (info) info->min_e = emin;
+done:
+  free(D); free(V); free(Vh); free(bv); free(Pd); free(en); free(eh); free(eH); free(eL); free(K); free(be);
+  free(Pe); free(wall);
+  return st;
+}
+
+/* eq. continuous_Strang: U <- H(tau) P(2 tau) H(tau) U, tau the CFL step of
+ * the first hyperbolic step (dt <= 0) or dt. */
+int oracle_ns_step(oracle_ctx *c, const oracle_parabolic *pp, double *U, double dt, double *tau_used,
+                   oracle_parabolic_info *info) {
+  double tau = 0.0;
+  int st = oracle_ssprk3_step(c, U, dt, &tau, NULL);
+  if (st) return st;
+  st = oracle_parabolic_step(c, pp, U, 2.0 * tau, info);
+  if (st) return st;
+  st = oracle_ssprk3_step(c, U, tau, NULL, NULL);
+  if (st) return st;
+  if (tau_used) *tau_used = tau;
+  return ORACLE_OK;
+}

@@ -54,6 +54,10 @@ class Mesh:
     bnd_normal: np.ndarray
     bnd_mass_full: np.ndarray
     bnd_normal_full: np.ndarray
+    # the cells (node ids) and their vertex coordinates, kept for the
+    # parabolic (viscous) operators; None for meshes built by other means
+    cells: np.ndarray | None = None
+    cell_xyz: np.ndarray | None = None
 
     @property
     def n(self) -> int:
@@ -278,16 +282,79 @@ def _finish(name, dim, coords, cells, xyz, local_fn, faces, face_xyz, face_kind,
     else:
         b = _boundary(n, dim, faces, face_xyz, face_kind, cent[face_cell])
     return Mesh(name=name, dim=dim, coords=coords, row_ptr=row_ptr, col=col, cij=cij, mij=mij, mi=mi,
-                bnd_node=b[0], bnd_kind=b[1], bnd_normal=b[2], bnd_mass_full=b[3], bnd_normal_full=b[4])
+                bnd_node=b[0], bnd_kind=b[1], bnd_normal=b[2], bnd_mass_full=b[3], bnd_normal_full=b[4],
+                cells=np.ascontiguousarray(cells, dtype=np.int32), cell_xyz=np.ascontiguousarray(xyz))
+
+
+def parabolic_data(mesh: Mesh) -> dict:
+    """The finite-element data of the parabolic (viscous) sub-step of Sec. 5
+    for a 2D P1 or Q1 mesh, with one quadrature rule for everything (P1: the
+    centroid, exact; Q1: 2 x 2 Gauss):
+      L[nnz]          L_ij = int grad phi_i . grad phi_j (Fourier term b)
+      G[2][2][nnz]    G_ij[k][m] = int d_k phi_i d_m phi_j (viscous term a)
+      qw[nc][nq]      quadrature weights times |det J|
+      qphi[nc][nq][nv], qgrad[nc][nq][2][nv]  shape values and physical gradients
+      cells[nc][nv]   node ids
+    (the viscous energy source K_i of eq. def_Ki_nplusone is evaluated with
+    the same quadrature)."""
+    if mesh.dim != 2 or mesh.cells is None:
+        raise ValueError("parabolic data: 2D P1/Q1 meshes built by this module")
+    cells, xyz = mesh.cells, mesh.cell_xyz
+    nc, nv = cells.shape
+    if nv == 3:
+        x0, x1, x2 = xyz[:, 0], xyz[:, 1], xyz[:, 2]
+        e1, e2 = x1 - x0, x2 - x0
+        det = e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0]
+        g1 = np.stack([e2[:, 1], -e2[:, 0]], axis=-1) / det[:, None]
+        g2 = np.stack([-e1[:, 1], e1[:, 0]], axis=-1) / det[:, None]
+        grads = np.stack([-(g1 + g2), g1, g2], axis=1)  # [nc, 3, 2]
+        qw = (0.5 * det)[:, None]
+        qphi = np.full((nc, 1, 3), 1.0 / 3.0)
+        qgrad = np.ascontiguousarray(grads.transpose(0, 2, 1)[:, None])  # [nc, 1, 2, 3]
+    elif nv == 4:
+        gx, gw = _gauss(2)
+        XI, ETA = np.meshgrid(gx, gx, indexing="ij")
+        W = np.outer(gw, gw).ravel()
+        phi, dphi = _q1_2d_shape(XI.ravel(), ETA.ravel())
+        J = np.einsum("car,qas->cqrs", xyz, dphi)
+        det = J[..., 0, 0] * J[..., 1, 1] - J[..., 0, 1] * J[..., 1, 0]
+        adjT = np.empty_like(J)
+        adjT[..., 0, 0] = J[..., 1, 1]
+        adjT[..., 0, 1] = -J[..., 1, 0]
+        adjT[..., 1, 0] = -J[..., 0, 1]
+        adjT[..., 1, 1] = J[..., 0, 0]
+        g = np.einsum("cqrs,qbs->cqrb", adjT, dphi) / det[..., None, None]  # [nc, q, 2, 4]
+        qw = W[None, :] * det
+        qphi = np.broadcast_to(phi[None], (nc, 4, 4)).copy()
+        qgrad = np.ascontiguousarray(g)
+    else:
+        raise ValueError("parabolic data: P1 or Q1 cells only")
+    Lloc = np.einsum("cq,cqka,cqkb->cab", qw, qgrad, qgrad)
+    Gloc = np.einsum("cq,cqka,cqmb->ckmab", qw, qgrad, qgrad)
+    key = mesh.row_of_entry().astype(np.int64) * mesh.n + mesh.col
+    rows = np.repeat(cells, nv, axis=1).ravel().astype(np.int64)
+    cols = np.tile(cells, (1, nv)).ravel().astype(np.int64)
+    pos = np.searchsorted(key, rows * mesh.n + cols)
+    if np.any(key[pos] != rows * mesh.n + cols):
+        raise ValueError("parabolic data: cell pair missing from the CSR pattern")
+    L = np.bincount(pos, weights=Lloc.reshape(nc, -1).ravel(), minlength=mesh.nnz)
+    G = np.empty((2, 2, mesh.nnz))
+    for k in range(2):
+        for m in range(2):
+            G[k, m] = np.bincount(pos, weights=Gloc[:, k, m].reshape(nc, -1).ravel(), minlength=mesh.nnz)
+    return dict(L=L, G=G, qw=np.ascontiguousarray(qw), qphi=np.ascontiguousarray(qphi), qgrad=qgrad,
+                cells=np.ascontiguousarray(cells, dtype=np.int32))
 
 
 # --------------------------------------------------------------------------
 # structured meshes
 # --------------------------------------------------------------------------
 
-def periodic_p1_square(nv: int = 64, lo: float = -5.0, hi: float = 5.0) -> Mesh:
+def periodic_p1_square(nv: int = 64, lo: float = -5.0, hi: float = 5.0, shear: float = 0.0) -> Mesh:
     """nv x nv-vertex periodic P1 mesh of [lo,hi]^2; every square is split by
-    its lower-left -> upper-right diagonal (7-point stencil)."""
+    its lower-left -> upper-right diagonal (7-point stencil). shear != 0 maps
+    (x, y) to (x + shear y, y): the periodic parallelogram with lattice vectors
+    (hi - lo)(1, 0) and (hi - lo)(shear, 1)."""
     h = (hi - lo) / nv
     a, b = np.meshgrid(np.arange(nv), np.arange(nv), indexing="ij")
     a, b = a.ravel(), b.ravel()
@@ -304,7 +371,12 @@ def periodic_p1_square(nv: int = 64, lo: float = -5.0, hi: float = 5.0) -> Mesh:
     p01 = np.stack([x0, y0 + h], -1)
     cells = np.concatenate([t1, t2])
     xyz = np.concatenate([np.stack([p00, p10, p11], 1), np.stack([p00, p11, p01], 1)])
-    return _finish(f"p1-periodic-{nv}x{nv}", 2, coords, cells, xyz, _local_p1, None, None, None, None)
+    if shear:
+        coords[:, 0] += shear * coords[:, 1]
+        xyz = xyz.copy()
+        xyz[..., 0] += shear * xyz[..., 1]
+    name = f"p1-periodic-{nv}x{nv}" + (f"-shear{shear:g}" if shear else "")
+    return _finish(name, 2, coords, cells, xyz, _local_p1, None, None, None, None)
 
 
 def structured_q1(nx: int, ny: int, x0=0.0, x1=1.0, y0=0.0, y1=1.0, periodic_x=False, periodic_y=False,

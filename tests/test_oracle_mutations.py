@@ -220,6 +220,67 @@ def pin_adaptive_cfl_accepts_admissible_low_order(lib):
     return True
 
 
+@_safe
+def pin_parabolic_plane_wave(lib):
+    import math as _m
+    from .test_oracle_parabolic import SHEAR, _box, _plane_wave, _state
+    mu, lam, T = 0.01, 0.02, 0.2
+    k = (1.0, 1.0 - SHEAR)
+    errs = []
+    for n in (16, 32):
+        mesh = _box(n, "p1sheared")
+        v0 = _plane_wave(mesh.coords, 0.0, mu, lam, k)
+        U = _state(mesh, v0[0], v0[1], np.full(mesh.n, 10.0))
+        o = oracle.Oracle(mesh, cfl=0.5, lib=lib)
+        o.set_viscosity(M.parabolic_data(mesh), mu, lam, 0.0)
+        for _ in range(n // 4):
+            U, _ = o.parabolic_step(U, T / (n // 4))
+        ex = _plane_wave(mesh.coords, T, mu, lam, k)
+        errs.append(np.sqrt((mesh.mi * ((U[1:3] / U[0] - ex) ** 2).sum(0)).sum()))
+    return _m.log2(errs[0] / errs[1]) >= 1.8
+
+
+@_safe
+def pin_parabolic_energy_conservation(lib):
+    from .test_oracle_parabolic import _box, _random_smooth
+    mesh = _box(20, "q1")
+    U = _random_smooth(mesh, 1)
+    o = oracle.Oracle(mesh, cfl=0.5, lib=lib)
+    o.set_viscosity(M.parabolic_data(mesh), 0.05, 0.03, 0.04)
+    U1, _ = o.parabolic_step(U, 0.01)
+    E0, E1 = (mesh.mi * U[3]).sum(), (mesh.mi * U1[3]).sum()
+    return abs(E1 - E0) <= 1e-11 * E0
+
+
+@_safe
+def pin_parabolic_energy_conservation_traction_free(lib):
+    from .test_oracle_parabolic import _state
+    mesh = M.structured_q1(14, 10, 0.0, 1.0, 0.0, 0.8)
+    x = mesh.coords
+    U = _state(mesh, np.sin(2.0 * x[:, 0]) * np.cos(1.5 * x[:, 1]), np.cos(2.5 * x[:, 0] * x[:, 1]),
+               3.0 + x[:, 0] * x[:, 1], 1.0 + 0.2 * x[:, 0])
+    o = oracle.Oracle(mesh, cfl=0.5, lib=lib)
+    o.set_viscosity(M.parabolic_data(mesh), 0.05, 0.03, 0.04)
+    U1, _ = o.parabolic_step(U, 0.02)
+    E0, E1 = (mesh.mi * U[3]).sum(), (mesh.mi * U1[3]).sum()
+    return abs(E1 - E0) <= 1e-11 * E0
+
+
+@_safe
+def pin_parabolic_fct(lib):
+    from .test_oracle_parabolic import _box, _state
+    mesh = _box(32, "q1")
+    x = mesh.coords
+    e = np.where(np.abs(x[:, 0] - 0.5) < 0.1, 50.0, 1e-3)
+    U = _state(mesh, np.zeros(mesh.n), np.zeros(mesh.n), e)
+    o = oracle.Oracle(mesh, cfl=0.5, lib=lib)
+    o.set_viscosity(M.parabolic_data(mesh), 0.0, 0.0, 5.0)
+    U1, info = o.parabolic_step(U, 0.05)
+    e1 = U1[3] / U1[0]
+    return bool(info["limited"] == 1 and e1.min() >= e.min() * (1 - 1e-12)
+                and abs((mesh.mi * U1[3]).sum() - (mesh.mi * U[3]).sum()) <= 1e-11 * (mesh.mi * U[3]).sum())
+
+
 MUTATIONS = {
     "bar_state_sign": ("ubar[s] = dL > 0.0 ? 0.5 * (ui[s] + uj[s]) - dfc[s] / (2.0 * dL) : ui[s];",
                        "ubar[s] = dL > 0.0 ? 0.5 * (ui[s] + uj[s]) + dfc[s] / (2.0 * dL) : ui[s];",
@@ -250,6 +311,21 @@ MUTATIONS = {
                               "out->rho = l->rho * (p / l->p - g6) / (g6 * p / l->p + 1.0);", pin_godunov_exact),
     "adaptive_cfl_ignores_low_order_states": ("(st == ORACLE_OK && (c->low_not_admissible > 0 ||",
                                               "(st == ORACLE_OK && (0 ||", pin_adaptive_cfl_accepts_admissible_low_order),
+    "parabolic_bulk_coefficient": ("const double lm = pp->lambda - 2.0 * pp->mu / 3.0;\n  for (int i = 0; i < n; ++i) {\n    if (wall[i])",
+                                   "const double lm = pp->lambda + 2.0 * pp->mu / 3.0;\n  for (int i = 0; i < n; ++i) {\n    if (wall[i])",
+                                   pin_parabolic_plane_wave),
+    # in the continuum both orders give grad div v (so the waves converge either way); the
+    # discrete dissipation then differs from int sigma:eps, and total energy drifts
+    "parabolic_stress_transpose": ("pp->mu * pp->G[(m * 2 + a) * nnz + k]", "pp->mu * pp->G[(a * 2 + m) * nnz + k]",
+                                   pin_parabolic_energy_conservation_traction_free),
+    "parabolic_crank_nicolson_extrapolation": ("eH[i] = 2.0 * eh[i] - en[i];", "eH[i] = eh[i];",
+                                               pin_parabolic_energy_conservation),
+    "parabolic_viscous_heating_factor": ("const double se = 2.0 * pp->mu * ee + lm * div * div;",
+                                         "const double se = pp->mu * ee + lm * div * div;",
+                                         pin_parabolic_energy_conservation),
+    "parabolic_fct_limiter_sides": ("const double l = A > 0.0 ? fmin(Rp[i], Rm[j]) : fmin(Rm[i], Rp[j]);",
+                                    "const double l = A > 0.0 ? fmin(Rp[i], Rp[j]) : fmin(Rm[i], Rm[j]);",
+                                    pin_parabolic_fct),
     "godunov_tangential_side": ("  for (int d = 0; d < dim; ++d) out->vt[d] = r->vt[d];\n  if (p > r->p) {",
                                 "  for (int d = 0; d < dim; ++d) out->vt[d] = l->vt[d];\n  if (p > r->p) {",
                                 pin_godunov_exact),
