@@ -159,6 +159,44 @@ eh_status eh_run(eh_ctx *ctx, int32_t nsteps, double dt);
  * (EH_ERR_STATE after eh_set_instances with more than one). */
 eh_status eh_step_adaptive(eh_ctx *ctx, double cfl_max, double *dt_used, double *cfl_used, int32_t *restarts);
 
+/* ---- the parabolic sub-step and the Navier-Stokes step (Sec. 5, 2D only) ----
+ * eh_set_viscosity: the shear and bulk viscosities mu, lambda >= 0 and
+ * kappa / c_v >= 0 (sigma(v) = 2 mu eps(v) + (lambda - 2 mu/3) div v I, heat
+ * flux -kappa/c_v grad e), the finite-element data of the mesh (host arrays,
+ * copied): L[nnz] = int grad phi_i . grad phi_j, G[2][2][nnz] = int d_k phi_i
+ * d_m phi_j, and the cells with their quadrature (n_cells cells of nv = 3 or 4
+ * nodes, nq points: cells[n_cells][nv], qw[n_cells][nq] weights x |det J|,
+ * qphi[n_cells][nq][nv], qgrad[n_cells][nq][2][nv]); the no-slip nodes
+ * wall[n_wall] (velocity 0; homogeneous Neumann elsewhere and for e); the
+ * relative residual cg_tol and the iteration limit of the CG solves.
+ * EH_ERR_INVALID_ARG / EH_ERR_BAD_MESH on bad input, EH_ERR_STATE without a
+ * mesh. */
+eh_status eh_set_viscosity(eh_ctx *ctx, double mu, double lambda, double kappa_cv, const double *L, const double *G,
+                           int32_t n_cells, int32_t nv, int32_t nq, const int32_t *cells, const double *qw,
+                           const double *qphi, const double *qgrad, int32_t n_wall, const int32_t *wall, double cg_tol,
+                           int32_t cg_max_iter);
+
+typedef struct {
+  int32_t cg_iter_velocity, cg_iter_energy, cg_iter_low; /* CG iterations (low: 0 unless limited) */
+  int32_t limited;  /* 1 if Crank-Nicolson gave a non-positive internal energy and FCT was applied */
+  double min_e;     /* min_i e_i^{n+1} */
+} eh_parabolic_info;
+
+/* One parabolic sub-step S_P over dt on the current state (synchronises):
+ * rho unchanged; velocity by Crank-Nicolson (eqs. mt_parabolic_discrete,
+ * vel_parabolic_discrete); internal energy by Crank-Nicolson with the viscous
+ * source (eqs. def_Ki_nplusone, high_int_energy_CN) and, if that gives a
+ * non-positive value, the low-order update and FCT limiting (eqs.
+ * low_order_update_internal_energy, Aij_for_internal_energy); total energy by
+ * eq. energy_parabolic_discrete. info may be NULL. */
+eh_status eh_parabolic_step(eh_ctx *ctx, double dt, eh_parabolic_info *info);
+
+/* One Strang-split Navier-Stokes step (eq. continuous_Strang): H(tau) P(2 tau)
+ * H(tau) with tau the CFL step of the first hyperbolic step (dt <= 0) or dt;
+ * the second hyperbolic step is held to the invariant-domain limit like a
+ * prescribed dt (EH_ERR_CFL). Synchronises. tau_used and info may be NULL. */
+eh_status eh_step_ns(eh_ctx *ctx, double dt, double *tau_used, eh_parabolic_info *info);
+
 /* Waits for queued work and reports a pending device-side error. */
 eh_status eh_synchronize(eh_ctx *ctx);
 

@@ -18,7 +18,7 @@ _ROOT = os.path.dirname(_HERE)
 CSRC = os.path.join(_HERE, "csrc")
 BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libeuler_hyp.so")
-SOURCES = ("kernels.cu", "capi.cu", "noalloc.cu")
+SOURCES = ("kernels.cu", "capi.cu", "noalloc.cu", "parabolic.cu")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 
@@ -35,7 +35,7 @@ EXPORTS = ("eh_config_default", "eh_create", "eh_upload_mesh", "eh_set_state", "
            "eh_get_diagnostics", "eh_trace", "eh_profile_enable", "eh_profile_read", "eh_launches_per_step",
            "eh_last_error", "eh_status_string", "eh_destroy", "eh_cfl_dt_noalloc", "eh_set_instances",
            "eh_get_instances", "eh_autotune", "eh_get_block_sizes", "eh_get_rows_per_sm", "eh_set_launch_shape",
-           "eh_step_adaptive")
+           "eh_step_adaptive", "eh_set_viscosity", "eh_parabolic_step", "eh_step_ns")
 CFL_NOALLOC_MAX_ROWS = 1 << 23
 KERNEL_NAMES = ("prep", "visc", "low", "tau", "lim1", "pass", "final", "lsearch")
 
@@ -67,6 +67,11 @@ class Diagnostics(ctypes.Structure):
                 ("last_stage_bound", ctypes.c_double * 3), ("cfl_violations", ctypes.c_int64),
                 ("not_admissible", ctypes.c_int64), ("line_searches_deferred", ctypes.c_int64),
                 ("line_searches_iterated", ctypes.c_int64), ("low_order_not_admissible", ctypes.c_int64)]
+
+
+class ParabolicInfo(ctypes.Structure):
+    _fields_ = [("cg_iter_velocity", ctypes.c_int32), ("cg_iter_energy", ctypes.c_int32),
+                ("cg_iter_low", ctypes.c_int32), ("limited", ctypes.c_int32), ("min_e", ctypes.c_double)]
 
 
 _lib = None
@@ -113,6 +118,10 @@ def load(path: str | None = None):
     lib.eh_get_rows_per_sm.argtypes = [vp, vp]
     lib.eh_set_launch_shape.argtypes = [vp, i32, i32, i32]
     lib.eh_step_adaptive.argtypes = [vp, ctypes.c_double, dp, dp, ctypes.POINTER(i32)]
+    lib.eh_set_viscosity.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, i32, i32, i32,
+                                     vp, vp, vp, vp, i32, vp, ctypes.c_double, i32]
+    lib.eh_parabolic_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ParabolicInfo)]
+    lib.eh_step_ns.argtypes = [vp, ctypes.c_double, dp, ctypes.POINTER(ParabolicInfo)]
     lib.eh_cfl_dt_noalloc.argtypes = [i32, ctypes.c_double, ctypes.c_double, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("eh_config_default", "eh_destroy", "eh_launches_per_step", "eh_last_error",
@@ -236,6 +245,35 @@ class Solver:
 
     def run(self, nsteps, dt=0.0):
         self._check(self.lib.eh_run(self.ctx, int(nsteps), float(dt)), "eh_run")
+
+    def set_viscosity(self, pdata, mu, lam=0.0, kappa_cv=0.0, wall=None, cg_tol=1e-13, cg_max_iter=2000):
+        """The finite-element data of meshes.parabolic_data and the constants of
+        the parabolic sub-step (Sec. 5); wall: no-slip node ids."""
+        keep = dict(L=np.ascontiguousarray(pdata["L"], dtype=np.float64),
+                    G=np.ascontiguousarray(pdata["G"], dtype=np.float64),
+                    cells=np.ascontiguousarray(pdata["cells"], dtype=np.int32),
+                    qw=np.ascontiguousarray(pdata["qw"], dtype=np.float64),
+                    qphi=np.ascontiguousarray(pdata["qphi"], dtype=np.float64),
+                    qgrad=np.ascontiguousarray(pdata["qgrad"], dtype=np.float64),
+                    wall=np.ascontiguousarray(np.zeros(0) if wall is None else wall, dtype=np.int32))
+        nc, nq, nv = keep["qphi"].shape
+        self._check(self.lib.eh_set_viscosity(self.ctx, float(mu), float(lam), float(kappa_cv), _p(keep["L"]),
+                                              _p(keep["G"]), nc, nv, nq, _p(keep["cells"]), _p(keep["qw"]),
+                                              _p(keep["qphi"]), _p(keep["qgrad"]), int(keep["wall"].size),
+                                              _p(keep["wall"]), float(cg_tol), int(cg_max_iter)),
+                    "eh_set_viscosity")
+
+    def parabolic_step(self, dt):
+        info = ParabolicInfo()
+        self._check(self.lib.eh_parabolic_step(self.ctx, float(dt), ctypes.byref(info)), "eh_parabolic_step")
+        return {f: getattr(info, f) for f, _ in ParabolicInfo._fields_}
+
+    def step_ns(self, dt=0.0):
+        """One Strang-split Navier-Stokes step; returns (tau, info)."""
+        info = ParabolicInfo()
+        tau = ctypes.c_double(0.0)
+        self._check(self.lib.eh_step_ns(self.ctx, float(dt), ctypes.byref(tau), ctypes.byref(info)), "eh_step_ns")
+        return tau.value, {f: getattr(info, f) for f, _ in ParabolicInfo._fields_}
 
     def step_adaptive(self, cfl_max):
         """One step with the CFL number adapted above 1; returns (dt, cfl, restarts)."""

@@ -13,6 +13,7 @@
 
 #include "../../include/euler_hyp.h"
 #include "kernels.cuh"
+#include "parabolic.cuh"
 
 using namespace eh;
 
@@ -59,6 +60,14 @@ struct eh_ctx {
   int ninst = 1;
   std::vector<void *> inst_allocs;
   double *Usave = nullptr;  // state saved while autotuning
+  // parabolic sub-step (Sec. 5): finite-element data, constants, work arrays
+  bool have_visc = false;
+  ParView pv{};
+  ParWork pw{};
+  double cg_tol = 1e-13;
+  int cg_max_iter = 2000;
+  std::vector<void *> par_allocs;
+  double *host_scal = nullptr;  // pinned, one double
 };
 
 namespace {
@@ -105,7 +114,14 @@ void free_instances(eh_ctx *c) {
   c->inst_allocs.clear();
 }
 
+void free_parabolic(eh_ctx *c) {
+  for (void *p : c->par_allocs) cudaFree(p);
+  c->par_allocs.clear();
+  c->have_visc = false;
+}
+
 void free_mesh(eh_ctx *c) {
+  free_parabolic(c);
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
@@ -434,6 +450,7 @@ void eh_destroy(eh_ctx *c) {
   free_mesh(c);
   if (c->st) cudaFree(c->st);
   if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->host_scal) cudaFreeHost(c->host_scal);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -844,6 +861,254 @@ eh_status eh_step_adaptive(eh_ctx *c, double cfl_max, double *dt_used, double *c
   if (dt_used) *dt_used = c->st_host->tau;
   if (cfl_used) *cfl_used = cfl;
   if (restarts) *restarts = r;
+  return EH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 5: the parabolic sub-step and the Strang-split Navier-Stokes step
+// ---------------------------------------------------------------------------
+eh_status eh_set_viscosity(eh_ctx *c, double mu, double lambda, double kappa_cv, const double *L, const double *G,
+                           int32_t n_cells, int32_t nv, int32_t nq, const int32_t *cells, const double *qw,
+                           const double *qphi, const double *qgrad, int32_t n_wall, const int32_t *wall, double cg_tol,
+                           int32_t cg_max_iter) {
+  if (!c) return EH_ERR_INVALID_ARG;
+  if (!c->have_mesh) return fail(c, EH_ERR_STATE, "no mesh uploaded");
+  if (c->cfg.dim != 2) return fail(c, EH_ERR_INVALID_ARG, "the parabolic step is implemented for 2D meshes");
+  if (!(mu >= 0.0 && lambda >= 0.0 && kappa_cv >= 0.0) || !L || !G || n_cells <= 0 || (nv != 3 && nv != 4) ||
+      nq < 1 || nq > 16 || !cells || !qw || !qphi || !qgrad || n_wall < 0 || (n_wall > 0 && !wall) ||
+      !(cg_tol > 0.0 && cg_tol < 1.0) || cg_max_iter < 1)
+    return fail(c, EH_ERR_INVALID_ARG, "invalid viscosity arguments");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const int n = c->n;
+  const int64_t nnz = c->nnz;
+  for (int64_t q = 0; q < (int64_t)n_cells * nv; ++q)
+    if (cells[q] < 0 || cells[q] >= n) return fail(c, EH_ERR_BAD_MESH, "cell node %d out of range", cells[q]);
+  for (int q = 0; q < n_wall; ++q)
+    if (wall[q] < 0 || wall[q] >= n) return fail(c, EH_ERR_BAD_MESH, "wall node %d out of range", wall[q]);
+  free_parabolic(c);
+  // host tables: diagonal positions, cells around every node, wall mask
+  std::vector<int64_t> rp(n + 1), diag(n, -1);
+  std::vector<int32_t> col(nnz);
+  CUDA_TRY(c, cudaMemcpy(rp.data(), c->mv.row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(col.data(), c->mv.col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (col[k] == i) diag[i] = k;
+  std::vector<int64_t> nc_ptr(n + 1, 0);
+  for (int64_t q = 0; q < (int64_t)n_cells * nv; ++q) nc_ptr[cells[q] + 1]++;
+  for (int i = 0; i < n; ++i) nc_ptr[i + 1] += nc_ptr[i];
+  std::vector<int32_t> nc_cell(nc_ptr[n]), nc_local(nc_ptr[n]);
+  std::vector<int64_t> fill(nc_ptr.begin(), nc_ptr.end() - 1);
+  for (int e = 0; e < n_cells; ++e)
+    for (int a = 0; a < nv; ++a) {
+      const int i = cells[(int64_t)e * nv + a];
+      nc_cell[fill[i]] = e;
+      nc_local[fill[i]++] = a;
+    }
+  std::vector<unsigned char> wm(n, 0);
+  for (int q = 0; q < n_wall; ++q) wm[wall[q]] = 1;
+  auto palloc = [&](void **ptr, size_t bytes) -> eh_status {
+    cudaError_t e = cudaMalloc(ptr, std::max<size_t>(bytes, 8));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_parabolic(c);
+      return fail(c, EH_ERR_OOM, "cudaMalloc of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    c->par_allocs.push_back(*ptr);
+    return EH_OK;
+  };
+  auto upload = [&](void **ptr, const void *src, size_t bytes) -> eh_status {
+    eh_status st = palloc(ptr, bytes);
+    if (st) return st;
+    if (cudaMemcpy(*ptr, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      free_parabolic(c);
+      return fail(c, EH_ERR_CUDA, "parabolic data upload");
+    }
+    return EH_OK;
+  };
+  ParView &v = c->pv;
+  ParWork &w = c->pw;
+  v = ParView{};
+  w = ParWork{};
+  void *p;
+  eh_status st;
+#define UP(field, type, src, count)                                            \
+  if ((st = upload(&p, src, sizeof(type) * (size_t)(count)))) return st; \
+  field = (type *)p;
+  UP(v.diag, const int64_t, diag.data(), n);
+  UP(v.L, const double, L, nnz);
+  UP(v.G, const double, G, 4 * nnz);
+  UP(v.cells, const int32_t, cells, (int64_t)n_cells * nv);
+  UP(v.qw, const double, qw, (int64_t)n_cells * nq);
+  UP(v.qphi, const double, qphi, (int64_t)n_cells * nq * nv);
+  UP(v.qgrad, const double, qgrad, (int64_t)n_cells * nq * 2 * nv);
+  UP(v.nc_ptr, const int64_t, nc_ptr.data(), n + 1);
+  UP(v.nc_cell, const int32_t, nc_cell.data(), nc_ptr[n]);
+  UP(v.nc_local, const int32_t, nc_local.data(), nc_ptr[n]);
+  UP(v.wall, const unsigned char, wm.data(), n);
+#undef UP
+#define WA(field, count)                                                  \
+  if ((st = palloc(&p, sizeof(double) * (size_t)(count)))) return st; \
+  field = (double *)p;
+  WA(w.D, n);
+  WA(w.V, 2 * n);
+  WA(w.Vh, 2 * n);
+  WA(w.x, 2 * n);
+  WA(w.b, 2 * n);
+  WA(w.Pd, 2 * n);
+  WA(w.r, 2 * n);
+  WA(w.z, 2 * n);
+  WA(w.d, 2 * n);
+  WA(w.q, 2 * n);
+  WA(w.en, n);
+  WA(w.eH, n);
+  WA(w.eL, n);
+  WA(w.K, n);
+  WA(w.Rp, n);
+  WA(w.Rm, n);
+  WA(w.part, kRedBlocks);
+  WA(w.scal, 8);
+#undef WA
+  if ((st = palloc(&p, sizeof(int)))) return st;
+  w.flag = (int *)p;
+  if (!c->host_scal && cudaMallocHost(&c->host_scal, sizeof(double) * 2) != cudaSuccess) {
+    cudaGetLastError();
+    free_parabolic(c);
+    return fail(c, EH_ERR_OOM, "pinned scalar");
+  }
+  v.n = n;
+  v.nnz = nnz;
+  v.row_ptr = c->mv.row_ptr;
+  v.col = c->mv.col;
+  v.mi = c->mv.mi;
+  v.n_cells = n_cells;
+  v.nv = nv;
+  v.nq = nq;
+  v.mu = mu;
+  v.lam = lambda;
+  v.kc = kappa_cv;
+  c->cg_tol = cg_tol;
+  c->cg_max_iter = cg_max_iter;
+  c->have_visc = true;
+  return EH_OK;
+}
+
+namespace {
+
+// reads one device scalar (synchronises)
+eh_status read_scal(eh_ctx *c, int slot, double *out) {
+  CUDA_TRY(c, cudaMemcpyAsync(c->host_scal, c->pw.scal + slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *out = c->host_scal[0];
+  return EH_OK;
+}
+
+// Diagonally preconditioned CG on (D + coef A) x = b (velocity, m = 2n) or
+// (D + coef L) x = b (energy, m = n); x holds the initial guess. Stops when
+// ||r|| <= tol ||b||; *iters = the iteration count (-1: no convergence).
+eh_status run_pcg(eh_ctx *c, bool velocity, double coef, int *iters) {
+  const ParView &v = c->pv;
+  const ParWork &w = c->pw;
+  cudaStream_t s = c->stream;
+  const int64_t m = velocity ? 2 * (int64_t)c->n : c->n;
+  auto apply = [&](const double *x, double *y) {
+    if (velocity) par_vel_apply(v, w, coef, x, y, s); else par_en_apply(v, w, coef, x, y, s);
+  };
+  apply(w.x, w.q);
+  par_sub(w.b, w.q, w.r, m, s);
+  par_dot(w, w.b, w.b, m, SC_BN2, s);
+  par_dot(w, w.r, w.r, m, SC_RN2, s);
+  double bn2, rn2;
+  eh_status st;
+  if ((st = read_scal(c, SC_BN2, &bn2))) return st;
+  if ((st = read_scal(c, SC_RN2, &rn2))) return st;
+  const double stop = c->cg_tol * std::sqrt(bn2);
+  *iters = 0;
+  if (std::sqrt(rn2) <= stop) return EH_OK;
+  par_precond(w.r, w.Pd, w.z, w.d, m, s);
+  par_dot(w, w.r, w.z, m, SC_RZ, s);
+  for (int k = 1; k <= c->cg_max_iter; ++k) {
+    apply(w.d, w.q);
+    par_dot(w, w.d, w.q, m, SC_DOT, s);
+    par_ratio(w, SC_RZ, SC_DOT, SC_ALPHA, s);
+    par_xr_update(w, w.x, w.r, w.d, w.q, m, s);
+    par_dot(w, w.r, w.r, m, SC_RN2, s);
+    if ((st = read_scal(c, SC_RN2, &rn2))) return st;
+    if (std::sqrt(rn2) <= stop) {
+      *iters = k;
+      return EH_OK;
+    }
+    par_precond(w.r, w.Pd, w.z, nullptr, m, s);
+    par_dot(w, w.r, w.z, m, SC_TMP, s);
+    par_ratio(w, SC_TMP, SC_RZ, SC_BETA, s);
+    par_copy_scal(w, SC_TMP, SC_RZ, s);
+    par_d_update(w, w.d, w.z, m, s);
+  }
+  *iters = -1;
+  return EH_OK;
+}
+
+}  // namespace
+
+eh_status eh_parabolic_step(eh_ctx *c, double dt, eh_parabolic_info *info) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  if (!c->have_visc) return fail(c, EH_ERR_STATE, "no viscosity data (eh_set_viscosity)");
+  if (!(dt > 0.0)) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if ((st = check_device_error(c))) return st;
+  const ParView &v = c->pv;
+  const ParWork &w = c->pw;
+  cudaStream_t s = c->stream;
+  eh_parabolic_info out{};
+  // velocity (eq. mt_parabolic_discrete): (D + dt/2 A) V^{n+1/2} = D V^n
+  par_init(v, w, c->U, dt, s);
+  int it;
+  if ((st = run_pcg(c, true, 0.5 * dt, &it))) return st;
+  if (it < 0) return fail(c, EH_ERR_NOT_ADMISSIBLE, "velocity CG did not converge");
+  out.cg_iter_velocity = it;
+  CUDA_TRY(c, cudaMemcpyAsync(w.Vh, w.x, sizeof(double) * 2 * c->n, cudaMemcpyDeviceToDevice, s));
+  // internal energy (eqs. def_Ki_nplusone, high_int_energy_CN)
+  par_source(v, w, w.Vh, s);
+  par_en_rhs(v, w, 0.5 * dt, 0.5 * dt * v.kc, s);
+  if ((st = run_pcg(c, false, 0.5 * dt * v.kc, &it))) return st;
+  if (it < 0) return fail(c, EH_ERR_NOT_ADMISSIBLE, "energy CG did not converge");
+  out.cg_iter_energy = it;
+  CUDA_TRY(c, cudaMemsetAsync(w.flag, 0, sizeof(int), s));
+  par_en_extrapolate(v, w, s);
+  int flag = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&flag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(c, cudaStreamSynchronize(s));
+  if (flag) {
+    // low-order update and FCT (eqs. low_order_update_internal_energy, Aij_for_internal_energy)
+    par_en_rhs(v, w, dt, dt * v.kc, s);
+    if ((st = run_pcg(c, false, dt * v.kc, &it))) return st;
+    if (it < 0) return fail(c, EH_ERR_NOT_ADMISSIBLE, "low-order energy CG did not converge");
+    out.cg_iter_low = it;
+    out.limited = 1;
+    CUDA_TRY(c, cudaMemcpyAsync(w.eL, w.x, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+    par_fct(v, w, dt, s);
+  }
+  par_final(v, w, c->U, s);
+  par_min_e(v, w, SC_TMP, s);
+  CUDA_TRY(c, cudaGetLastError());
+  if ((st = read_scal(c, SC_TMP, &out.min_e))) return st;
+  if (info) *info = out;
+  return EH_OK;
+}
+
+eh_status eh_step_ns(eh_ctx *c, double dt, double *tau_used, eh_parabolic_info *info) {
+  if (!c) return EH_ERR_INVALID_ARG;
+  if (!c->have_visc) return fail(c, EH_ERR_STATE, "no viscosity data (eh_set_viscosity)");
+  double tau = 0.0;
+  eh_status st = eh_step(c, dt, &tau);  // H(tau)
+  if (st) return st;
+  if ((st = eh_parabolic_step(c, 2.0 * tau, info))) return st;  // P(2 tau)
+  if ((st = eh_step(c, tau, nullptr))) return st;  // H(tau)
+  if ((st = check_device_error(c))) return st;
+  if (tau_used) *tau_used = tau;
   return EH_OK;
 }
 
