@@ -51,7 +51,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("cylinder", "vortex", "batch", "serve", "cylinder3d", "nrbc", "adaptive"),
+    ap.add_argument("--workload", choices=("cylinder", "vortex", "batch", "serve", "cylinder3d", "nrbc", "adaptive",
+                                           "ns"),
                     default="cylinder")
     ap.add_argument("--requests", type=int, default=48, help="serve workload: requests in the trace")
     ap.add_argument("--instances", type=int, default=256, help="batch workload: number of instances")
@@ -821,6 +822,69 @@ def run_adaptive(args, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_ns(args, dist):
+    """Strang-split Navier-Stokes steps (eq. continuous_Strang, Sec. 5) on the Q1
+    cylinder channel (--vertices), Mach-3 inflow, no-slip cylinder and walls in
+    the parabolic step, mu = 1e-4, lambda = 0, kappa/c_v = 1.4e-4 (Pr ~ 1):
+    vertices x 2 hyperbolic steps x 3 stages per second of NS steps, the
+    parabolic sub-step's share and its CG iteration counts, against the plain
+    Euler path's own steps on the same mesh."""
+    import torch
+    from paper_2106_02159_gb300 import binding, meshes, workloads
+    torch.cuda.set_device(dist.local_rank)
+    binding.build()
+    if dist.rank != 0:
+        return
+    m = meshes.cylinder_m_for_vertices(args.vertices)
+    mesh, U0, bs = workloads.cylinder_problem(m)
+    wall = mesh.bnd_node[mesh.bnd_kind == meshes.BC_SLIP]
+    pdata = meshes.parabolic_data(mesh)
+    stream = torch.cuda.Stream()
+    s = binding.Solver(dim=2, cfl=0.5, stream=stream.cuda_stream)
+    s.upload_mesh(mesh, bs)
+    mu, kc = 1e-4, 1.4e-4
+    s.set_viscosity(pdata, mu, 0.0, kc, wall=wall)
+    U0 = U0.copy()
+    U0[1:3, wall] = 0.0
+    s.set_state(U0)
+    s.apply_boundary_conditions()
+    for _ in range(args.warmup):
+        s.step_ns()
+    s.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters, par_ms = [], 0.0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        tau, info = s.step_ns()
+        iters.append((info["cg_iter_velocity"], info["cg_iter_energy"], info["cg_iter_low"]))
+    ns_wall = time.perf_counter() - t0
+    # the parabolic sub-step alone, and the hyperbolic steps alone, on the same state
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.parabolic_step(2.0 * tau)
+    par_wall = time.perf_counter() - t0
+    e0.record(stream)
+    s.run(2 * args.steps)
+    e1.record(stream)
+    stream.synchronize()
+    euler_ms = e0.elapsed_time(e1) / (2 * args.steps)
+    d = s.diagnostics()
+    line = {"metric": "DOF-updates/s per RK stage (Navier-Stokes steps)", "unit": UNIT, "n_gpus": 1,
+            "value": mesh.n * 2 * 3 * args.steps / ns_wall, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * ns_wall / args.steps, "higher_is_better": True, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": f"Q1 cylinder channel, {mesh.n} vertices, Mach-3 inflow, no-slip cylinder and "
+                                   f"walls in the parabolic step, mu={mu:g}, lambda=0, kappa/c_v={kc:g}, CFL 0.5, "
+                                   "strict bounds; one NS step = H(tau) P(2 tau) H(tau)",
+                       "vertices": mesh.n, "nnz": mesh.nnz},
+            "parabolic_ms_per_step": 1e3 * par_wall / args.steps,
+            "euler_ms_per_ssprk3_step": euler_ms,
+            "cg_iterations_velocity_energy_low": iters[-1],
+            "cg_iterations_mean": [float(np.mean([it[q] for it in iters])) for q in range(3)],
+            "not_admissible": d["not_admissible"],
+            "timing": "host wall clock around synchronising calls (each CG iteration reads its residual)"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     dist = Dist()
@@ -837,6 +901,8 @@ def main():
             run_nrbc(args, dist)
         elif args.workload == "adaptive":
             run_adaptive(args, dist)
+        elif args.workload == "ns":
+            run_ns(args, dist)
         else:
             run_ours(args, dist)
     finally:
