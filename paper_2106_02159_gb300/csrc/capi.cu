@@ -550,6 +550,8 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   ALLOC(d_lam, n);
   ALLOC(d_isb, n);
   ALLOC(d_bidx, n);
+  int32_t *d_bnode = nullptr;
+  ALLOC(d_bnode, n_bnd);
   ALLOC(d_bkind, n_bnd);
   ALLOC(d_bnorm, (size_t)dim * n_bnd);
   ALLOC(d_bstate, (size_t)S * n_bnd);
@@ -638,6 +640,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   if (e == cudaSuccess) e = up(d_lam, lam.data(), sizeof(double) * n);
   if (e == cudaSuccess) e = up(d_isb, isb.data(), n);
   if (e == cudaSuccess) e = up(d_bidx, bidx.data(), sizeof(int32_t) * n);
+  if (e == cudaSuccess) e = up(d_bnode, bnd_node, sizeof(int32_t) * n_bnd);
   if (e == cudaSuccess) e = up(d_bkind, bnd_kind, sizeof(int32_t) * n_bnd);
   if (e == cudaSuccess) e = up(d_bnorm, bnd_normal, sizeof(double) * dim * n_bnd);
   if (e == cudaSuccess && bnd_state) e = up(d_bstate, bnd_state, sizeof(double) * S * n_bnd);
@@ -674,6 +677,10 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   m.vcn = f_cn ? (const void *)f_cn : (const void *)d_cn;
   m.vcinv = f_cinv ? (const void *)f_cinv : (const void *)d_cinv;
   m.bnd_index = d_bidx;
+  m.bnd_node = d_bnode;
+  m.n_nonreflecting = 0;
+  for (int b = 0; b < n_bnd; ++b)
+    if (bnd_kind[b] == EH_BC_CHARACTERISTIC || bnd_kind[b] == EH_BC_GODUNOV) ++m.n_nonreflecting;
   m.bnd_kind = d_bkind;
   m.bnd_normal = d_bnorm;
   m.bnd_state = d_bstate;
@@ -1282,7 +1289,7 @@ int32_t eh_launches_per_step(const eh_ctx *c) {
   // prep, visc, alpha, low, tau, lim1, (passes - 1) x pass, final; three stages
   // per stage: prep, visc, alpha, low, tau, lim1, final, one k_pass per
   // further pass and k_ls_deferred + k_ls_iterate per pass
-  return 3 * (7 + (c->cfg.limiter_passes - 1) + 2 * c->cfg.limiter_passes);
+  return 3 * (7 + (c->cfg.limiter_passes - 1) + 2 * c->cfg.limiter_passes + (c->mv.n_nonreflecting > 0 ? 1 : 0));
 }
 
 eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {

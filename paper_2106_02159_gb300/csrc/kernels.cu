@@ -1219,6 +1219,28 @@ __device__ void bc_godunov(double *u, const double *nv, const double *ud, double
   join_normal<DIM>(rho, un, ut, pr, nv, gamma, u);
 }
 
+// Sec. 4 without the non-reflecting kinds: slip and Dirichlet applied, the
+// return value tells whether the node is a non-reflecting one (its
+// post-processing then runs in k_final_nonreflecting, out of the row kernel,
+// whose register budget it would otherwise set)
+template <int DIM>
+__device__ __forceinline__ bool apply_bc_node_local(const MeshView &m, int i, double *u) {
+  const int b = m.bnd_index[i];
+  if (b < 0) return false;
+  const int kind = m.bnd_kind[b];
+  if (kind == 1) {  // slip: M <- M - (M . n^s) n^s
+    double mn = 0.0;
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) mn += u[1 + q] * m.bnd_normal[(int64_t)q * m.n_bnd + b];
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) u[1 + q] -= mn * m.bnd_normal[(int64_t)q * m.n_bnd + b];
+  } else if (kind == 2) {  // supersonic inflow: U <- U^D
+#pragma unroll
+    for (int s = 0; s < DIM + 2; ++s) u[s] = m.bnd_state[(int64_t)s * m.n_bnd + b];
+  }
+  return kind == 4 || kind == 5;
+}
+
 // Sec. 4: slip (M <- M - (M . n^s) n^s), Dirichlet / supersonic inflow
 // (U <- U^D), do nothing, and the two non-reflecting post-processings
 template <int DIM>
@@ -1281,7 +1303,14 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
   }
   // a finished instance (tau = 0) keeps its state bit for bit: the stage is
   // the identity there, and re-applying the post-processing would not be
-  if (w.tau_inst[m.inst ? m.inst[i] : 0] != 0.0) apply_bc_node<DIM>(m, p, i, u);
+  if (w.tau_inst[m.inst ? m.inst[i] : 0] != 0.0 && apply_bc_node_local<DIM>(m, i, u)) {
+    // non-reflecting node: hand the state to k_final_nonreflecting (the
+    // low-order increment rows are free at this point of the stage)
+    double *h = w.inc + (int64_t)i * SP;
+#pragma unroll
+    for (int s = 0; s < S; ++s) h[s] = u[s];
+    return;
+  }
   if (coef >= 0.0) {
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -1305,6 +1334,46 @@ __global__ void __launch_bounds__(TPB_MAX) k_final(MeshView m, Params p, Work w,
     if (w.st->err) return;
     final_row<DIM>(m, p, w, Uin, lin, U0, coef, out, Upre_trace, i);
   }
+}
+
+// the non-reflecting boundary nodes of a stage: post-processing (Sec. 4.2),
+// SSP combination and admissibility, as k_final does for the other nodes
+template <int DIM>
+__global__ void __launch_bounds__(256) k_final_nonreflecting(MeshView m, Params p, Work w, const double *U0,
+                                                             double coef, double *out) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= m.n_bnd || w.st->err) return;
+  const int kind = m.bnd_kind[b];
+  if (kind != 4 && kind != 5) return;
+  const int i = m.bnd_node[b];
+  if (w.tau_inst[m.inst ? m.inst[i] : 0] == 0.0) return;  // frozen instance: k_final wrote it
+  double u[S], nv[DIM], ud[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    u[s] = w.inc[(int64_t)i * SP + s];
+    ud[s] = m.bnd_state[(int64_t)s * m.n_bnd + b];
+  }
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) nv[q] = m.bnd_normal[(int64_t)q * m.n_bnd + b];
+  if (kind == 4)
+    bc_characteristic<DIM>(u, nv, ud, p.gamma);
+  else
+    bc_godunov<DIM>(u, nv, ud, p.gamma);
+  if (coef >= 0.0) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const double u0 = U0[(int64_t)s * m.n + i];
+      u[s] = u0 + coef * (u[s] - u0);
+    }
+  }
+  if (!admissible<DIM>(u)) {
+    atomicAdd(&w.st->not_admissible, 1ull);
+    atomicExch(&w.st->err, 4);  // EH_ERR_NOT_ADMISSIBLE
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) out[(int64_t)s * m.n + i] = u[s];
 }
 
 template <int DIM> __global__ void k_apply_bc(MeshView m, Params p, double *U) {
@@ -1378,6 +1447,8 @@ void launch_final(const MeshView &m, const Params &p, const Work &w, const doubl
                   const double *U0, double coef, double *out, double *Upre_trace, int tpb, int max_blocks,
                   cudaStream_t s) {
   k_final<DIM><<<capped_grid(m.n, tpb, max_blocks), tpb, 0, s>>>(m, p, w, Uin, lin, U0, coef, out, Upre_trace);
+  if (m.n_nonreflecting > 0)
+    k_final_nonreflecting<DIM><<<nblocks(m.n_bnd, 256), 256, 0, s>>>(m, p, w, U0, coef, out);
 }
 template <int DIM> void launch_apply_bc(const MeshView &m, const Params &p, double *U, cudaStream_t s) {
   k_apply_bc<DIM><<<nblocks(m.n, 256), 256, 0, s>>>(m, p, U);

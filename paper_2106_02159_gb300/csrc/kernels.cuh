@@ -81,6 +81,8 @@ struct MeshView {
   const void *vcn;
   const void *vcinv;
   const int32_t *bnd_index;  // per node: index into the boundary arrays, -1 inside
+  const int32_t *bnd_node;   // [n_bnd] node of every boundary entry
+  int n_nonreflecting;       // boundary nodes of the two non-reflecting kinds
   const int32_t *bnd_kind;   // [n_bnd]
   const double *bnd_normal;  // [dim][n_bnd]
   const double *bnd_state;   // [S][n_bnd]
