@@ -881,7 +881,8 @@ def run_ns(args, dist):
             "cg_iterations_velocity_energy_low": iters[-1],
             "cg_iterations_mean": [float(np.mean([it[q] for it in iters])) for q in range(3)],
             "not_admissible": d["not_admissible"],
-            "timing": "host wall clock around synchronising calls (each CG iteration reads its residual)"}
+            "timing": "host wall clock around synchronising calls (the CG loops read their control pair once per "
+                      "batch of queued iterations)"}
     print(json.dumps(line), flush=True)
 
 

@@ -67,7 +67,9 @@ struct eh_ctx {
   double cg_tol = 1e-13;
   int cg_max_iter = 2000;
   std::vector<void *> par_allocs;
-  double *host_scal = nullptr;  // pinned, one double
+  double *host_scal = nullptr;  // pinned, two doubles
+  int *host_ctl = nullptr;      // pinned, the CG control pair
+  int cg_last[3] = {8, 8, 8};   // iterations of the last velocity, energy and low-order solves
 };
 
 namespace {
@@ -429,6 +431,7 @@ eh_status eh_create(const eh_config *cfg, eh_ctx **out) {
     c->rows_per_sm[EH_KERNEL_FINAL] = 768;
   } else {
     c->rows_per_sm[EH_KERNEL_PASS] = 768;
+    c->rows_per_sm[EH_KERNEL_FINAL] = 1024;
   }
   Params &p = c->prm;
   p.gamma = cfg->gamma;
@@ -451,6 +454,7 @@ void eh_destroy(eh_ctx *c) {
   if (c->st) cudaFree(c->st);
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->host_scal) cudaFreeHost(c->host_scal);
+  if (c->host_ctl) cudaFreeHost(c->host_ctl);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -946,7 +950,6 @@ eh_status eh_set_viscosity(eh_ctx *c, double mu, double lambda, double kappa_cv,
   field = (type *)p;
   UP(v.diag, const int64_t, diag.data(), n);
   UP(v.L, const double, L, nnz);
-  UP(v.G, const double, G, 4 * nnz);
   UP(v.cells, const int32_t, cells, (int64_t)n_cells * nv);
   UP(v.qw, const double, qw, (int64_t)n_cells * nq);
   UP(v.qphi, const double, qphi, (int64_t)n_cells * nq * nv);
@@ -956,35 +959,6 @@ eh_status eh_set_viscosity(eh_ctx *c, double mu, double lambda, double kappa_cv,
   UP(v.nc_local, const int32_t, nc_local.data(), nc_ptr[n]);
   UP(v.wall, const unsigned char, wm.data(), n);
 #undef UP
-#define WA(field, count)                                                  \
-  if ((st = palloc(&p, sizeof(double) * (size_t)(count)))) return st; \
-  field = (double *)p;
-  WA(w.D, n);
-  WA(w.V, 2 * n);
-  WA(w.Vh, 2 * n);
-  WA(w.x, 2 * n);
-  WA(w.b, 2 * n);
-  WA(w.Pd, 2 * n);
-  WA(w.r, 2 * n);
-  WA(w.z, 2 * n);
-  WA(w.d, 2 * n);
-  WA(w.q, 2 * n);
-  WA(w.en, n);
-  WA(w.eH, n);
-  WA(w.eL, n);
-  WA(w.K, n);
-  WA(w.Rp, n);
-  WA(w.Rm, n);
-  WA(w.part, kRedBlocks);
-  WA(w.scal, 8);
-#undef WA
-  if ((st = palloc(&p, sizeof(int)))) return st;
-  w.flag = (int *)p;
-  if (!c->host_scal && cudaMallocHost(&c->host_scal, sizeof(double) * 2) != cudaSuccess) {
-    cudaGetLastError();
-    free_parabolic(c);
-    return fail(c, EH_ERR_OOM, "pinned scalar");
-  }
   v.n = n;
   v.nnz = nnz;
   v.row_ptr = c->mv.row_ptr;
@@ -996,6 +970,65 @@ eh_status eh_set_viscosity(eh_ctx *c, double mu, double lambda, double kappa_cv,
   v.mu = mu;
   v.lam = lambda;
   v.kc = kappa_cv;
+  {
+    // the velocity operator's coefficients, formed once from G (not kept)
+    if ((st = palloc(&p, sizeof(double) * 4 * (size_t)nnz))) return st;
+    v.A = (const double *)p;
+    void *g = nullptr;
+    cudaError_t e = cudaMalloc(&g, sizeof(double) * 4 * (size_t)nnz);
+    if (e == cudaSuccess) e = cudaMemcpy(g, G, sizeof(double) * 4 * (size_t)nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      par_vel_coef(v, (const double *)g, (double *)p, c->stream);
+      e = cudaStreamSynchronize(c->stream);
+    }
+    if (g) cudaFree(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_parabolic(c);
+      return fail(c, e == cudaErrorMemoryAllocation ? EH_ERR_OOM : EH_ERR_CUDA, "velocity coefficients: %s",
+                  cudaGetErrorString(e));
+    }
+  }
+#define WA(field, count)                                                  \
+  if ((st = palloc(&p, sizeof(double) * (size_t)(count)))) return st; \
+  field = (double *)p;
+  WA(w.D, n);
+  WA(w.V, 2 * n);
+  WA(w.Vh, 2 * n);
+  WA(w.x, 2 * n);
+  WA(w.b, 2 * n);
+  WA(w.iPd, 2 * n);
+  WA(w.r, 2 * n);
+  WA(w.z, 2 * n);
+  WA(w.d, 2 * n);
+  WA(w.q, 2 * n);
+  WA(w.en, n);
+  WA(w.eH, n);
+  WA(w.eL, n);
+  WA(w.K, n);
+  WA(w.Rp, n);
+  WA(w.Rm, n);
+  WA(w.ce, (int64_t)n_cells * nv);
+  WA(w.part, 3 * kRedBlocks);
+  WA(w.scal, 8);
+#undef WA
+  if ((st = palloc(&p, sizeof(int)))) return st;
+  w.flag = (int *)p;
+  if ((st = palloc(&p, sizeof(int) * 2))) return st;
+  w.ctl = (int *)p;
+  if ((st = palloc(&p, sizeof(unsigned)))) return st;
+  w.count = (unsigned *)p;
+  if (cudaMemset(w.count, 0, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    free_parabolic(c);
+    return fail(c, EH_ERR_CUDA, "reduction counter");
+  }
+  if ((!c->host_scal && cudaMallocHost(&c->host_scal, sizeof(double) * 2) != cudaSuccess) ||
+      (!c->host_ctl && cudaMallocHost(&c->host_ctl, sizeof(int) * 2) != cudaSuccess)) {
+    cudaGetLastError();
+    free_parabolic(c);
+    return fail(c, EH_ERR_OOM, "pinned scalars");
+  }
   c->cg_tol = cg_tol;
   c->cg_max_iter = cg_max_iter;
   c->have_visc = true;
@@ -1015,43 +1048,40 @@ eh_status read_scal(eh_ctx *c, int slot, double *out) {
 // Diagonally preconditioned CG on (D + coef A) x = b (velocity, m = 2n) or
 // (D + coef L) x = b (energy, m = n); x holds the initial guess. Stops when
 // ||r|| <= tol ||b||; *iters = the iteration count (-1: no convergence).
-eh_status run_pcg(eh_ctx *c, bool velocity, double coef, int *iters) {
+// Iterations are queued in batches (the first as long as the last solve of
+// the same system took, then two at a time) and the host reads the device's
+// control pair after each batch; iterations queued past convergence do
+// nothing, so the result does not depend on the batching.
+eh_status run_pcg(eh_ctx *c, bool velocity, double coef, int which, int *iters) {
   const ParView &v = c->pv;
   const ParWork &w = c->pw;
   cudaStream_t s = c->stream;
   const int64_t m = velocity ? 2 * (int64_t)c->n : c->n;
-  auto apply = [&](const double *x, double *y) {
-    if (velocity) par_vel_apply(v, w, coef, x, y, s); else par_en_apply(v, w, coef, x, y, s);
+  const int *skip = w.ctl + CTL_DONE;
+  auto apply = [&](const double *x, double *y, const int *sk) {
+    if (velocity) par_vel_apply(v, w, coef, x, y, sk, s); else par_en_apply(v, w, coef, x, y, sk, s);
   };
-  apply(w.x, w.q);
-  par_sub(w.b, w.q, w.r, m, s);
-  par_dot(w, w.b, w.b, m, SC_BN2, s);
-  par_dot(w, w.r, w.r, m, SC_RN2, s);
-  double bn2, rn2;
-  eh_status st;
-  if ((st = read_scal(c, SC_BN2, &bn2))) return st;
-  if ((st = read_scal(c, SC_RN2, &rn2))) return st;
-  const double stop = c->cg_tol * std::sqrt(bn2);
-  *iters = 0;
-  if (std::sqrt(rn2) <= stop) return EH_OK;
-  par_precond(w.r, w.Pd, w.z, w.d, m, s);
-  par_dot(w, w.r, w.z, m, SC_RZ, s);
-  for (int k = 1; k <= c->cg_max_iter; ++k) {
-    apply(w.d, w.q);
-    par_dot(w, w.d, w.q, m, SC_DOT, s);
-    par_ratio(w, SC_RZ, SC_DOT, SC_ALPHA, s);
-    par_xr_update(w, w.x, w.r, w.d, w.q, m, s);
-    par_dot(w, w.r, w.r, m, SC_RN2, s);
-    if ((st = read_scal(c, SC_RN2, &rn2))) return st;
-    if (std::sqrt(rn2) <= stop) {
-      *iters = k;
+  apply(w.x, w.q, nullptr);
+  par_cg_init(w, m, c->cg_tol, s);
+  int k = 0, batch = std::max(1, c->cg_last[which]);
+  while (k < c->cg_max_iter) {
+    const int nb = std::min(batch, c->cg_max_iter - k);
+    for (int b = 0; b < nb; ++b) {
+      apply(w.d, w.q, skip);
+      par_cg_alpha(w, m, s);
+      par_cg_update(w, m, s);
+      par_cg_dir(w, m, s);
+    }
+    k += nb;
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(c->host_ctl, w.ctl, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    if (c->host_ctl[CTL_DONE]) {
+      *iters = c->host_ctl[CTL_IT];
+      c->cg_last[which] = *iters;
       return EH_OK;
     }
-    par_precond(w.r, w.Pd, w.z, nullptr, m, s);
-    par_dot(w, w.r, w.z, m, SC_TMP, s);
-    par_ratio(w, SC_TMP, SC_RZ, SC_BETA, s);
-    par_copy_scal(w, SC_TMP, SC_RZ, s);
-    par_d_update(w, w.d, w.z, m, s);
+    batch = 2;
   }
   *iters = -1;
   return EH_OK;
@@ -1073,14 +1103,15 @@ eh_status eh_parabolic_step(eh_ctx *c, double dt, eh_parabolic_info *info) {
   // velocity (eq. mt_parabolic_discrete): (D + dt/2 A) V^{n+1/2} = D V^n
   par_init(v, w, c->U, dt, s);
   int it;
-  if ((st = run_pcg(c, true, 0.5 * dt, &it))) return st;
+  if ((st = run_pcg(c, true, 0.5 * dt, 0, &it))) return st;
   if (it < 0) return fail(c, EH_ERR_NOT_ADMISSIBLE, "velocity CG did not converge");
   out.cg_iter_velocity = it;
   CUDA_TRY(c, cudaMemcpyAsync(w.Vh, w.x, sizeof(double) * 2 * c->n, cudaMemcpyDeviceToDevice, s));
   // internal energy (eqs. def_Ki_nplusone, high_int_energy_CN)
-  par_source(v, w, w.Vh, s);
+  par_cell_source(v, w, w.Vh, s);
+  par_source(v, w, s);
   par_en_rhs(v, w, 0.5 * dt, 0.5 * dt * v.kc, s);
-  if ((st = run_pcg(c, false, 0.5 * dt * v.kc, &it))) return st;
+  if ((st = run_pcg(c, false, 0.5 * dt * v.kc, 1, &it))) return st;
   if (it < 0) return fail(c, EH_ERR_NOT_ADMISSIBLE, "energy CG did not converge");
   out.cg_iter_energy = it;
   CUDA_TRY(c, cudaMemsetAsync(w.flag, 0, sizeof(int), s));
@@ -1091,7 +1122,7 @@ eh_status eh_parabolic_step(eh_ctx *c, double dt, eh_parabolic_info *info) {
   if (flag) {
     // low-order update and FCT (eqs. low_order_update_internal_energy, Aij_for_internal_energy)
     par_en_rhs(v, w, dt, dt * v.kc, s);
-    if ((st = run_pcg(c, false, dt * v.kc, &it))) return st;
+    if ((st = run_pcg(c, false, dt * v.kc, 2, &it))) return st;
     if (it < 0) return fail(c, EH_ERR_NOT_ADMISSIBLE, "low-order energy CG did not converge");
     out.cg_iter_low = it;
     out.limited = 1;

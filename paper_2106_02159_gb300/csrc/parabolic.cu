@@ -6,8 +6,8 @@
 // conjugate gradients, the viscous energy source K_i (eq. def_Ki_nplusone),
 // the FCT limiting of the internal energy (eq. Aij_for_internal_energy) and
 // the final update (eqs. vel_parabolic_discrete, energy_parabolic_discrete).
-// The iteration itself is driven by the host (capi.cu). State layout [S][n]
-// with S = 4; velocity vectors [n][2].
+// The CG iterations are queued by the host (capi.cu) in batches; their scalars
+// live on the device. State layout [S][n] with S = 4; velocity vectors [n][2].
 #include "parabolic.cuh"
 
 #include <cmath>
@@ -31,44 +31,63 @@ __global__ void k_par_init(ParView v, ParWork w, const double *__restrict__ U, d
   w.en[i] = U[3 * n + i] / rho - 0.5 * (vx * vx + vy * vy);
   const bool wl = v.wall[i] != 0;
   const int64_t kd = v.diag[i];
-  const double lm = v.lam - 2.0 * v.mu / 3.0;
   const double c = 0.5 * dt;
   const double vv[2] = {vx, vy};
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
     w.b[2 * i + a] = wl ? 0.0 : D * vv[a];
     w.x[2 * i + a] = wl ? 0.0 : vv[a];
-    const double Gaa = v.G[(a * 2 + a) * v.nnz + kd];
-    w.Pd[2 * i + a] = wl ? 1.0 : D + c * (v.mu * v.L[kd] + v.mu * Gaa + lm * Gaa);
+    w.iPd[2 * i + a] = wl ? 1.0 : 1.0 / (D + c * v.A[4 * kd + 3 * a]);
   }
 }
 
-// y = D x + coef A x with A_ij[a][m] = mu delta_am L_ij + mu G_ij[m][a] + (lambda - 2 mu/3) G_ij[a][m];
-// wall rows are the identity, wall columns drop out
-__global__ void k_vel_apply(ParView v, ParWork w, double coef, const double *__restrict__ x, double *__restrict__ y) {
+// A_ij[a][m] = mu delta_am L_ij + mu G_ij[m][a] + (lambda - 2 mu/3) G_ij[a][m]
+// (eq. mt_parabolic_discrete), zero where j is a wall node: the wall values
+// are held at 0 and drop out of every row
+__global__ void k_vel_coef(ParView v, const double *__restrict__ G, double *__restrict__ A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.n) return;
+  const double lm = v.lam - 2.0 * v.mu / 3.0;
+  for (int64_t k = v.row_ptr[i]; k < v.row_ptr[i + 1]; ++k) {
+    double *a = A + 4 * k;
+    if (v.wall[v.col[k]]) {
+      a[0] = a[1] = a[2] = a[3] = 0.0;
+      continue;
+    }
+    const double L = v.L[k], g00 = G[k], g01 = G[v.nnz + k], g10 = G[2 * v.nnz + k], g11 = G[3 * v.nnz + k];
+    a[0] = v.mu * L + v.mu * g00 + lm * g00;
+    a[1] = v.mu * g10 + lm * g01;
+    a[2] = v.mu * g01 + lm * g10;
+    a[3] = v.mu * L + v.mu * g11 + lm * g11;
+  }
+}
+
+// y = D x + coef A x; wall rows are the identity
+__global__ void k_vel_apply(ParView v, ParWork w, double coef, const double *__restrict__ x, double *__restrict__ y,
+                            const int *skip) {
+  if (skip && *skip) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.n) return;
+  const double2 xi = *(const double2 *)(x + 2 * i);
   if (v.wall[i]) {
-    y[2 * i] = x[2 * i];
-    y[2 * i + 1] = x[2 * i + 1];
+    *(double2 *)(y + 2 * i) = xi;
     return;
   }
-  const double lm = v.lam - 2.0 * v.mu / 3.0;
   double a0 = 0.0, a1 = 0.0;
   for (int64_t k = v.row_ptr[i]; k < v.row_ptr[i + 1]; ++k) {
     const int j = v.col[k];
-    if (v.wall[j]) continue;
-    const double L = v.L[k], g00 = v.G[k], g01 = v.G[v.nnz + k], g10 = v.G[2 * v.nnz + k], g11 = v.G[3 * v.nnz + k];
-    const double x0 = x[2 * j], x1 = x[2 * j + 1];
-    a0 += (v.mu * L + v.mu * g00 + lm * g00) * x0 + (v.mu * g10 + lm * g01) * x1;
-    a1 += (v.mu * g01 + lm * g10) * x0 + (v.mu * L + v.mu * g11 + lm * g11) * x1;
+    const double2 r0 = *(const double2 *)(v.A + 4 * k), r1 = *(const double2 *)(v.A + 4 * k + 2);
+    const double2 xj = *(const double2 *)(x + 2 * j);
+    a0 += r0.x * xj.x + r0.y * xj.y;
+    a1 += r1.x * xj.x + r1.y * xj.y;
   }
   const double D = w.D[i];
-  y[2 * i] = D * x[2 * i] + coef * a0;
-  y[2 * i + 1] = D * x[2 * i + 1] + coef * a1;
+  *(double2 *)(y + 2 * i) = make_double2(D * xi.x + coef * a0, D * xi.y + coef * a1);
 }
 
-__global__ void k_en_apply(ParView v, ParWork w, double coef, const double *__restrict__ x, double *__restrict__ y) {
+__global__ void k_en_apply(ParView v, ParWork w, double coef, const double *__restrict__ x, double *__restrict__ y,
+                           const int *skip) {
+  if (skip && *skip) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.n) return;
   double acc = 0.0;
@@ -76,32 +95,114 @@ __global__ void k_en_apply(ParView v, ParWork w, double coef, const double *__re
   y[i] = w.D[i] * x[i] + coef * acc;
 }
 
-// block sums in a fixed tree; one partial per block
-__global__ void k_dot_partial(const double *__restrict__ a, const double *__restrict__ b, int64_t m,
-                              double *__restrict__ part) {
-  __shared__ double sh[kT];
-  double acc = 0.0;
-  for (int64_t q = (int64_t)blockIdx.x * kT + threadIdx.x; q < m; q += (int64_t)gridDim.x * kT) acc += a[q] * b[q];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int h = kT / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-    __syncthreads();
+// ---------------------------------------------------------------------------
+// conjugate-gradient kernels: grid-stride over kRedBlocks blocks of kT
+// threads, block sums by fixed shuffle and shared-memory trees, and the block
+// that finishes last sums the partials in a fixed order and forms the scalars
+// ---------------------------------------------------------------------------
+template <int NV> __device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][kT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    if (lane == 0) sh[q][warp] = v[q];
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      v[q] = lane < kT / 32 ? sh[q][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    }
+  }
+  __syncthreads();
 }
 
-__global__ void k_sum_partials(const double *__restrict__ part, int np, double *out) {
-  __shared__ double sh[1024];
-  double acc = 0.0;
-  for (int q = threadIdx.x; q < np; q += blockDim.x) acc += part[q];
-  sh[threadIdx.x] = acc;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-    __syncthreads();
+// thread 0 of every block passes its sums in v; returns true in the block that
+// finishes last, whose thread 0 then holds the totals in v
+template <int NV> __device__ __forceinline__ bool grid_sum(const ParWork &w, double (&v)[NV]) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) w.part[q * kRedBlocks + blockIdx.x] = v[q];
+    __threadfence();
+    last = atomicAdd(w.count, 1u) == gridDim.x - 1;
   }
-  if (threadIdx.x == 0) *out = sh[0];
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < kRedBlocks; t += kT) acc += __ldcg(w.part + q * kRedBlocks + t);
+    v[q] = acc;
+  }
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) *w.count = 0u;
+  return true;
+}
+
+__global__ void __launch_bounds__(kT, 4) k_cg_init(ParWork w, int64_t m, double tol) {
+  double v[3] = {0.0, 0.0, 0.0};  // b.b, r.r, r.z
+  for (int64_t s = (int64_t)blockIdx.x * kT + threadIdx.x; s < m; s += (int64_t)kRedBlocks * kT) {
+    const double bs = w.b[s], rs = bs - w.q[s], zs = rs * w.iPd[s];
+    w.r[s] = rs;
+    w.z[s] = zs;
+    w.d[s] = zs;
+    v[0] += bs * bs;
+    v[1] += rs * rs;
+    v[2] += rs * zs;
+  }
+  block_sum<3>(v);
+  if (grid_sum<3>(w, v) && threadIdx.x == 0) {
+    const double stop = tol * sqrt(v[0]);
+    w.scal[SC_STOP] = stop;
+    w.scal[SC_RZ] = v[2];
+    w.ctl[CTL_DONE] = sqrt(v[1]) <= stop;
+    w.ctl[CTL_IT] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kT, 4) k_cg_alpha(ParWork w, int64_t m) {
+  if (w.ctl[CTL_DONE]) return;
+  double v[1] = {0.0};  // d.q
+  for (int64_t s = (int64_t)blockIdx.x * kT + threadIdx.x; s < m; s += (int64_t)kRedBlocks * kT) v[0] += w.d[s] * w.q[s];
+  block_sum<1>(v);
+  if (grid_sum<1>(w, v) && threadIdx.x == 0) w.scal[SC_ALPHA] = w.scal[SC_RZ] / v[0];
+}
+
+__global__ void __launch_bounds__(kT, 4) k_cg_update(ParWork w, int64_t m) {
+  if (w.ctl[CTL_DONE]) return;
+  const double alpha = w.scal[SC_ALPHA];
+  double v[2] = {0.0, 0.0};  // r.r, r.z
+  for (int64_t s = (int64_t)blockIdx.x * kT + threadIdx.x; s < m; s += (int64_t)kRedBlocks * kT) {
+    w.x[s] += alpha * w.d[s];
+    const double rs = w.r[s] - alpha * w.q[s], zs = rs * w.iPd[s];
+    w.r[s] = rs;
+    w.z[s] = zs;
+    v[0] += rs * rs;
+    v[1] += rs * zs;
+  }
+  block_sum<2>(v);
+  if (grid_sum<2>(w, v) && threadIdx.x == 0) {
+    w.ctl[CTL_IT] += 1;
+    if (sqrt(v[0]) <= w.scal[SC_STOP]) {
+      w.ctl[CTL_DONE] = 1;
+    } else {
+      w.scal[SC_BETA] = v[1] / w.scal[SC_RZ];
+      w.scal[SC_RZ] = v[1];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kT, 4) k_cg_dir(ParWork w, int64_t m) {
+  if (w.ctl[CTL_DONE]) return;
+  const double beta = w.scal[SC_BETA];
+  for (int64_t s = (int64_t)blockIdx.x * kT + threadIdx.x; s < m; s += (int64_t)kRedBlocks * kT)
+    w.d[s] = w.z[s] + beta * w.d[s];
 }
 
 __global__ void k_min_partial(const double *__restrict__ a, int64_t m, double *__restrict__ part) {
@@ -123,64 +224,50 @@ __global__ void k_min_partials(const double *__restrict__ part, int np, double *
   *out = acc;
 }
 
-__global__ void k_sub(const double *__restrict__ b, const double *__restrict__ q, double *__restrict__ r, int64_t m) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < m) r[s] = b[s] - q[s];
+// every cell's share of int sigma(v):eps(v) phi_a for its nv nodes a, by the
+// cell's quadrature, with sigma = 2 mu eps + (lambda - 2 mu/3) div v I
+// (eq. def_Ki_nplusone)
+template <int NV>
+__global__ void k_cell_source(ParView v, ParWork w, const double *__restrict__ vh) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= v.n_cells) return;
+  const double lm = v.lam - 2.0 * v.mu / 3.0;
+  const int32_t *cn = v.cells + (int64_t)e * NV;
+  double2 u[NV];
+  double ce[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    u[a] = *(const double2 *)(vh + 2 * cn[a]);
+    ce[a] = 0.0;
+  }
+  for (int q = 0; q < v.nq; ++q) {
+    const int64_t eq = (int64_t)e * v.nq + q;
+    const double *gr = v.qgrad + eq * 2 * NV;
+    double d00 = 0.0, d01 = 0.0, d10 = 0.0, d11 = 0.0;  // d_km = d_m v_k
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const double g0 = gr[a], g1 = gr[NV + a];
+      d00 += u[a].x * g0;
+      d01 += u[a].x * g1;
+      d10 += u[a].y * g0;
+      d11 += u[a].y * g1;
+    }
+    const double e01 = 0.5 * (d01 + d10), div = d00 + d11;
+    const double se = 2.0 * v.mu * (d00 * d00 + 2.0 * e01 * e01 + d11 * d11) + lm * div * div;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) ce[a] += v.qw[eq] * v.qphi[eq * NV + a] * se;
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) w.ce[(int64_t)e * NV + a] = ce[a];
 }
 
-__global__ void k_precond(const double *__restrict__ r, const double *__restrict__ Pd, double *__restrict__ z,
-                          double *__restrict__ d, int64_t m) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= m) return;
-  const double zz = r[s] / Pd[s];
-  z[s] = zz;
-  if (d) d[s] = zz;
-}
-
-__global__ void k_ratio(double *scal, int num, int den, int out) { scal[out] = scal[num] / scal[den]; }
-__global__ void k_copy_scal(double *scal, int from, int to) { scal[to] = scal[from]; }
-
-__global__ void k_xr_update(const double *__restrict__ scal, double *__restrict__ x, double *__restrict__ r,
-                            const double *__restrict__ d, const double *__restrict__ q, int64_t m) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= m) return;
-  const double alpha = scal[SC_ALPHA];
-  x[s] += alpha * d[s];
-  r[s] -= alpha * q[s];
-}
-
-__global__ void k_d_update(const double *__restrict__ scal, double *__restrict__ d, const double *__restrict__ z,
-                           int64_t m) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < m) d[s] = z[s] + scal[SC_BETA] * d[s];
-}
-
-// K_i = (1/m_i) int sigma(v):eps(v) phi_i over the cells around i (the
-// quadrature values of sigma:eps recomputed per node; fixed order)
-__global__ void k_source(ParView v, ParWork w, const double *__restrict__ vh) {
+// K_i = (1/m_i) int sigma(v):eps(v) phi_i: the shares of the cells around i
+// in a fixed order
+__global__ void k_source(ParView v, ParWork w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.n) return;
-  const double lm = v.lam - 2.0 * v.mu / 3.0;
   double acc = 0.0;
-  for (int64_t t = v.nc_ptr[i]; t < v.nc_ptr[i + 1]; ++t) {
-    const int e = v.nc_cell[t], loc = v.nc_local[t];
-    const int32_t *cn = v.cells + (int64_t)e * v.nv;
-    for (int q = 0; q < v.nq; ++q) {
-      const double *gr = v.qgrad + ((int64_t)e * v.nq + q) * 2 * v.nv;
-      double d00 = 0.0, d01 = 0.0, d10 = 0.0, d11 = 0.0;  // d_km = d_m v_k
-      for (int a = 0; a < v.nv; ++a) {
-        const double g0 = gr[a], g1 = gr[v.nv + a];
-        const double u0 = vh[2 * cn[a]], u1 = vh[2 * cn[a] + 1];
-        d00 += u0 * g0;
-        d01 += u0 * g1;
-        d10 += u1 * g0;
-        d11 += u1 * g1;
-      }
-      const double e01 = 0.5 * (d01 + d10), div = d00 + d11;
-      const double se = 2.0 * v.mu * (d00 * d00 + 2.0 * e01 * e01 + d11 * d11) + lm * div * div;
-      acc += v.qw[(int64_t)e * v.nq + q] * v.qphi[((int64_t)e * v.nq + q) * v.nv + loc] * se;
-    }
-  }
+  for (int64_t t = v.nc_ptr[i]; t < v.nc_ptr[i + 1]; ++t) acc += w.ce[(int64_t)v.nc_cell[t] * v.nv + v.nc_local[t]];
   w.K[i] = acc / v.mi[i];
 }
 
@@ -190,7 +277,7 @@ __global__ void k_en_rhs(ParView v, ParWork w, double src, double coefL) {
   const double D = w.D[i];
   w.b[i] = D * w.en[i] + src * v.mi[i] * w.K[i];
   w.x[i] = w.en[i];
-  w.Pd[i] = D + coefL * v.L[v.diag[i]];
+  w.iPd[i] = 1.0 / (D + coefL * v.L[v.diag[i]]);
 }
 
 __global__ void k_en_extrapolate(ParView v, ParWork w) {
@@ -251,39 +338,33 @@ __global__ void k_final(ParView v, ParWork w, double *__restrict__ U) {
 
 }  // namespace
 
+void par_vel_coef(const ParView &v, const double *G, double *A, cudaStream_t s) {
+  k_vel_coef<<<grid_for(v.n), kT, 0, s>>>(v, G, A);
+}
 void par_init(const ParView &v, const ParWork &w, const double *U, double dt, cudaStream_t s) {
   k_par_init<<<grid_for(v.n), kT, 0, s>>>(v, w, U, dt);
 }
-void par_vel_apply(const ParView &v, const ParWork &w, double coef, const double *x, double *y, cudaStream_t s) {
-  k_vel_apply<<<grid_for(v.n), kT, 0, s>>>(v, w, coef, x, y);
-}
-void par_en_apply(const ParView &v, const ParWork &w, double coef, const double *x, double *y, cudaStream_t s) {
-  k_en_apply<<<grid_for(v.n), kT, 0, s>>>(v, w, coef, x, y);
-}
-void par_dot(const ParWork &w, const double *a, const double *b, int64_t m, int slot, cudaStream_t s) {
-  k_dot_partial<<<kRedBlocks, kT, 0, s>>>(a, b, m, w.part);
-  k_sum_partials<<<1, 1024, 0, s>>>(w.part, kRedBlocks, w.scal + slot);
-}
-void par_sub(const double *b, const double *q, double *r, int64_t m, cudaStream_t s) {
-  k_sub<<<grid_for(m), kT, 0, s>>>(b, q, r, m);
-}
-void par_precond(const double *r, const double *Pd, double *z, double *d, int64_t m, cudaStream_t s) {
-  k_precond<<<grid_for(m), kT, 0, s>>>(r, Pd, z, d, m);
-}
-void par_ratio(const ParWork &w, int num, int den, int out, cudaStream_t s) {
-  k_ratio<<<1, 1, 0, s>>>(w.scal, num, den, out);
-}
-void par_copy_scal(const ParWork &w, int from, int to, cudaStream_t s) { k_copy_scal<<<1, 1, 0, s>>>(w.scal, from, to); }
-void par_xr_update(const ParWork &w, double *x, double *r, const double *d, const double *q, int64_t m,
+void par_vel_apply(const ParView &v, const ParWork &w, double coef, const double *x, double *y, const int *skip,
                    cudaStream_t s) {
-  k_xr_update<<<grid_for(m), kT, 0, s>>>(w.scal, x, r, d, q, m);
+  k_vel_apply<<<grid_for(v.n), kT, 0, s>>>(v, w, coef, x, y, skip);
 }
-void par_d_update(const ParWork &w, double *d, const double *z, int64_t m, cudaStream_t s) {
-  k_d_update<<<grid_for(m), kT, 0, s>>>(w.scal, d, z, m);
+void par_en_apply(const ParView &v, const ParWork &w, double coef, const double *x, double *y, const int *skip,
+                  cudaStream_t s) {
+  k_en_apply<<<grid_for(v.n), kT, 0, s>>>(v, w, coef, x, y, skip);
 }
-void par_source(const ParView &v, const ParWork &w, const double *vh, cudaStream_t s) {
-  k_source<<<grid_for(v.n), kT, 0, s>>>(v, w, vh);
+void par_cg_init(const ParWork &w, int64_t m, double tol, cudaStream_t s) {
+  k_cg_init<<<kRedBlocks, kT, 0, s>>>(w, m, tol);
 }
+void par_cg_alpha(const ParWork &w, int64_t m, cudaStream_t s) { k_cg_alpha<<<kRedBlocks, kT, 0, s>>>(w, m); }
+void par_cg_update(const ParWork &w, int64_t m, cudaStream_t s) { k_cg_update<<<kRedBlocks, kT, 0, s>>>(w, m); }
+void par_cg_dir(const ParWork &w, int64_t m, cudaStream_t s) { k_cg_dir<<<kRedBlocks, kT, 0, s>>>(w, m); }
+void par_cell_source(const ParView &v, const ParWork &w, const double *vh, cudaStream_t s) {
+  if (v.nv == 3)
+    k_cell_source<3><<<grid_for(v.n_cells), kT, 0, s>>>(v, w, vh);
+  else
+    k_cell_source<4><<<grid_for(v.n_cells), kT, 0, s>>>(v, w, vh);
+}
+void par_source(const ParView &v, const ParWork &w, cudaStream_t s) { k_source<<<grid_for(v.n), kT, 0, s>>>(v, w); }
 void par_en_rhs(const ParView &v, const ParWork &w, double src, double coefL, cudaStream_t s) {
   k_en_rhs<<<grid_for(v.n), kT, 0, s>>>(v, w, src, coefL);
 }
