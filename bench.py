@@ -171,7 +171,7 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
     S = dim + 2 state components, SP = padded stride, REC = node record."""
     S = dim + 2
     SP = 4 if dim == 2 else 6
-    rec = 8 * (2 * dim + 9)            # node record fields written by prep
+    rec = 8 * (2 * dim + 12)           # node record fields written by prep
     per = {
         "prep": (8 * S + rec, 0),
         # k_visc (c_ij, |c_ij|, 1/|c_ij| and the transpose index of the j > i half;
@@ -213,8 +213,9 @@ def algorithmic_fp64_flops(kernel: str, n: int, nnz: int, dim: int) -> float:
     e = nnz - n
     per_entry = {
         "prep": 0,
-        # k_visc once per unique edge (w_ij, a_ij, lambda_max, d_ij) + k_alpha per entry
-        "visc": (3 * S * dim + 4 * dim + 5 * dim + 15) / 2.0 + 2 * S + 4,
+        # k_visc once per unique edge (v.c_ij of both nodes, w_ij from them, a_ij,
+        # the normal velocities, lambda_max, d_ij) + k_alpha per entry
+        "visc": (12 * dim + 21) / 2.0 + 2 * S + 4,
         "low": 7 * S + 12,
         "lim1": 9 * S + 2 * dim + 18,
         "pass": 5 * S + 2 * dim + 16,
@@ -223,8 +224,8 @@ def algorithmic_fp64_flops(kernel: str, n: int, nnz: int, dim: int) -> float:
         "lsearch": 0,
     }[kernel]
     per_node = {
-        "prep": 4 * dim + S * dim + 45,
-        "visc": 3 * dim + 12,
+        "prep": 4 * dim + 46,
+        "visc": 2 * dim + 12,
         "low": 11,
         "lim1": 2 * S + 6,
         "pass": 3,

@@ -571,7 +571,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
     ALLOC(f_cij, (size_t)dim * nnz);
     ALLOC(f_cn, nnz);
     ALLOC(f_cinv, nnz);
-    ALLOC(f_rec, (size_t)n * REC_MAX);
+    ALLOC(f_rec, (size_t)n * VREC_MAX);
     ALLOC(f_fh, (size_t)n * SP);
     // packed slots [w (S), a, d, 0...] in both dimensions
     static_assert(EdgeLayout<2, float>::packed && EdgeLayout<3, float>::packed, "FP32 edge slots are packed");

@@ -423,16 +423,17 @@ __device__ __forceinline__ void defer_line_searches(const Work &w, int slot, int
 // ---------------------------------------------------------------------------
 // flux f(U) (Sec. 2.1) from the state and the node record's v and p
 // ---------------------------------------------------------------------------
-template <int DIM>
-__device__ __forceinline__ void flux(const double *u, const double *v, double pr, double f[DIM + 2][DIM]) {
+// f(U) = (m, m v^T + p I, v (E + p)) of one node, row s = component
+template <int DIM, typename T>
+__device__ __forceinline__ void node_flux(const T *mv, const T *v, T pr, T H, T f[DIM + 2][DIM]) {
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) f[0][k] = u[1 + k];
+  for (int q = 0; q < DIM; ++q) f[0][q] = mv[q];
 #pragma unroll
   for (int a = 0; a < DIM; ++a)
 #pragma unroll
-    for (int b = 0; b < DIM; ++b) f[1 + a][b] = v[b] * u[1 + a] + (a == b ? pr : 0.0);
+    for (int b = 0; b < DIM; ++b) f[1 + a][b] = mv[a] * v[b] + (a == b ? pr : T(0));
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) f[DIM + 1][k] = v[k] * (u[DIM + 1] + pr);
+  for (int q = 0; q < DIM; ++q) f[DIM + 1][q] = v[q] * H;
 }
 
 // ---------------------------------------------------------------------------
@@ -482,19 +483,20 @@ __global__ void __launch_bounds__(TPB_MAX) k_prep(MeshView m, Params p, const do
   Rr[R::PHI] = phi;
   Rr[R::ETA] = eta;
   Rr[R::EPS] = eps;
+  Rr[R::H] = u[S - 1] + pr;
   Rr[R::IRHO] = irho;
   Rr[R::IEPS] = 1.0 / eps;
-  double f[S][DIM];
-  flux<DIM>(u, v, pr, f);
-#pragma unroll
-  for (int s = 0; s < S; ++s)
-#pragma unroll
-    for (int q = 0; q < DIM; ++q) Rr[R::F + s * DIM + q] = f[s][q];
   if constexpr (!std::is_same<T, double>::value) {
-    // the same record in the viscosity precision (mixed mode)
-    T *Rv = vrec + (int64_t)i * R::SIZE;
+    // the same record in the viscosity precision (mixed mode), with the flux
+    T *Rv = vrec + (int64_t)i * R::VSIZE;
 #pragma unroll
     for (int q = 0; q <= R::IEPS; ++q) Rv[q] = (T)Rr[q];
+    double f[S][DIM];
+    node_flux<DIM, double>(u + 1, v, pr, Rr[R::H], f);
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) Rv[R::F + s * DIM + q] = (T)f[s][q];
   }
 }
 
@@ -513,43 +515,87 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
   const T *cn = (const T *)m.vcn;
   const T *cinv = (const T *)m.vcinv;
   constexpr bool packed = EdgeLayout<DIM, T>::packed;
-  const T *Ri = rec + (int64_t)i * R::SIZE;
-  T vi[DIM], fi[S][DIM], qi[DIM];
+  constexpr int RS = vrec_stride<DIM, T>();
+  const T *Ri = rec + (int64_t)i * RS;
+  T vi[DIM], mi[DIM];
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) vi[k] = Ri[R::V + k];
-  const T pi = Ri[R::P], ai = Ri[R::A], azi = Ri[R::AZ], ipi = Ri[R::IP], etai = Ri[R::ETA];
+  for (int k = 0; k < DIM; ++k) {
+    vi[k] = Ri[R::V + k];
+    mi[k] = Ri[1 + k];
+  }
+  const T pi = Ri[R::P], ai = Ri[R::A], azi = Ri[R::AZ], ipi = Ri[R::IP], etai = Ri[R::ETA], Hi = Ri[R::H];
+  // FP64: w_ij from v.c_ij of both nodes (fewest FP64 operations). FP32: as
+  // differences of the two nodes' fluxes (rounded from FP64 by k_prep), then
+  // dotted with c_ij -- products taken per entry in FP32 (m_i (v_i.c_ij), or
+  // the flux formed in FP32) carry rounding errors that the difference of
+  // rounded fluxes does not: they left ~20x more of the limiter's l = 1
+  // checks failing on the Mach-3 cylinder and raised the error against FP64
+  constexpr bool flux_diff = sizeof(T) == 4;
+  T fi[DIM + 2][DIM], qi[DIM];
+  if constexpr (flux_diff) {
 #pragma unroll
-  for (int s = 0; s < S; ++s)
+    for (int s = 0; s < S; ++s)
 #pragma unroll
-    for (int q = 0; q < DIM; ++q) fi[s][q] = Ri[R::F + s * DIM + q];
+      for (int q = 0; q < DIM; ++q) fi[s][q] = Ri[R::F + s * DIM + q];
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) qi[k] = vi[k] * etai;
+    for (int q = 0; q < DIM; ++q) qi[q] = vi[q] * etai;
+  }
   const bool bi = m.isb[i] != 0;
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
   for (int64_t k = k0; k < k1; ++k) {
     const int j = m.col[k];
     if (j <= i) continue;  // each unique edge once, from the row of min(i, j)
-    const T *Rj = rec + (int64_t)j * R::SIZE;
+    const T *Rj = rec + (int64_t)j * RS;
     const int32_t kt = m.tr[k];
-    T vj[DIM], c[DIM], qj[DIM];
-    const T etaj = Rj[R::ETA];
+    T vj[DIM], mj[DIM], c[DIM];
+    const T pj = Rj[R::P], etaj = Rj[R::ETA], Hj = Rj[R::H];
 #pragma unroll
     for (int q = 0; q < DIM; ++q) {
       vj[q] = Rj[R::V + q];
-      qj[q] = vj[q] * etaj;
+      mj[q] = Rj[1 + q];
       c[q] = cij[(int64_t)q * m.nnz + k];
     }
-    // w_ij = (f_j - f_i) c_ij and a_ij = (q_j - q_i) . c_ij
-    T wv[S], a_ = T(0);
+    // w_ij = (f(U_j) - f(U_i)) c_ij with f = (m, m v^T + p I, v (E + p));
+    // a_ij = (q_j - q_i) . c_ij with q = eta v
+    T vjc = T(0), vic = T(0);
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      T acc = T(0);
-#pragma unroll
-      for (int q = 0; q < DIM; ++q) acc += (Rj[R::F + s * DIM + q] - fi[s][q]) * c[q];
-      wv[s] = acc;
+    for (int q = 0; q < DIM; ++q) {
+      vjc += vj[q] * c[q];
+      vic += vi[q] * c[q];
     }
+    const T dp = pj - pi;
+    T wv[S], a_ = T(0), dm[DIM];
+    if constexpr (flux_diff) {
 #pragma unroll
-    for (int q = 0; q < DIM; ++q) a_ += (qj[q] - qi[q]) * c[q];
+      for (int s = 0; s < S; ++s) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) acc += (Rj[R::F + s * DIM + q] - fi[s][q]) * c[q];
+        wv[s] = acc;
+      }
+      T qj[DIM];
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) qj[q] = vj[q] * etaj;
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) a_ += (qj[q] - qi[q]) * c[q];
+    } else {
+      // X_j (v_j.c) - X_i (v_i.c) as (X_j - X_i) (v_j.c) + X_i (v_j.c - v_i.c):
+      // exactly 0 when the two states are equal (a contracted X_j v_j.c -
+      // X_i v_i.c leaves the rounding error of one product), so that uniform
+      // regions keep P_ij = 0 and the limiter's cheapest exit
+      T w0 = T(0);
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) {
+        dm[q] = mj[q] - mi[q];
+        w0 += dm[q] * c[q];
+      }
+      const T dv = vjc - vic;
+      wv[0] = w0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) wv[1 + a] = dm[a] * vjc + mi[a] * dv + dp * c[a];
+      wv[S - 1] = (Hj - Hi) * vjc + Hi * dv;
+      a_ = (etaj - etai) * vjc + etai * dv;
+    }
     const bool both = bi && m.isb[j];
     // the transposed entry: c_ji = -c_ij unless both nodes lie on the boundary
     // (Sec. 3.1), so w_ji = w_ij and a_ji = a_ij; otherwise evaluate with c_ji.
@@ -558,7 +604,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
     // FP64 3D slots are two sectors: [w0..w3] stored at once, [w4, a, d, 0]
     // once d_ij is known
     constexpr bool two_sectors = packed && sizeof(T) == 8;
-    T wt[S], at = a_;
+    T wt[S], at = a_, vjct = T(0), vict = T(0);
     if constexpr (!packed) {
       T *wk = w_slot<DIM, T>(w, k);
 #pragma unroll
@@ -572,18 +618,36 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
       for (int s = 0; s < S; ++s) wt[s] = wv[s];
     } else {
       T ct[DIM];
-      at = T(0);
 #pragma unroll
       for (int q = 0; q < DIM; ++q) ct[q] = cij[(int64_t)q * m.nnz + kt];
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        T acc = T(0);
-#pragma unroll
-        for (int q = 0; q < DIM; ++q) acc += (fi[s][q] - Rj[R::F + s * DIM + q]) * ct[q];
-        wt[s] = acc;
+      for (int q = 0; q < DIM; ++q) {
+        vjct += vj[q] * ct[q];
+        vict += vi[q] * ct[q];
       }
+      if constexpr (flux_diff) {
+        at = T(0);
 #pragma unroll
-      for (int q = 0; q < DIM; ++q) at += (qi[q] - qj[q]) * ct[q];
+        for (int s = 0; s < S; ++s) {
+          T acc = T(0);
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) acc += (fi[s][q] - Rj[R::F + s * DIM + q]) * ct[q];
+          wt[s] = acc;
+        }
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) at += (qi[q] - vj[q] * etaj) * ct[q];  // q_j as above
+      } else {
+        // (f_i - f_j) . c_ji = -[(f_j . c_ji) - (f_i . c_ji)], in the form above
+        T w0t = T(0);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) w0t += dm[q] * ct[q];
+        const T dvt = vjct - vict;
+        wt[0] = -w0t;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) wt[1 + a] = -(dm[a] * vjct + mi[a] * dvt + dp * ct[a]);
+        wt[S - 1] = -((Hj - Hi) * vjct + Hi * dvt);
+        at = -((etaj - etai) * vjct + etai * dvt);
+      }
     }
     if constexpr (!packed) {
       T *wtk = w_slot<DIM, T>(w, kt);
@@ -593,25 +657,32 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
     } else if constexpr (two_sectors) {
       store_sector((double *)w_slot<DIM, T>(w, kt), wt[0], wt[1], wt[2], wt[3]);
     }
-    // d_ij (Sec. 3.1), mirrored
+    // d_ij (Sec. 3.1), mirrored; normal velocities v . c_ij / |c_ij| (FP32:
+    // v . (c_ij / |c_ij|))
     const T ci = cinv[k];
-    T unl = T(0), unr = T(0);
-#pragma unroll
-    for (int q = 0; q < DIM; ++q) {
-      unl += vi[q] * (c[q] * ci);
-      unr += vj[q] * (c[q] * ci);
-    }
-    T dij = lambda_max<T>(p, unl, pi, ai, azi, ipi, unr, Rj[R::P], Rj[R::A], Rj[R::AZ], Rj[R::IP]) * cn[k];
-    if (both) {
-      const T cit = cinv[kt];
-      T unj = T(0), uni = T(0);
+    T unl = vic * ci, unr = vjc * ci;
+    if constexpr (flux_diff) {
+      unl = unr = T(0);
 #pragma unroll
       for (int q = 0; q < DIM; ++q) {
-        T nq = cij[(int64_t)q * m.nnz + kt] * cit;
-        unj += vj[q] * nq;
-        uni += vi[q] * nq;
+        unl += vi[q] * (c[q] * ci);
+        unr += vj[q] * (c[q] * ci);
       }
-      T dji = lambda_max<T>(p, unj, Rj[R::P], Rj[R::A], Rj[R::AZ], Rj[R::IP], uni, pi, ai, azi, ipi) * cn[kt];
+    }
+    T dij = lambda_max<T>(p, unl, pi, ai, azi, ipi, unr, pj, Rj[R::A], Rj[R::AZ], Rj[R::IP]) * cn[k];
+    if (both) {
+      const T cit = cinv[kt];
+      T unj = vjct * cit, uni = vict * cit;
+      if constexpr (flux_diff) {
+        unj = uni = T(0);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) {
+          T nq = cij[(int64_t)q * m.nnz + kt] * cit;
+          unj += vj[q] * nq;
+          uni += vi[q] * nq;
+        }
+      }
+      T dji = lambda_max<T>(p, unj, pj, Rj[R::A], Rj[R::AZ], Rj[R::IP], uni, pi, ai, azi, ipi) * cn[kt];
       dij = max_nonneg(dij, dji);
     }
     if constexpr (two_sectors) {
@@ -647,7 +718,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_alpha(MeshView m, Params p, Work w)
   using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || w.st->err) return;
-  const T *Ri = (const T *)w.vrec + (int64_t)i * R::SIZE;
+  const T *Ri = (const T *)w.vrec + (int64_t)i * vrec_stride<DIM, T>();
   // eta'(U_i)
   T deta[S];
   {

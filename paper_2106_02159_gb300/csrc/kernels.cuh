@@ -28,8 +28,9 @@ template <int DIM, typename T> struct EdgeLayout {
 };
 
 // Node record written once per stage by k_prep and gathered by the edge loops:
-// [0..S) state, then the primitive and derived quantities below, then the
-// flux f(U) (S x DIM, row-major).
+// [0..S) state, then the primitive and derived quantities below. 2D: 16
+// values (one 128-byte line), 3D: 24. The FP32 copy of mixed mode appends
+// the flux f(U) (S x DIM, row-major) at F, rounded from FP64.
 template <int DIM> struct Rec {
   static constexpr int V = DIM + 2;       // v_1..v_dim
   static constexpr int P = 2 * DIM + 2;   // pressure p
@@ -39,13 +40,20 @@ template <int DIM> struct Rec {
   static constexpr int PHI = 2 * DIM + 6; // Phi = eps rho^-gamma
   static constexpr int ETA = 2 * DIM + 7; // eta = -rho s
   static constexpr int EPS = 2 * DIM + 8; // internal energy eps
-  static constexpr int F = 2 * DIM + 9;   // flux f(U)[s][q] at F + s * DIM + q
-  static constexpr int IRHO = F + (DIM + 2) * DIM;  // 1/rho
-  static constexpr int IEPS = IRHO + 1;             // 1/eps
-  static constexpr int SIZE = DIM == 2 ? 24 : 32;
+  static constexpr int H = 2 * DIM + 9;   // E + p
+  static constexpr int IRHO = 2 * DIM + 10;  // 1/rho
+  static constexpr int IEPS = 2 * DIM + 11;  // 1/eps
+  static constexpr int SIZE = DIM == 2 ? 16 : 24;
   static_assert(IEPS < SIZE, "node record too small");
+  static constexpr int F = SIZE;                                     // FP32 copy only
+  static constexpr int VSIZE = SIZE + ((DIM + 2) * DIM + 7) / 8 * 8;  // FP32 copy: 24 (2D), 40 (3D)
 };
-constexpr int REC_MAX = 32;  // record stride allocated for either dimension
+constexpr int REC_MAX = 24;   // FP64 record stride allocated for either dimension
+constexpr int VREC_MAX = 40;  // FP32 record stride allocated for either dimension
+// stride of the record in the viscosity precision T
+template <int DIM, typename T> __host__ __device__ constexpr int vrec_stride() {
+  return sizeof(T) == 8 ? Rec<DIM>::SIZE : Rec<DIM>::VSIZE;
+}
 
 struct DevStatus {
   int err;                       // eh_status of a device-detected failure, 0 if none

@@ -54,10 +54,10 @@ def device_bytes(mesh, precision=binding.EH_PRECISION_FP64) -> int:
     allocates, rounded up)."""
     S, SP = mesh.dim + 2, (4 if mesh.dim == 2 else 6)
     per_entry = 4 + 4 + 8 * mesh.dim + 8 * 4 + 8 * SP * 2 + 8 * 3 + 8 + 5
-    per_node = 8 * (32 + 8 * SP + 3 * S + 13)
+    per_node = 8 * (24 + 8 * SP + 3 * S + 13)
     if precision == binding.EH_PRECISION_MIXED:
         per_entry += 4 * (mesh.dim + 2 + SP + 1)
-        per_node += 4 * (32 + SP)
+        per_node += 4 * (24 + SP)
     return int(1.1 * (per_entry * mesh.nnz + per_node * mesh.n)) + (1 << 20)
 
 

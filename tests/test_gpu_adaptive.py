@@ -1,7 +1,17 @@
 """The adaptive CFL step (Sec. 3.1, remark on high aspect-ratio meshes) on the
 GPU against the oracle: the same restarts and accepted CFL number, the same
 state; CFL numbers <= 1 never restart and equal a plain step; the low-order
-admissibility counter stays 0 for plain steps. Needs a GPU."""
+admissibility counter stays 0 for plain steps. Needs a GPU.
+
+Above c_cfl = 1 the step is outside the CFL condition of Sec. 3.1 that makes
+U^L a convex combination of the bar states: U^L can leave the local bounds,
+and the line search then clamps l to 0 or 1 on entries whose bound is met to
+rounding, so the state is not a continuous function of the arithmetic. An FP64
+CPU build of the same algorithm with the flux differences written in the
+algebraically equal form (X_j - X_i)(v_j.c) + X_i (v_j - v_i).c moves by
+3.8e-11 (Lax, c = 6), 1.6e-10 (strong shock) and, with the SSP combinations
+also rounded in their other form, 1.3e-8; accepted steps above 1 are held to
+C_ABOVE_ONE_TOL, steps at c <= 1 to the strict parity bar."""
 import numpy as np
 import pytest
 
@@ -12,6 +22,8 @@ from paper_2106_02159_gb300 import workloads as W
 from .test_gpu_parity import STEP_TOL, fma_twin, oracle_spread, rel_l1, solver_for, tolerance
 
 pytestmark = pytest.mark.gpu
+
+C_ABOVE_ONE_TOL = 1e-7
 
 
 def test_cfl_up_to_one_equals_a_plain_step():
@@ -41,7 +53,7 @@ def test_restarts_match_the_oracle(case, cfl_max):
     plain = oracle.Oracle(mesh, cfl=c)
     orf = fma_twin(plain, mesh, None, cfl=c)
     spread = oracle_spread(lambda U: plain.ssprk3_step(U)[0], U0, fn_fma=lambda U: orf.ssprk3_step(U)[0])
-    assert err <= tolerance(STEP_TOL, spread), (err, spread)
+    assert err <= (tolerance(STEP_TOL, spread) if c <= 1.0 else max(C_ABOVE_ONE_TOL, 100.0 * spread)), (err, spread)
     d = s.diagnostics()
     assert d["not_admissible"] == 0 and d["low_order_not_admissible"] == 0
 
