@@ -41,6 +41,22 @@ def test_parabolic_step_matches_oracle(elem):
     assert rel_l1(s.get_state(), ref).max() <= PAR_TOL
 
 
+def test_cg_batching_leaves_the_result_bitwise_unchanged():
+    # the first solve queues CG iterations in a batch of the default length,
+    # the repeat in a batch as long as the first solve took: iterations queued
+    # past convergence must do nothing
+    mesh = _box(24, "q1")
+    U = _random_smooth(mesh, 3)
+    _, s = _pair(mesh, 0.05, 0.03, 0.04)
+    s.set_state(U)
+    info1 = s.parabolic_step(0.01)
+    first = s.get_state()
+    s.set_state(U)
+    info2 = s.parabolic_step(0.01)
+    assert info1 == info2
+    assert np.array_equal(s.get_state(), first)
+
+
 def test_fct_branch_matches_oracle():
     mesh = _box(32, "q1")
     x = mesh.coords
