@@ -1021,9 +1021,18 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
     }
     const double l = lmin(lin[k], lin[m.tr[k]]);
     if (lsym_trace) lsym_trace[k] = l;
-    const double *Pk = w.P + k * SP;
+    // the update with l P. 2D: the remainder (1 - l) P the next search starts
+    // from is stored at once, so the second walk over the row reads it back
+    // instead of gathering the transposed limiter again. 3D: the second walk
+    // forms it (27-entry rows find the first walk's lines of P still in L1,
+    // and storing there in the first walk doubled the kernel's time)
+    double *Pk = w.P + k * SP;
 #pragma unroll
-    for (int s = 0; s < S; ++s) u[s] += lambda_i * l * Pk[s];
+    for (int s = 0; s < S; ++s) {
+      const double pk = Pk[s];
+      u[s] += lambda_i * l * pk;
+      if constexpr (DIM == 2) Pk[s] = (1.0 - l) * pk;
+    }
   }
   double *Uo = Uout + (int64_t)i * SP;
 #pragma unroll
@@ -1037,13 +1046,18 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
       lout[k] = 1.0;
       continue;
     }
-    const double l = lmin(lin[k], lin[m.tr[k]]);
     double *Pk = w.P + k * SP;
     double P[S];
+    if constexpr (DIM == 2) {
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      P[s] = (1.0 - l) * Pk[s];
-      Pk[s] = P[s];
+      for (int s = 0; s < S; ++s) P[s] = Pk[s];
+    } else {
+      const double l = lmin(lin[k], lin[m.tr[k]]);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        P[s] = (1.0 - l) * Pk[s];
+        Pk[s] = P[s];
+      }
     }
     if (line_search_at_one<DIM>(p, u, P, rmin, rmax, phimin5))
       lout[k] = 1.0;
