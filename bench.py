@@ -192,13 +192,13 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
 # developed flow); a launch moves about this times nnz. Only valid for the
 # kernels as captured there, and only for the 2D FP64 cylinder workload.
 NCU_DRAM_BYTES_PER_ENTRY_2D_FP64 = {
-    "prep": 5.7, "visc": 180.6, "low": 75.4, "lim1": 121.8, "pass": 88.0, "final": 57.0,
+    "prep": 5.6, "visc": 180.3, "low": 75.4, "lim1": 121.4, "pass": 86.9, "final": 56.9,
 }
 # FP64 pipe activity (sm__pipe_fp64_cycles_active, % of peak) on the same capture:
 # how busy the issue-bound kernels keep the FP64 units (k_visc and k_alpha
 # time-weighted as "visc")
 NCU_FP64_PIPE_ACTIVE_2D_FP64 = {
-    "prep": 0.836, "visc": 0.826, "low": 0.859, "lim1": 0.839, "pass": 0.578, "final": 0.632,
+    "prep": 0.835, "visc": 0.827, "low": 0.859, "lim1": 0.838, "pass": 0.611, "final": 0.633,
 }
 
 
