@@ -307,6 +307,68 @@ eh_status eh_set_launch_shape(eh_ctx *ctx, int32_t kernel, int32_t threads_per_b
 /* Number of kernel launches one eh_step issues (for accounting). */
 int32_t eh_launches_per_step(const eh_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Served stream of independent solves (continuous batching, one device).
+ * A batch admits requests first come, first served while their device memory
+ * fits a budget next to the requests already running (the first request is
+ * always admitted); each admitted request keeps its mesh and state resident in
+ * a context of its own, on that context's own stream, configured as cfg. The
+ * caller owns the batch and frees it with eh_batch_destroy; the batch owns the
+ * requests' contexts. Not thread-safe: one host thread per batch.
+ * ------------------------------------------------------------------------ */
+typedef struct eh_batch eh_batch;
+
+/* Device bytes a context needs for a mesh of n nodes and nnz CSR entries in
+ * dimension dim and precision EH_PRECISION_* (the estimate admission uses:
+ * the arrays eh_upload_mesh allocates, plus 10% and 1 MiB). Host only.
+ * EH_ERR_INVALID_ARG for dim not 2 or 3, an unknown precision, n < 1 or
+ * nnz < n. */
+eh_status eh_estimate_device_bytes(int32_t dim, int32_t precision, int32_t n, int64_t nnz, uint64_t *bytes);
+
+/* Creates an empty batch. cfg as for eh_create, with cfg->stream NULL (every
+ * request runs on a stream of its own); hbm_budget_bytes > 0 is the device
+ * memory the running requests may hold together. EH_ERR_INVALID_ARG
+ * otherwise; *out is NULL on error. */
+eh_status eh_batch_create(const eh_config *cfg, uint64_t hbm_budget_bytes, eh_batch **out);
+
+/* Admits one request: a mesh (arguments as eh_upload_mesh, host pointers,
+ * copied), its initial state U0[S][n] (host, copied; the boundary
+ * post-processing of Sec. 4 is applied to it) and its end time t_final > 0
+ * (the last step is shortened to land on it, as eh_set_instances). *ticket
+ * receives the request's identifier. EH_ERR_OOM: the request does not fit the
+ * budget now (nothing changed; admit it after a poll has freed memory);
+ * errors of eh_upload_mesh / eh_set_state otherwise (nothing kept). */
+eh_status eh_batch_admit(eh_batch *b, int32_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                         const double *cij, const double *mij, const double *mi, int32_t n_bnd,
+                         const int32_t *bnd_node, const int32_t *bnd_kind, const double *bnd_normal,
+                         const double *bnd_state, const double *U0, double t_final, int64_t *ticket);
+
+/* Launches 'steps' >= 1 SSPRK(3,3) steps (CUDA-graph replays) for every
+ * running request, one step of each request in turn, each on its own stream
+ * (the requests overlap on the device); then synchronises every running
+ * request and marks those that reached t_final, or failed, as finished.
+ * *n_finished (may be NULL) receives the number of finished requests not yet
+ * polled. A request's failure does not stop the others: eh_batch_poll returns
+ * its status. */
+eh_status eh_batch_advance(eh_batch *b, int32_t steps, int32_t *n_finished);
+
+/* *done = 0 while the request runs. Once it has finished: *done = 1, U_out
+ * (host, [S][n], or NULL) receives its state, t (may be NULL) its simulated
+ * time, steps (may be NULL) the steps launched for it; its context is freed
+ * and its ticket retired. Returns the status that stopped the request
+ * (EH_OK when it reached t_final); EH_ERR_INVALID_ARG for an unknown ticket. */
+eh_status eh_batch_poll(eh_batch *b, int64_t ticket, int32_t *done, double *U_out, double *t, int64_t *steps);
+
+/* Requests admitted and not yet polled, and the device bytes they hold by the
+ * admission estimate (either pointer may be NULL). */
+eh_status eh_batch_active(const eh_batch *b, int32_t *n_requests, uint64_t *bytes_in_use);
+
+/* Text of the batch's last error (never NULL). */
+const char *eh_batch_last_error(const eh_batch *b);
+
+/* Frees the batch and every request still in it; NULL is a no-op. */
+void eh_batch_destroy(eh_batch *b);
+
 /* Text of the last error of this context (never NULL). */
 const char *eh_last_error(const eh_ctx *ctx);
 

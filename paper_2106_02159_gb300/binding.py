@@ -18,7 +18,7 @@ _ROOT = os.path.dirname(_HERE)
 CSRC = os.path.join(_HERE, "csrc")
 BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libeuler_hyp.so")
-SOURCES = ("kernels.cu", "capi.cu", "noalloc.cu", "parabolic.cu")
+SOURCES = ("kernels.cu", "capi.cu", "noalloc.cu", "parabolic.cu", "batch.cu")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]
 
@@ -35,7 +35,9 @@ EXPORTS = ("eh_config_default", "eh_create", "eh_upload_mesh", "eh_set_state", "
            "eh_get_diagnostics", "eh_trace", "eh_profile_enable", "eh_profile_read", "eh_launches_per_step",
            "eh_last_error", "eh_status_string", "eh_destroy", "eh_cfl_dt_noalloc", "eh_set_instances",
            "eh_get_instances", "eh_autotune", "eh_get_block_sizes", "eh_get_rows_per_sm", "eh_set_launch_shape",
-           "eh_step_adaptive", "eh_set_viscosity", "eh_parabolic_step", "eh_step_ns")
+           "eh_step_adaptive", "eh_set_viscosity", "eh_parabolic_step", "eh_step_ns",
+           "eh_estimate_device_bytes", "eh_batch_create", "eh_batch_admit", "eh_batch_advance", "eh_batch_poll",
+           "eh_batch_active", "eh_batch_last_error", "eh_batch_destroy")
 CFL_NOALLOC_MAX_ROWS = 1 << 23
 KERNEL_NAMES = ("prep", "visc", "low", "tau", "lim1", "pass", "final", "lsearch")
 
@@ -123,9 +125,21 @@ def load(path: str | None = None):
     lib.eh_parabolic_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ParabolicInfo)]
     lib.eh_step_ns.argtypes = [vp, ctypes.c_double, dp, ctypes.POINTER(ParabolicInfo)]
     lib.eh_cfl_dt_noalloc.argtypes = [i32, ctypes.c_double, ctypes.c_double, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    u64 = ctypes.c_uint64
+    lib.eh_estimate_device_bytes.argtypes = [i32, i32, i32, i64, ctypes.POINTER(u64)]
+    lib.eh_batch_create.argtypes = [ctypes.POINTER(Config), u64, ctypes.POINTER(vp)]
+    lib.eh_batch_admit.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, ctypes.c_double,
+                                   ctypes.POINTER(i64)]
+    lib.eh_batch_advance.argtypes = [vp, i32, ctypes.POINTER(i32)]
+    lib.eh_batch_poll.argtypes = [vp, i64, ctypes.POINTER(i32), vp, dp, ctypes.POINTER(i64)]
+    lib.eh_batch_active.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(u64)]
+    lib.eh_batch_last_error.argtypes = [vp]
+    lib.eh_batch_last_error.restype = ctypes.c_char_p
+    lib.eh_batch_destroy.argtypes = [vp]
+    lib.eh_batch_destroy.restype = None
     for name in EXPORTS:
         if name not in ("eh_config_default", "eh_destroy", "eh_launches_per_step", "eh_last_error",
-                        "eh_status_string"):
+                        "eh_status_string", "eh_batch_last_error", "eh_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     if path == LIB_PATH:
         _lib = lib
@@ -160,6 +174,93 @@ def _arr(a, dtype):
 
 def _p(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def estimate_device_bytes(dim, precision, n, nnz, lib=None) -> int:
+    """Device bytes a context needs for a mesh (eh_estimate_device_bytes)."""
+    lib = lib or load()
+    out = ctypes.c_uint64(0)
+    st = lib.eh_estimate_device_bytes(int(dim), int(precision), int(n), int(nnz), ctypes.byref(out))
+    if st != EH_OK:
+        raise EulerError(st, "eh_estimate_device_bytes: invalid arguments")
+    return int(out.value)
+
+
+class Batch:
+    """A served stream of independent solves (eh_batch_create ... eh_batch_destroy)."""
+
+    def __init__(self, hbm_budget_bytes, dim=2, gamma=1.4, cfl=0.5, limiter_passes=2, bound_relaxation=False,
+                 device=0, precision=EH_PRECISION_FP64, lib=None):
+        self.lib = lib or load()
+        cfg = Config()
+        self.lib.eh_config_default(ctypes.byref(cfg))
+        cfg.dim, cfg.gamma, cfg.cfl, cfg.limiter_passes = dim, gamma, cfl, limiter_passes
+        cfg.bound_relaxation, cfg.precision, cfg.device = int(bool(bound_relaxation)), precision, device
+        cfg.stream = None
+        self.dim, self.S = dim, dim + 2
+        b = ctypes.c_void_p()
+        st = self.lib.eh_batch_create(ctypes.byref(cfg), int(hbm_budget_bytes), ctypes.byref(b))
+        if st != EH_OK:
+            raise EulerError(st, f"eh_batch_create failed: {self.lib.eh_status_string(st).decode()}")
+        self.b = b
+        self.n_of = {}
+
+    def _check(self, st, what):
+        if st != EH_OK:
+            raise EulerError(st, f"{what}: {self.lib.eh_batch_last_error(self.b).decode()}")
+
+    def admit(self, mesh, U0, t_final, bnd_state=None):
+        """Admits a request; returns its ticket, or None when it does not fit
+        the budget now (EH_ERR_OOM)."""
+        k = dict(row_ptr=_arr(mesh.row_ptr, np.int64), col=_arr(mesh.col, np.int32), cij=_arr(mesh.cij, np.float64),
+                 mij=_arr(mesh.mij, np.float64), mi=_arr(mesh.mi, np.float64), bnd_node=_arr(mesh.bnd_node, np.int32),
+                 bnd_kind=_arr(mesh.bnd_kind, np.int32), bnd_normal=_arr(mesh.bnd_normal, np.float64),
+                 bnd_state=None if bnd_state is None else _arr(bnd_state, np.float64), U0=_arr(U0, np.float64))
+        assert k["U0"].shape == (self.S, mesh.n), k["U0"].shape
+        ticket = ctypes.c_int64(0)
+        st = self.lib.eh_batch_admit(self.b, mesh.n, mesh.nnz, _p(k["row_ptr"]), _p(k["col"]), _p(k["cij"]),
+                                     _p(k["mij"]), _p(k["mi"]), mesh.n_bnd, _p(k["bnd_node"]), _p(k["bnd_kind"]),
+                                     _p(k["bnd_normal"]), _p(k["bnd_state"]), _p(k["U0"]), float(t_final),
+                                     ctypes.byref(ticket))
+        if st == EH_ERR_OOM:
+            return None
+        self._check(st, "eh_batch_admit")
+        self.n_of[ticket.value] = mesh.n
+        return ticket.value
+
+    def advance(self, steps=1) -> int:
+        """steps SSPRK(3,3) steps of every running request; returns the
+        number of finished requests not yet polled."""
+        fin = ctypes.c_int32(0)
+        self._check(self.lib.eh_batch_advance(self.b, int(steps), ctypes.byref(fin)), "eh_batch_advance")
+        return int(fin.value)
+
+    def poll(self, ticket):
+        """None while the request runs; else (U [S, n], t, steps) and the
+        request is retired."""
+        done, t, steps = ctypes.c_int32(0), ctypes.c_double(0.0), ctypes.c_int64(0)
+        n = self.n_of.get(ticket)
+        U = None if n is None else np.empty((self.S, n))
+        st = self.lib.eh_batch_poll(self.b, int(ticket), ctypes.byref(done), _p(U), ctypes.byref(t),
+                                    ctypes.byref(steps))
+        if done.value:
+            del self.n_of[ticket]
+        self._check(st, "eh_batch_poll")
+        return (U, t.value, steps.value) if done.value else None
+
+    def active(self):
+        """(requests admitted and not yet polled, device bytes they hold)."""
+        n, used = ctypes.c_int32(0), ctypes.c_uint64(0)
+        self._check(self.lib.eh_batch_active(self.b, ctypes.byref(n), ctypes.byref(used)), "eh_batch_active")
+        return int(n.value), int(used.value)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.eh_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        self.close()
 
 
 class Solver:

@@ -1,16 +1,16 @@
 """Continuous-batching solve server on one GPU.
 
 Requests (a mesh, an initial state, boundary data and a final time) arrive
-over time. The server admits a waiting request as soon as its device memory
-fits in the budget next to the requests already running, keeps every admitted
-request's mesh and state resident in its own solver context on its own CUDA
-stream, and advances all admitted requests together: each loop iteration
-launches one SSPRK(3,3) step (one CUDA-graph launch) for every active request,
-and the launches of different requests overlap on the device. Each request
-stops on the device at its final time (the last step is shortened, see
-eh_set_instances); the server retires it between iterations, frees its memory
-and admits the next ones. Every step runs in the CUDA library; this module
-only orchestrates.
+over time. The server hands every arrived request to the library's batch
+(eh_batch_admit), which admits it as soon as its device memory fits in the
+budget next to the requests already running, keeps its mesh and state
+resident in a context of its own on its own CUDA stream, and advances all
+admitted requests together (eh_batch_advance: one SSPRK(3,3) step -- one
+CUDA-graph launch -- per request in turn, the launches overlapping on the
+device). Each request stops on the device at its final time (the last step is
+shortened); eh_batch_poll returns its state and frees its memory. Admission,
+stepping and retirement run in the library; this module keeps the arrival
+clock and the results.
 """
 from __future__ import annotations
 
@@ -50,82 +50,58 @@ class Result:
 
 
 def device_bytes(mesh, precision=binding.EH_PRECISION_FP64) -> int:
-    """Device memory a context needs for this mesh (the arrays eh_upload_mesh
-    allocates, rounded up)."""
-    S, SP = mesh.dim + 2, (4 if mesh.dim == 2 else 6)
-    per_entry = 4 + 4 + 8 * mesh.dim + 8 * 4 + 8 * SP * 2 + 8 * 3 + 8 + 5
-    per_node = 8 * (24 + 8 * SP + 3 * S + 13)
-    if precision == binding.EH_PRECISION_MIXED:
-        per_entry += 4 * (mesh.dim + 2 + SP + 1)
-        per_node += 4 * (24 + SP)
-    return int(1.1 * (per_entry * mesh.nnz + per_node * mesh.n)) + (1 << 20)
+    """Device memory a context needs for this mesh (the library's admission
+    estimate, eh_estimate_device_bytes)."""
+    return binding.estimate_device_bytes(mesh.dim, precision, mesh.n, mesh.nnz)
 
 
 class SolveServer:
     def __init__(self, hbm_budget_bytes: int, precision=binding.EH_PRECISION_FP64, device=0, poll_every=4,
                  lib=None):
-        import torch  # streams only
-        self.torch = torch
         self.budget = int(hbm_budget_bytes)
         self.precision = precision
         self.device = device
         self.poll_every = poll_every
         self.lib = lib or binding.load()
 
-    def _start(self, req):
-        stream = self.torch.cuda.Stream(device=self.device)
-        s = binding.Solver(dim=req.mesh.dim, precision=self.precision, device=self.device,
-                           stream=stream.cuda_stream, lib=self.lib)
-        s.upload_mesh(req.mesh, req.bnd_state)
-        s.set_instances([0, req.mesh.n], [req.t_final])
-        s.set_state(req.U0)
-        s.apply_boundary_conditions()
-        return s, stream
-
     def run(self, requests, clock=time.perf_counter):
         """Serve the requests (sorted by arrival); returns the Results in
         completion order. Arrival times are honoured against ``clock``."""
         pending = sorted(requests, key=lambda r: r.arrival)
-        waiting, active, done = [], [], []
-        used = 0
+        if not pending:
+            return []
+        dims = {r.mesh.dim for r in pending}
+        assert len(dims) == 1, "one batch serves one dimension"
+        batch = binding.Batch(self.budget, dim=dims.pop(), device=self.device, precision=self.precision,
+                              lib=self.lib)
+        waiting, active, done = [], {}, []
         t0 = clock()
-        it = 0
-        while pending or waiting or active:
-            now = clock() - t0
-            while pending and pending[0].arrival <= now:
-                waiting.append(pending.pop(0))
-            # admission by free device memory (first come, first served)
-            while waiting:
-                need = device_bytes(waiting[0].mesh, self.precision)
-                if active and used + need > self.budget:
-                    break
-                req = waiting.pop(0)
-                s, stream = self._start(req)
-                active.append(dict(req=req, solver=s, stream=stream, need=need, admitted=clock() - t0, steps=0))
-                used += need
-            if not active:
-                if pending:  # idle until the next arrival
-                    time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
-                continue
-            # one step for every active request; the launches overlap on the device
-            for a in active:
-                a["solver"].run(1)
-                a["steps"] += 1
-            it += 1
-            if it % self.poll_every:
-                continue
-            still = []
-            for a in active:
-                info = a["solver"].instances()
-                if info["t"][0] >= a["req"].t_final:
-                    U = a["solver"].get_state()
-                    done.append(Result(a["req"].name, a["req"].mesh.n, a["req"].arrival, a["admitted"],
-                                       clock() - t0, a["steps"], float(info["t"][0]), U))
-                    a["solver"].close()
-                    used -= a["need"]
-                else:
-                    still.append(a)
-            active = still
+        try:
+            while pending or waiting or active:
+                now = clock() - t0
+                while pending and pending[0].arrival <= now:
+                    waiting.append(pending.pop(0))
+                # admission by free device memory (first come, first served)
+                while waiting:
+                    ticket = batch.admit(waiting[0].mesh, waiting[0].U0, waiting[0].t_final, waiting[0].bnd_state)
+                    if ticket is None:
+                        break
+                    active[ticket] = (waiting.pop(0), clock() - t0)
+                if not active:
+                    if pending:  # idle until the next arrival
+                        time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
+                    continue
+                if batch.advance(self.poll_every) == 0:
+                    continue
+                for ticket in list(active):
+                    out = batch.poll(ticket)
+                    if out is None:
+                        continue
+                    U, t, steps = out
+                    req, admitted = active.pop(ticket)
+                    done.append(Result(req.name, req.mesh.n, req.arrival, admitted, clock() - t0, steps, t, U))
+        finally:
+            batch.close()
         return done
 
 

@@ -43,6 +43,16 @@ def test_host_only_calls(lib):
     assert lib.eh_create(None, ctypes.byref(out)) == binding.EH_ERR_INVALID_ARG and not out.value
     bad = binding.Config()
     lib.eh_config_default(ctypes.byref(bad))
+    assert lib.eh_batch_last_error(None) == b"null batch"
+    lib.eh_batch_destroy(None)
+    assert lib.eh_batch_create(None, 1 << 30, ctypes.byref(out)) == binding.EH_ERR_INVALID_ARG and not out.value
+    nbytes = ctypes.c_uint64(0)
+    assert lib.eh_estimate_device_bytes(2, 0, 1000, 9000, ctypes.byref(nbytes)) == binding.EH_OK
+    small = nbytes.value
+    assert lib.eh_estimate_device_bytes(2, 0, 2000, 18000, ctypes.byref(nbytes)) == binding.EH_OK
+    assert (1 << 20) < small < nbytes.value
+    for args in ((4, 0, 10, 10), (2, 5, 10, 10), (2, 0, 0, 10), (2, 0, 10, 5)):
+        assert lib.eh_estimate_device_bytes(*args, ctypes.byref(nbytes)) == binding.EH_ERR_INVALID_ARG, args
     for field, value in (("dim", 4), ("gamma", 2.0), ("cfl", 1.5), ("limiter_passes", 0)):
         b2 = binding.Config.from_buffer_copy(bad)
         setattr(b2, field, value)

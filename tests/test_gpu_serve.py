@@ -33,3 +33,27 @@ def test_admission_respects_the_memory_budget():
     spans = sorted((r.admitted, r.finished) for r in results)
     for (a0, f0), (a1, f1) in zip(spans, spans[1:]):
         assert a1 >= f0 - 1e-9  # never two at once
+
+
+def test_batch_api_budget_tickets_and_results():
+    # the C batch directly: a second request does not fit a one-request budget
+    # until the first has been polled; unknown tickets are refused; the
+    # result equals the solve alone
+    reqs = serve.poisson_trace(2, rate=1e6, seed=7, n_range=(1500, 2500), t_final=0.01)
+    need = max(serve.device_bytes(r.mesh) for r in reqs)
+    b = B.Batch(need)
+    t0 = b.admit(reqs[0].mesh, reqs[0].U0, reqs[0].t_final, reqs[0].bnd_state)
+    assert t0 is not None
+    assert b.admit(reqs[1].mesh, reqs[1].U0, reqs[1].t_final, reqs[1].bnd_state) is None
+    assert b.active() == (1, serve.device_bytes(reqs[0].mesh))
+    with pytest.raises(B.EulerError):
+        b.poll(t0 + 100)
+    assert b.poll(t0) is None  # still running
+    while b.advance(3) == 0:
+        pass
+    U, t, steps = b.poll(t0)
+    assert t == reqs[0].t_final and steps > 0
+    assert np.array_equal(U, serve.solve_alone(reqs[0])[0])
+    assert b.active() == (0, 0)
+    assert b.admit(reqs[1].mesh, reqs[1].U0, reqs[1].t_final, reqs[1].bnd_state) is not None
+    b.close()
