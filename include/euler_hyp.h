@@ -85,6 +85,13 @@ typedef struct {
   int64_t line_searches_iterated; /* of those, searches that ran the bracketing iteration */
   int64_t low_order_not_admissible; /* rows whose low-order update U^L left the admissible set
                                        (always 0 with c_cfl <= 1; see eh_step_adaptive) */
+  /* of the current state (all instances together; 0 before eh_set_state): */
+  double rho_min;             /* min_i rho_i */
+  double e_min;               /* min_i of the specific internal energy E/rho - |m|^2/(2 rho^2) */
+  double total[5];            /* sum_i m_i U_i with the lumped masses: mass, momentum, total energy
+                                 (S = dim + 2 values, the rest 0); constant up to the boundary
+                                 fluxes (Lemma 3.1; exactly so, to roundoff, on periodic or closed
+                                 slip domains, Lemma 4.5) */
 } eh_diagnostics;
 
 /* Fills *cfg with the defaults: dim 2, gamma 1.4, cfl 0.5, 2 limiter passes,
@@ -200,7 +207,9 @@ eh_status eh_step_ns(eh_ctx *ctx, double dt, double *tau_used, eh_parabolic_info
 /* Waits for queued work and reports a pending device-side error. */
 eh_status eh_synchronize(eh_ctx *ctx);
 
-/* Diagnostics of the last steps (synchronises). */
+/* Diagnostics of the last steps and of the current state (synchronises; the
+ * state statistics are two reductions on the device, in a fixed order, so the
+ * same state gives the same bits). */
 eh_status eh_get_diagnostics(eh_ctx *ctx, eh_diagnostics *out);
 
 /* Intermediate arrays of the last forward-Euler stage, for checking against

@@ -68,7 +68,8 @@ class Diagnostics(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_int64), ("last_dt", ctypes.c_double),
                 ("last_stage_bound", ctypes.c_double * 3), ("cfl_violations", ctypes.c_int64),
                 ("not_admissible", ctypes.c_int64), ("line_searches_deferred", ctypes.c_int64),
-                ("line_searches_iterated", ctypes.c_int64), ("low_order_not_admissible", ctypes.c_int64)]
+                ("line_searches_iterated", ctypes.c_int64), ("low_order_not_admissible", ctypes.c_int64),
+                ("rho_min", ctypes.c_double), ("e_min", ctypes.c_double), ("total", ctypes.c_double * 5)]
 
 
 class ParabolicInfo(ctypes.Structure):
@@ -393,7 +394,8 @@ class Solver:
                     cfl_violations=d.cfl_violations, not_admissible=d.not_admissible,
                     line_searches_deferred=d.line_searches_deferred,
                     line_searches_iterated=d.line_searches_iterated,
-                    low_order_not_admissible=d.low_order_not_admissible)
+                    low_order_not_admissible=d.low_order_not_admissible,
+                    rho_min=d.rho_min, e_min=d.e_min, total=list(d.total)[:self.S])
 
     def trace(self, what):
         sizes = {EH_TRACE_D_IJ: self.nnz, EH_TRACE_ALPHA: self.n, EH_TRACE_U_LOW: self.S * self.n,

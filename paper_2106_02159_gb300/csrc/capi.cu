@@ -60,6 +60,7 @@ struct eh_ctx {
   int ninst = 1;
   std::vector<void *> inst_allocs;
   double *Usave = nullptr;  // state saved while autotuning
+  double *stat_part = nullptr, *stat_out = nullptr;  // state statistics of eh_get_diagnostics
   // parabolic sub-step (Sec. 5): finite-element data, constants, work arrays
   bool have_visc = false;
   ParView pv{};
@@ -562,6 +563,8 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   const int SP = SP_of(c);
   Work &w = c->wk;
   ALLOC(w.rec, (size_t)n * REC_MAX);
+  ALLOC(c->stat_part, (size_t)7 * STAT_BLOCKS);
+  ALLOC(c->stat_out, 8);
   ALLOC(w.alpha, n);
   ALLOC(w.inc, (size_t)n * SP);
   float *f_cij = nullptr, *f_cn = nullptr, *f_cinv = nullptr;
@@ -1172,6 +1175,18 @@ eh_status eh_get_diagnostics(eh_ctx *c, eh_diagnostics *out) {
   out->line_searches_deferred = (int64_t)c->st_host->line_searches_deferred;
   out->line_searches_iterated = (int64_t)c->st_host->line_searches_iterated;
   out->low_order_not_admissible = (int64_t)c->st_host->low_not_admissible;
+  if (c->have_state) {
+    double stats[8] = {0.0};
+    if (c->cfg.dim == 2) launch_state_stats<2>(c->n, c->U, c->mv.mi, c->stat_part, c->stat_out, c->stream);
+    else launch_state_stats<3>(c->n, c->U, c->mv.mi, c->stat_part, c->stat_out, c->stream);
+    CUDA_TRY(c, cudaGetLastError());
+    CUDA_TRY(c, cudaMemcpyAsync(stats, c->stat_out, sizeof(double) * (c->cfg.dim + 4), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    out->rho_min = stats[0];
+    out->e_min = stats[1];
+    for (int q = 0; q < c->cfg.dim + 2; ++q) out->total[q] = stats[2 + q];
+  }
   return st;
 }
 

@@ -1538,6 +1538,66 @@ void launch_final(const MeshView &m, const Params &p, const Work &w, const doubl
 template <int DIM> void launch_apply_bc(const MeshView &m, const Params &p, double *U, cudaStream_t s) {
   k_apply_bc<DIM><<<nblocks(m.n, 256), 256, 0, s>>>(m, p, U);
 }
+// min_i rho_i, min_i e_i (e = E/rho - |m|^2/(2 rho^2)) and sum_i m_i U_i over
+// the whole state: a fixed grid of STAT_BLOCKS blocks with a grid stride,
+// fixed shuffle and shared-memory trees per block, then one block summing the
+// partials in a fixed order -- the same bits on every run
+template <int DIM> __global__ void __launch_bounds__(256) k_state_partial(int n, const double *__restrict__ U,
+                                                                        const double *__restrict__ mi,
+                                                                        double *__restrict__ part) {
+  constexpr int S = DIM + 2, NV = S + 2;
+  double v[NV];
+  v[0] = INFINITY;
+  v[1] = INFINITY;
+#pragma unroll
+  for (int s = 0; s < S; ++s) v[2 + s] = 0.0;
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += STAT_BLOCKS * 256) {
+    double u[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) u[s] = U[(int64_t)s * n + i];
+    const double irho = 1.0 / u[0];
+    double m2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) m2 += u[1 + q] * u[1 + q];
+    v[0] = fmin(v[0], u[0]);
+    v[1] = fmin(v[1], u[S - 1] * irho - 0.5 * m2 * irho * irho);
+    const double m = mi[i];
+#pragma unroll
+    for (int s = 0; s < S; ++s) v[2 + s] += m * u[s];
+  }
+  __shared__ double sh[NV][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double x = __shfl_down_sync(0xffffffffu, v[q], o);
+      v[q] = q < 2 ? fmin(v[q], x) : v[q] + x;
+    }
+    if (lane == 0) sh[q][warp] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    const int q = threadIdx.x;
+    double acc = sh[q][0];
+    for (int w = 1; w < 8; ++w) acc = q < 2 ? fmin(acc, sh[q][w]) : acc + sh[q][w];
+    part[q * STAT_BLOCKS + blockIdx.x] = acc;
+  }
+}
+
+__global__ void k_state_final(int nv, const double *__restrict__ part, double *__restrict__ out) {
+  const int q = threadIdx.x;
+  if (q >= nv) return;
+  double acc = part[q * STAT_BLOCKS];
+  for (int b = 1; b < STAT_BLOCKS; ++b) acc = q < 2 ? fmin(acc, part[q * STAT_BLOCKS + b]) : acc + part[q * STAT_BLOCKS + b];
+  out[q] = acc;
+}
+
+template <int DIM>
+void launch_state_stats(int n, const double *U, const double *mi, double *part, double *out, cudaStream_t s) {
+  k_state_partial<DIM><<<STAT_BLOCKS, 256, 0, s>>>(n, U, mi, part);
+  k_state_final<<<1, 32, 0, s>>>(DIM + 4, part, out);
+}
 template <int DIM> void launch_count_not_admissible(int n, const double *U, DevStatus *st, cudaStream_t s) {
   k_count_not_admissible<DIM><<<nblocks(n, 256), 256, 0, s>>>(n, U, st);
 }
@@ -1562,7 +1622,8 @@ EH_INSTANTIATE_T(3, float)
   template void launch_final<DIM>(const MeshView &, const Params &, const Work &, const double *, const double *,     \
                                   const double *, double, double *, double *, int, int, cudaStream_t);                \
   template void launch_apply_bc<DIM>(const MeshView &, const Params &, double *, cudaStream_t);                       \
-  template void launch_count_not_admissible<DIM>(int, const double *, DevStatus *, cudaStream_t);
+  template void launch_count_not_admissible<DIM>(int, const double *, DevStatus *, cudaStream_t);            \
+  template void launch_state_stats<DIM>(int, const double *, const double *, double *, double *, cudaStream_t);
 
 EH_INSTANTIATE(2)
 EH_INSTANTIATE(3)

@@ -196,5 +196,11 @@ void launch_final(const MeshView &m, const Params &p, const Work &w, const doubl
                   cudaStream_t s);
 template <int DIM> void launch_apply_bc(const MeshView &m, const Params &p, double *U, cudaStream_t s);
 template <int DIM> void launch_count_not_admissible(int n, const double *U, DevStatus *st, cudaStream_t s);
+// out[0] = min rho, out[1] = min specific internal energy, out[2 + s] =
+// sum_i m_i U_i[s] of the state U[S][n] (deterministic); part holds
+// (DIM + 4) x STAT_BLOCKS partials
+constexpr int STAT_BLOCKS = 304;
+template <int DIM>
+void launch_state_stats(int n, const double *U, const double *mi, double *part, double *out, cudaStream_t s);
 
 }  // namespace eh
