@@ -6,10 +6,11 @@
 // is bound by FP64 instruction issue, not by HBM. Every edge loop therefore
 // runs one thread per CSR row (no idle lanes in 7/9/27-entry rows), sums in
 // the row's column order (bitwise reproducible), and trades bytes for FP64
-// work: per-node quantities (primitives, a p^-z, Phi, eta, the flux f(U)) are
-// computed once per stage in k_prep and gathered; |c_ij|, 1/|c_ij|, m_ij/m_j and m_ji/m_i are
-// static per-edge arrays; (f(U_j) - f(U_i)) c_ij is computed once per edge in
-// k_visc and reused by k_low; the limiter directions P_ij are stored.
+// work: per-node quantities (primitives, a p^-z, Phi, eta, E + p; in the FP32
+// record of mixed mode also the flux f(U)) are computed once per stage in
+// k_prep and gathered; |c_ij|, 1/|c_ij|, m_ij/m_j and m_ji/m_i are static
+// per-edge arrays; (f(U_j) - f(U_i)) c_ij is computed once per edge in k_visc
+// and reused by k_low; the limiter directions P_ij are stored.
 #include "kernels.cuh"
 
 #include <cooperative_groups.h>
@@ -421,9 +422,9 @@ __device__ __forceinline__ void defer_line_searches(const Work &w, int slot, int
 }
 
 // ---------------------------------------------------------------------------
-// flux f(U) (Sec. 2.1) from the state and the node record's v and p
+// flux f(U) = (m, m v^T + p I, v (E + p)) of one node (Sec. 2.1), row s =
+// component, from its momentum, velocity, pressure and E + p
 // ---------------------------------------------------------------------------
-// f(U) = (m, m v^T + p I, v (E + p)) of one node, row s = component
 template <int DIM, typename T>
 __device__ __forceinline__ void node_flux(const T *mv, const T *v, T pr, T H, T f[DIM + 2][DIM]) {
 #pragma unroll
