@@ -1385,7 +1385,10 @@ eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {
       if ((st = vcopy(c->wk.vd, nnz, buf))) return st;
       std::copy(buf.begin(), buf.end(), host_out);
       return EH_OK;
-    case EH_TRACE_ALPHA: return plain(c->wk.alpha, n);
+    case EH_TRACE_ALPHA:  // stored halved
+      if ((st = plain(c->wk.alpha, n))) return st;
+      for (int64_t i = 0; i < n; ++i) host_out[i] *= 2.0;
+      return EH_OK;
     case EH_TRACE_U_LOW: return aos_to_soa(c->wk.UL, SP, S);
     case EH_TRACE_F_HIGH:
       if (count != S * n) return fail(c, EH_ERR_INVALID_ARG, "count must be %lld", (long long)(S * n));

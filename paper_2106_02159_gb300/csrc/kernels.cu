@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_alpha(MeshView m, Params p, Work w)
     N += a_ - b_;
     D += abs_bits(a_) + abs_bits(b_);
   }
-  w.alpha[i] = D > T(0) ? (double)(fabs(N) / D) : 0.0;
+  w.alpha[i] = D > T(0) ? 0.5 * (double)(fabs(N) / D) : 0.0;  // alpha_i / 2 (exact): d^H_ij = (a_i/2 + a_j/2) d_ij
 }
 
 // ---------------------------------------------------------------------------
@@ -795,7 +795,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
       const T *wk = w_slot<DIM, T>(w, k);
       const T dkT = *d_ptr<DIM, T>(w, k);
       const double dk = (double)dkT;
-      const T dH = T(0.5 * (alphai + w.alpha[j])) * dkT;
+      const T dH = T(alphai + w.alpha[j]) * dkT;  // w.alpha holds alpha / 2
       double w0 = 0.0;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
@@ -965,7 +965,7 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
     const double *Rj = w.rec + (int64_t)j * R::SIZE;
     const T *FHj = FHarr + (int64_t)j * SP;
     const double dk = (double)*d_ptr<DIM, T>(w, k);
-    const double dH = 0.5 * (alphai + w.alpha[j]) * dk;
+    const double dH = (alphai + w.alpha[j]) * dk;  // w.alpha holds alpha / 2
     const double b = m.beta[k], bt = m.betat[k];
     double P[S];
 #pragma unroll

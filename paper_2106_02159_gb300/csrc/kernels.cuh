@@ -113,7 +113,7 @@ struct Params {
 
 struct Work {
   double *rec;     // [n][Rec<DIM>::SIZE]
-  double *alpha;   // [n]
+  double *alpha;   // [n]      alpha_i / 2 (so that d^H_ij = (alpha_i/2 + alpha_j/2) d_ij, exactly as 0.5 (alpha_i + alpha_j) d_ij)
   double *w;       // [nnz][SP]  (f(U_j) - f(U_i)) c_ij
   double *d;       // [nnz]      d^L_ij (diagonal: d_ii)
   double *inc;     // [n][SP]    sum_{j != i} d_ij (U_j - U_i) - w_ij
