@@ -192,13 +192,13 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
 # developed flow); a launch moves about this times nnz. Only valid for the
 # kernels as captured there, and only for the 2D FP64 cylinder workload.
 NCU_DRAM_BYTES_PER_ENTRY_2D_FP64 = {
-    "prep": 5.6, "visc": 180.3, "low": 75.4, "lim1": 121.4, "pass": 86.9, "final": 56.9,
+    "prep": 5.6, "visc": 180.6, "low": 75.5, "lim1": 121.1, "pass": 86.8, "final": 56.9,
 }
 # FP64 pipe activity (sm__pipe_fp64_cycles_active, % of peak) on the same capture:
 # how busy the issue-bound kernels keep the FP64 units (k_visc and k_alpha
 # time-weighted as "visc")
 NCU_FP64_PIPE_ACTIVE_2D_FP64 = {
-    "prep": 0.835, "visc": 0.827, "low": 0.859, "lim1": 0.838, "pass": 0.611, "final": 0.633,
+    "prep": 0.837, "visc": 0.825, "low": 0.862, "lim1": 0.839, "pass": 0.610, "final": 0.630,
 }
 
 
