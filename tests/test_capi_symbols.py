@@ -46,6 +46,12 @@ def test_host_only_calls(lib):
     assert lib.eh_batch_last_error(None) == b"null batch"
     lib.eh_batch_destroy(None)
     assert lib.eh_batch_create(None, 1 << 30, ctypes.byref(out)) == binding.EH_ERR_INVALID_ARG and not out.value
+    ticket, done = ctypes.c_int64(0), ctypes.c_int32(0)
+    assert lib.eh_batch_admit(None, 10, 10, None, None, None, None, None, 0, None, None, None, None, None, 1.0,
+                              ctypes.byref(ticket)) == binding.EH_ERR_INVALID_ARG
+    assert lib.eh_batch_advance(None, 1, None) == binding.EH_ERR_INVALID_ARG
+    assert lib.eh_batch_poll(None, 1, ctypes.byref(done), None, None, None) == binding.EH_ERR_INVALID_ARG
+    assert lib.eh_batch_active(None, None, None) == binding.EH_ERR_INVALID_ARG
     nbytes = ctypes.c_uint64(0)
     assert lib.eh_estimate_device_bytes(2, 0, 1000, 9000, ctypes.byref(nbytes)) == binding.EH_OK
     small = nbytes.value
