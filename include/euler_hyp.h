@@ -107,7 +107,8 @@ eh_status eh_create(const eh_config *cfg, eh_ctx **out);
  *   row_ptr[n+1]  : int64 CSR offsets; col[nnz] int32 columns, sorted and
  *                   unique within a row, diagonal present, pattern symmetric
  *   cij[dim][nnz] : c_ij = int phi_i grad phi_j (component-major)
- *   mij[nnz]      : consistent mass m_ij; mi[n]: lumped mass m_i > 0
+ *   mij[nnz]      : consistent mass m_ij, symmetric (m_ij = m_ji to 1e-12
+ *                   relative, else EH_ERR_BAD_MESH); mi[n]: lumped mass m_i > 0
  *   n_bnd, bnd_node[n_bnd], bnd_kind[n_bnd] (EH_BC_*): every node on the
  *                   boundary, once (nodes not listed are interior)
  *   bnd_normal[dim][n_bnd] : unit normal of the node's kind: n^s_i of eq.

@@ -496,7 +496,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
       tr[k] = (int32_t)(row_ptr[j] + (f - b));
     }
   }
-  std::vector<double> cn(nnz), cinv(nnz), beta(nnz), betat(nnz);
+  std::vector<double> cn(nnz), cinv(nnz), betat(nnz);
   for (int i = 0; i < n; ++i) {
     for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
       double s2 = 0.0;
@@ -504,8 +504,12 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
       cn[k] = std::sqrt(s2);
       cinv[k] = cn[k] > 0.0 ? 1.0 / cn[k] : 0.0;
       if (col[k] != i && !(cn[k] > 0.0)) return fail(c, EH_ERR_BAD_MESH, "c_ij = 0 at an off-diagonal entry");
-      beta[k] = mij[k] / mi[col[k]];
-      betat[k] = mij[tr[k]] / mi[i];
+      // the consistent mass matrix is symmetric (m_ij = int phi_i phi_j);
+      // k_lim1 relies on it, with the mean of the two entries
+      const double a = mij[k], b = mij[tr[k]];
+      if (std::fabs(a - b) > 1e-12 * std::max(std::fabs(a), std::fabs(b)))
+        return fail(c, EH_ERR_BAD_MESH, "consistent mass not symmetric at (%d,%d)", i, col[k]);
+      betat[k] = 0.5 * (a + b) / mi[i];
     }
   }
   std::vector<double> inv_mi(n), relax(n, 0.0), lam(n);
@@ -536,7 +540,7 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   m.n_bnd = n_bnd;
   int64_t *d_row = nullptr;
   int32_t *d_col = nullptr, *d_tr = nullptr, *d_bidx = nullptr, *d_bkind = nullptr;
-  double *d_cij, *d_cn, *d_cinv, *d_beta, *d_betat, *d_mi, *d_imi, *d_relax, *d_lam, *d_bnorm = nullptr,
+  double *d_cij, *d_cn, *d_cinv, *d_betat, *d_mi, *d_imi, *d_relax, *d_lam, *d_bnorm = nullptr,
       *d_bstate = nullptr;
   unsigned char *d_isb;
 #define ALLOC(ptr, cnt) \
@@ -547,7 +551,6 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   ALLOC(d_cij, (size_t)dim * nnz);
   ALLOC(d_cn, nnz);
   ALLOC(d_cinv, nnz);
-  ALLOC(d_beta, nnz);
   ALLOC(d_betat, nnz);
   ALLOC(d_mi, n);
   ALLOC(d_imi, n);
@@ -639,7 +642,6 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   if (e == cudaSuccess) e = up(d_cij, cij, sizeof(double) * dim * nnz);
   if (e == cudaSuccess) e = up(d_cn, cn.data(), sizeof(double) * nnz);
   if (e == cudaSuccess) e = up(d_cinv, cinv.data(), sizeof(double) * nnz);
-  if (e == cudaSuccess) e = up(d_beta, beta.data(), sizeof(double) * nnz);
   if (e == cudaSuccess) e = up(d_betat, betat.data(), sizeof(double) * nnz);
   if (e == cudaSuccess) e = up(d_mi, mi, sizeof(double) * n);
   if (e == cudaSuccess) e = up(d_imi, inv_mi.data(), sizeof(double) * n);
@@ -673,7 +675,6 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   m.cij = d_cij;
   m.cn = d_cn;
   m.cinv = d_cinv;
-  m.beta = d_beta;
   m.betat = d_betat;
   m.mi = d_mi;
   m.inv_mi = d_imi;
@@ -1390,12 +1391,15 @@ eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {
       for (int64_t i = 0; i < n; ++i) host_out[i] *= 2.0;
       return EH_OK;
     case EH_TRACE_U_LOW: return aos_to_soa(c->wk.UL, SP, S);
-    case EH_TRACE_F_HIGH:
+    case EH_TRACE_F_HIGH: {  // stored as F^H_i / m_i
       if (count != S * n) return fail(c, EH_ERR_INVALID_ARG, "count must be %lld", (long long)(S * n));
       if ((st = vcopy(c->wk.vFH, n * SP, buf))) return st;
+      std::vector<double> mi_host(n);
+      CUDA_TRY(c, cudaMemcpy(mi_host.data(), c->mv.mi, sizeof(double) * n, cudaMemcpyDeviceToHost));
       for (int64_t i = 0; i < n; ++i)
-        for (int s = 0; s < S; ++s) host_out[s * n + i] = buf[i * SP + s];
+        for (int s = 0; s < S; ++s) host_out[s * n + i] = buf[i * SP + s] * mi_host[i];
       return EH_OK;
+    }
     case EH_TRACE_BOUNDS: return aos_to_soa(c->wk.bounds, 4, 3);
     case EH_TRACE_L_PASS1:
       if (c->cfg.limiter_passes < 2) return fail(c, EH_ERR_STATE, "L_PASS1 needs limiter_passes >= 2");

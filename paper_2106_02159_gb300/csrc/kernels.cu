@@ -834,11 +834,12 @@ __global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
     *d_ptr<DIM, T>(w, kd) = (T)(-dsum);
     bound = p.cfl * m.mi[i] / (2.0 * dsum);
     double *inci = w.inc + (int64_t)i * SP;
-    T *fhi = (T *)w.vFH + (int64_t)i * SP;
+    T *fhi = (T *)w.vFH + (int64_t)i * SP;  // stored as F^H_i / m_i
+    const T imi = T(m.inv_mi[i]);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       inci[s] = inc[s];
-      fhi[s] = fh[s];
+      fhi[s] = fh[s] * imi;
     }
     const double rmin = dmin == 1.0 ? nmin : nmin / dmin;
     const double rmax = dmax == 1.0 ? nmax : nmax / dmax;
@@ -921,17 +922,17 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
   using R = Rec<DIM>;
   const double tau = w.tau_inst[m.inst ? m.inst[i] : 0];
   const double *Ri = w.rec + (int64_t)i * R::SIZE;
-  double ui[S], ul[S], fhi[S];
+  double ui[S], ul[S], gi[S];
   const double *inci = w.inc + (int64_t)i * SP;
-  const T *FHarr = (const T *)w.vFH;
+  const T *Garr = (const T *)w.vFH;  // G = F^H / m per node
 
-  const T *FHi = FHarr + (int64_t)i * SP;
+  const T *Gi = Garr + (int64_t)i * SP;
   const double tm = tau * m.inv_mi[i];
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     ui[s] = Ri[s];
     ul[s] = ui[s] + tm * inci[s];
-    fhi[s] = (double)FHi[s];
+    gi[s] = (double)Gi[s];
   }
   double *ULi = w.UL + (int64_t)i * SP;
 #pragma unroll
@@ -951,7 +952,12 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
   const double phimin2 = phimin * phimin, phimin5 = phimin2 * phimin2 * phimin;
   const double alphai = w.alpha[i];
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
-  const double coef = tau * (double)(k1 - k0 - 1) * m.inv_mi[i];
+  // P_ij = tau/(m_i lambda_i) (b_ij F^H_j - b_ji F^H_i + (d^H_ij - d_ij)(U_j - U_i))
+  // with b_ij = -m_ij/m_j, b_ji = -m_ji/m_i and m_ij = m_ji:
+  //      = (tc m_ij/m_i) (G_i - G_j) + (tc/m_i) (d^H_ij - d_ij)(U_j - U_i),
+  // G = F^H/m, tc = tau (card I(i) - 1)
+  const double tc = tau * (double)(k1 - k0 - 1);
+  const double coef = tc * m.inv_mi[i];
   uint64_t defer = 0;  // entries whose line search goes to k_ls_deferred
   for (int64_t k = k0; k < k1; ++k) {
     const int j = m.col[k];
@@ -963,14 +969,14 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
       continue;
     }
     const double *Rj = w.rec + (int64_t)j * R::SIZE;
-    const T *FHj = FHarr + (int64_t)j * SP;
+    const T *Gj = Garr + (int64_t)j * SP;
     const double dk = (double)*d_ptr<DIM, T>(w, k);
     const double dH = (alphai + w.alpha[j]) * dk;  // w.alpha holds alpha / 2
-    const double b = m.beta[k], bt = m.betat[k];
+    const double cm = tc * m.betat[k], cd = coef * (dH - dk);
     double P[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      P[s] = coef * (-b * (double)FHj[s] + bt * fhi[s] + (dH - dk) * (Rj[s] - ui[s]));
+      P[s] = cm * (gi[s] - (double)Gj[s]) + cd * (Rj[s] - ui[s]);
       Pk[s] = P[s];
     }
     if (line_search_at_one<DIM>(p, ul, P, rmin, rmax, phimin5))

@@ -76,8 +76,7 @@ struct MeshView {
   const double *cij;         // [dim][nnz]
   const double *cn;          // |c_ij|
   const double *cinv;        // 1/|c_ij|
-  const double *beta;        // m_ij / m_j
-  const double *betat;       // m_ji / m_i
+  const double *betat;       // m_ij / m_i (the consistent mass matrix is symmetric)
   const double *mi;
   const double *inv_mi;
   const double *relax;       // r_i (0 when the bounds are strict)
@@ -117,7 +116,7 @@ struct Work {
   double *w;       // [nnz][SP]  (f(U_j) - f(U_i)) c_ij
   double *d;       // [nnz]      d^L_ij (diagonal: d_ii)
   double *inc;     // [n][SP]    sum_{j != i} d_ij (U_j - U_i) - w_ij
-  double *FH;      // [n][SP]
+  double *FH;      // [n][SP]    F^H_i / m_i
   double *bounds;  // [n][4]     rho_min, rho_max, Phi_min
   double *UL;      // [n][SP]
   double *Ua;      // [n][SP]    limited state, ping
@@ -138,7 +137,7 @@ struct Work {
   void *vw;        // [nnz][EdgeLayout::SPW] w_ij (and, packed, a_ij and d_ij)
   void *vd;        // [nnz]      d_ij (not packed)
   void *va;        // [nnz]      (q(U_j) - q(U_i)) . c_ij of the indicator (not packed)
-  void *vFH;       // [n][SP]
+  void *vFH;       // [n][SP]    F^H_i / m_i
   // line searches that the fast check at l = 1 left open, run by
   // k_ls_deferred after each limiter pass (one queue, reused by every pass)
   int2 *lsq;             // [lsq_cap] (row i, entry k)

@@ -47,6 +47,9 @@ def test_corrupted_mesh_data_is_rejected_on_the_host():
         dataclasses.replace(mesh, mi=np.where(np.arange(mesh.n) == 3, -1.0, mesh.mi)),
         dataclasses.replace(mesh, cij=np.where(np.arange(mesh.nnz) == 5, np.nan, mesh.cij)),
         dataclasses.replace(mesh, col=np.where(np.arange(mesh.nnz) == 7, mesh.n + 4, mesh.col).astype(np.int32)),
+        # the consistent mass matrix must be symmetric (m_ij = int phi_i phi_j);
+        # entry 9 is off the diagonal (row 1, column 2)
+        dataclasses.replace(mesh, mij=np.where(np.arange(mesh.nnz) == 9, mesh.mij * (1.0 + 1e-6), mesh.mij)),
     ]
     for m in bad:
         with pytest.raises(B.EulerError) as e:
