@@ -178,7 +178,7 @@ def algorithmic_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
         # w_ij, a_ij, d_ij written once per entry) + k_alpha (w_ij, a_ij read; alpha written)
         "visc": (8 + rec + 1 + 8 * (S + 4) + 8, 4 + (4 + 8 * dim + 16) / 2 + 8 * S + 16 + 4 + 8 * S + 8),
         "low": (8 + 8 * (S + 1) + 8 * 3 + 8 * SP * 2 + 8 * 4, 4 + 8 + 8 * S),
-        "lim1": (8 + 8 * S + 8 * SP * 2 + 8 + 8 * 4 + 8 + 8 * SP, 4 + 8 * 3 + 8 * SP + 8),
+        "lim1": (8 + 8 * S + 8 * SP * 2 + 8 + 8 * 4 + 8 + 8 * SP, 4 + 8 * 2 + 8 * SP + 8),
         "pass": (8 + 8 * SP * 2 + 8 * 4, 4 + 4 + 8 + 8 * SP * 2 + 8),
         "final": (8 + 8 * SP + 8 * S * 2 + 4, 4 + 4 + 8 + 8 * SP),
         "tau": (0, 0),
