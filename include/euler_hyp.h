@@ -43,9 +43,6 @@ typedef enum {
   EH_ERR_STATE = 7            /* called out of order (e.g. eh_step before a mesh and a state) */
 } eh_status;
 
-/* Boundary kinds (Sec. 4): slip (eq. slip_bc), supersonic inflow = Dirichlet
- * state (eq. Supersonic_inflow), supersonic outflow = do nothing
- * (eq. Supersonic_outflow). */
 /* Boundary kinds (Sec. 4): slip (eq. slip_bc), Dirichlet / supersonic inflow
  * (eq. Supersonic_inflow), do nothing (supersonic outflow, eq.
  * Supersonic_outflow), and the two non-reflecting post-processings of
@@ -216,19 +213,33 @@ eh_status eh_get_diagnostics(eh_ctx *ctx, eh_diagnostics *out);
 /* Intermediate arrays of the last forward-Euler stage, for checking against
  * a reference (synchronises). 'what' selects one of EH_TRACE_*; host_out must
  * hold 'count' doubles, which must equal the array's size:
- *   D_IJ [nnz] graph viscosity d^L_ij (diagonal included)
- *   ALPHA [n] indicator alpha_i
- *   U_LOW [S][n] low-order update U^L
- *   F_HIGH [S][n] high-order fluxes F^H_i
- *   BOUNDS [3][n] rho_min, rho_max, Phi_min
- *   L_PASS1 [nnz] symmetrised limiter of the first pass (1 on the diagonal)
+ *   D_IJ [nnz] graph viscosity d^L_ij (diagonal included; Sec. 3.1)
+ *   ALPHA [n] indicator alpha_i (Sec. 3.2)
+ *   U_LOW [S][n] low-order update U^L (eq. loworder_bis)
+ *   F_HIGH [S][n] high-order fluxes F^H_i (Algorithm 1, step 3)
+ *   BOUNDS [3][n] rho_min, rho_max, Phi_min (Sec. 3.3)
+ *   L_PASS1 [nnz] symmetrised limiter l_ij = min(l_j^i, l_i^j) of the first
+ *     pass (1 on the diagonal; Sec. 3.3)
  *   U_PASS1 [S][n] state after the first limiting pass
- *   TAU [1] the stage's tau; TAU_BOUND [1] its own CFL bound */
+ *   TAU [1] the stage's tau; TAU_BOUND [1] its own CFL bound
+ *   P_PASS1 [S][nnz] limiter directions P_ij of the first pass (eq.
+ *     LambdaArrangement; 0 on the diagonal)
+ *   L_LAST [nnz] symmetrised limiter of the last pass (1 on the diagonal)
+ * The trace buffers are allocated by the first eh_stage call of a mesh. */
 enum {
   EH_TRACE_D_IJ = 0, EH_TRACE_ALPHA = 1, EH_TRACE_U_LOW = 2, EH_TRACE_F_HIGH = 3, EH_TRACE_BOUNDS = 4,
-  EH_TRACE_L_PASS1 = 5, EH_TRACE_U_PASS1 = 6, EH_TRACE_TAU = 7, EH_TRACE_TAU_BOUND = 8
+  EH_TRACE_L_PASS1 = 5, EH_TRACE_U_PASS1 = 6, EH_TRACE_TAU = 7, EH_TRACE_TAU_BOUND = 8, EH_TRACE_P_PASS1 = 9,
+  EH_TRACE_L_LAST = 10
 };
 eh_status eh_trace(eh_ctx *ctx, int what, double *host_out, int64_t count);
+
+/* The integer mesh data as the device holds it (synchronises; host arrays,
+ * any may be NULL): row_ptr[n+1] and col[nnz] as uploaded, and transpose[nnz],
+ * the position of entry (j, i) for every entry (i, j), built by
+ * eh_upload_mesh -- the index through which the symmetric edge quantities
+ * (d_ij, Sec. 3.1; l_ij, Sec. 3.3) are written once and mirrored.
+ * EH_ERR_STATE without a mesh. */
+eh_status eh_get_mesh_index(eh_ctx *ctx, int64_t *row_ptr, int32_t *col, int32_t *transpose);
 
 /* Per-kernel timing with CUDA events on the context's stream, for profiling.
  * While enabled, eh_step/eh_stage/eh_run launch eagerly (no graph) and record
@@ -258,14 +269,21 @@ eh_status eh_profile_read(eh_ctx *ctx, int kernel, double *total_ms, int64_t *la
  *     diagonal present, symmetric pattern -- not checked here);
  *   cij[dim][nnz], mi[n]; is_boundary[n] (1 for boundary nodes) or NULL when
  *     no node lies on the boundary; U[dim+2][n] an admissible state;
- *   dt_out: device pointer to one double, written by the last kernel.
+ *   dt_out: device pointer to one double, written by the last kernel. It
+ *     receives NaN when a row's state is not admissible (rho <= 0 or
+ *     internal energy <= 0 give an undefined wave speed): the reduction keeps
+ *     NaN rather than dropping the row, so check the value for NaN.
  * Work is queued on 'stream' (a cudaStream_t, NULL for the default stream) of
- * the current device; the call does not synchronise.
+ * the current device; the call does not synchronise. Returns EH_ERR_CUDA,
+ * without launching, if a CUDA error from earlier work is pending (it is left
+ * in place for the caller to read), and EH_ERR_CUDA if a launch fails.
  * Scratch: a file-scope device array of EH_CFL_NOALLOC_MAX_ROWS / 128 doubles
  * (512 KiB) that every GPU loading the library keeps until the process ends;
  * n above EH_CFL_NOALLOC_MAX_ROWS returns EH_ERR_INVALID_ARG before any work.
- * The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The first call in each CUDA context of a device looks the array's device
+ * address up (cudaGetSymbolAddress, which allocates nothing) and caches it
+ * under the context's id, so a device reset or a new context is handled; make
+ * that first call before any stream capture.
  * Every call overwrites the entries it reads, so nothing needs clearing, but
  * all calls share the array: two calls whose kernels overlap on the GPU (on
  * different streams without ordering) race and give wrong results.

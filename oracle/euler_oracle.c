@@ -35,7 +35,7 @@
  *    keeps positivity and lets smooth extrema converge at second order.
  *  - the line search for l_j^i: density by a closed-form ratio, the entropy
  *    bound psi(l) = eps(U + lP) - Phi_min rho(U + lP)^gamma (concave in l) by
- *    four fixed secant(left)/Newton(right) bracketing iterations.
+ *    six fixed secant(left)/Newton(right) bracketing iterations.
  *  - d_ij takes the max of both directions only when i and j are both
  *    boundary nodes (c_ji = -c_ij exactly whenever one of them is interior).
  *  - every limiter pass is symmetrised, l_ij = min(l_j^i, l_i^j).

@@ -27,12 +27,12 @@ EH_ERR_NOT_ADMISSIBLE, EH_ERR_CFL, EH_ERR_CUDA, EH_ERR_STATE = 4, 5, 6, 7
 EH_BC_SLIP, EH_BC_DIRICHLET, EH_BC_DO_NOTHING, EH_BC_CHARACTERISTIC, EH_BC_GODUNOV = 1, 2, 3, 4, 5
 EH_PRECISION_FP64, EH_PRECISION_MIXED = 0, 1
 (EH_TRACE_D_IJ, EH_TRACE_ALPHA, EH_TRACE_U_LOW, EH_TRACE_F_HIGH, EH_TRACE_BOUNDS, EH_TRACE_L_PASS1,
- EH_TRACE_U_PASS1, EH_TRACE_TAU, EH_TRACE_TAU_BOUND) = range(9)
+ EH_TRACE_U_PASS1, EH_TRACE_TAU, EH_TRACE_TAU_BOUND, EH_TRACE_P_PASS1, EH_TRACE_L_LAST) = range(11)
 
 # every symbol the header declares
 EXPORTS = ("eh_config_default", "eh_create", "eh_upload_mesh", "eh_set_state", "eh_get_state",
            "eh_apply_boundary_conditions", "eh_cfl_dt", "eh_stage", "eh_step", "eh_run", "eh_synchronize",
-           "eh_get_diagnostics", "eh_trace", "eh_profile_enable", "eh_profile_read", "eh_launches_per_step",
+           "eh_get_diagnostics", "eh_trace", "eh_get_mesh_index", "eh_profile_enable", "eh_profile_read", "eh_launches_per_step",
            "eh_last_error", "eh_status_string", "eh_destroy", "eh_cfl_dt_noalloc", "eh_set_instances",
            "eh_get_instances", "eh_autotune", "eh_get_block_sizes", "eh_get_rows_per_sm", "eh_set_launch_shape",
            "eh_step_adaptive", "eh_set_viscosity", "eh_parabolic_step", "eh_step_ns",
@@ -104,6 +104,7 @@ def load(path: str | None = None):
     lib.eh_synchronize.argtypes = [vp]
     lib.eh_get_diagnostics.argtypes = [vp, ctypes.POINTER(Diagnostics)]
     lib.eh_trace.argtypes = [vp, ctypes.c_int, dp, i64]
+    lib.eh_get_mesh_index.argtypes = [vp, vp, vp, vp]
     lib.eh_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.eh_profile_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(i64)]
     lib.eh_launches_per_step.argtypes = [vp]
@@ -400,7 +401,8 @@ class Solver:
     def trace(self, what):
         sizes = {EH_TRACE_D_IJ: self.nnz, EH_TRACE_ALPHA: self.n, EH_TRACE_U_LOW: self.S * self.n,
                  EH_TRACE_F_HIGH: self.S * self.n, EH_TRACE_BOUNDS: 3 * self.n, EH_TRACE_L_PASS1: self.nnz,
-                 EH_TRACE_U_PASS1: self.S * self.n, EH_TRACE_TAU: 1, EH_TRACE_TAU_BOUND: 1}
+                 EH_TRACE_U_PASS1: self.S * self.n, EH_TRACE_TAU: 1, EH_TRACE_TAU_BOUND: 1,
+                 EH_TRACE_P_PASS1: self.S * self.nnz, EH_TRACE_L_LAST: self.nnz}
         count = sizes[what]
         out = np.empty(count)
         self._check(self.lib.eh_trace(self.ctx, what, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), count),
@@ -409,9 +411,21 @@ class Solver:
             return out.reshape(self.S, self.n)
         if what == EH_TRACE_BOUNDS:
             return out.reshape(3, self.n)
+        if what == EH_TRACE_P_PASS1:
+            return out.reshape(self.S, self.nnz)
         if what in (EH_TRACE_TAU, EH_TRACE_TAU_BOUND):
             return float(out[0])
         return out
+
+    def mesh_index(self):
+        """(row_ptr, col, transpose) as the device holds them (eh_get_mesh_index)."""
+        row_ptr = np.empty(self.n + 1, dtype=np.int64)
+        col = np.empty(self.nnz, dtype=np.int32)
+        tr = np.empty(self.nnz, dtype=np.int32)
+        self._check(self.lib.eh_get_mesh_index(self.ctx, row_ptr.ctypes.data_as(ctypes.c_void_p),
+                                               col.ctypes.data_as(ctypes.c_void_p),
+                                               tr.ctypes.data_as(ctypes.c_void_p)), "eh_get_mesh_index")
+        return row_ptr, col, tr
 
     def profile(self, enable: bool):
         self._check(self.lib.eh_profile_enable(self.ctx, int(bool(enable))), "eh_profile_enable")

@@ -34,7 +34,11 @@ struct eh_ctx {
   Work wk{};
   // state [S][n], stage state, trace buffers
   double *U = nullptr, *W = nullptr;
-  double *trace_lsym = nullptr, *trace_upass = nullptr, *trace_pre = nullptr;
+  // trace buffers, allocated by the first eh_stage: symmetrised limiter of
+  // the first and of the last pass, state after the first pass, state before
+  // the post-processing, P_ij of the first pass ([nnz][SP])
+  double *trace_lsym = nullptr, *trace_upass = nullptr, *trace_pre = nullptr, *trace_llast = nullptr,
+         *trace_P = nullptr;
   DevStatus *st = nullptr;
   DevStatus *st_host = nullptr;  // pinned
   // host bookkeeping
@@ -135,7 +139,7 @@ void free_mesh(eh_ctx *c) {
   c->mv = MeshView{};
   c->wk = Work{};
   c->U = c->W = nullptr;
-  c->trace_lsym = c->trace_upass = c->trace_pre = nullptr;
+  c->trace_lsym = c->trace_upass = c->trace_pre = c->trace_llast = c->trace_P = nullptr;
   c->have_mesh = c->have_state = false;
 }
 
@@ -222,7 +226,7 @@ void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, con
   { ProfScope ps(c, EH_KERNEL_TAU); launch_tau(m, w, stage, dt_given, p.cfl, !trace, s); }
   {
     ProfScope ps(c, EH_KERNEL_LIM1);
-    launch_lim1<DIM, T>(m, p, w, tpb[EH_KERNEL_LIM1], max_blocks(c, EH_KERNEL_LIM1), s);
+    launch_lim1<DIM, T>(m, p, w, trace ? c->trace_P : nullptr, tpb[EH_KERNEL_LIM1], max_blocks(c, EH_KERNEL_LIM1), s);
   }
   { ProfScope ps(c, EH_KERNEL_LSEARCH); launch_ls_deferred<DIM>(m, p, w, w.UL, 0, w.la, tpb[EH_KERNEL_LSEARCH], s); }
   const double *ucur = w.UL;
@@ -247,7 +251,8 @@ void enqueue_stage(eh_ctx *c, const double *Uin, int stage, double dt_given, con
   }
   {
     ProfScope ps(c, EH_KERNEL_FINAL);
-    launch_final<DIM>(m, p, w, ucur, lcur, U0, coef, out, trace ? c->trace_pre : nullptr, tpb[EH_KERNEL_FINAL],
+    launch_final<DIM>(m, p, w, ucur, lcur, U0, coef, out, trace ? c->trace_pre : nullptr,
+                      trace ? c->trace_llast : nullptr, tpb[EH_KERNEL_FINAL],
                       max_blocks(c, EH_KERNEL_FINAL), s);
   }
 }
@@ -324,6 +329,19 @@ eh_status setup_instances(eh_ctx *c, int ninst, const int64_t *off, const double
     if ((st = ialloc(&p_inst, sizeof(int32_t) * c->n))) return st;
     CUDA_TRY(c, cudaMemcpy(p_inst, inst.data(), sizeof(int32_t) * c->n, cudaMemcpyHostToDevice));
   }
+  if (c->cfg.bound_relaxation) {
+    // r_i = (m_i / |D|)^(1.5/dim) with |D| the measure of the node's own
+    // instance, not of the whole block-diagonal mesh
+    const int n = c->n, dim = c->cfg.dim;
+    std::vector<double> mi(n), relax(n);
+    CUDA_TRY(c, cudaMemcpy(mi.data(), c->mv.mi, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < ninst; ++k) {
+      double area = 0.0;
+      for (int64_t i = off[k]; i < off[k + 1]; ++i) area += mi[i];
+      for (int64_t i = off[k]; i < off[k + 1]; ++i) relax[i] = std::pow(mi[i] / area, 1.5 / dim);
+    }
+    CUDA_TRY(c, cudaMemcpy((void *)c->mv.relax, relax.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+  }
   c->ninst = ninst;
   c->mv.ninst = ninst;
   c->mv.inst = (const int32_t *)p_inst;
@@ -353,6 +371,19 @@ eh_status require_ready(eh_ctx *c) {
   if (!c->have_mesh) return fail(c, EH_ERR_STATE, "no mesh uploaded");
   if (!c->have_state) return fail(c, EH_ERR_STATE, "no state set");
   return EH_OK;
+}
+
+// the trace buffers of eh_stage, allocated on first use (they are freed with
+// the mesh)
+eh_status ensure_trace_buffers(eh_ctx *c) {
+  if (c->trace_P) return EH_OK;
+  const int SP = SP_of(c);
+  eh_status st;
+  if ((st = dalloc(c, &c->trace_lsym, (size_t)c->nnz))) return st;
+  if ((st = dalloc(c, &c->trace_llast, (size_t)c->nnz))) return st;
+  if ((st = dalloc(c, &c->trace_upass, (size_t)c->n * SP))) return st;
+  if ((st = dalloc(c, &c->trace_pre, (size_t)c->n * SP))) return st;
+  return dalloc(c, &c->trace_P, (size_t)c->nnz * SP);
 }
 
 eh_status reset_status(eh_ctx *c) {
@@ -569,6 +600,8 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   ALLOC(c->stat_part, (size_t)7 * STAT_BLOCKS);
   ALLOC(c->stat_out, 8);
   ALLOC(w.alpha, n);
+  ALLOC(w.rough, n);
+  ALLOC(w.rough2, n);
   ALLOC(w.inc, (size_t)n * SP);
   float *f_cij = nullptr, *f_cn = nullptr, *f_cinv = nullptr;
   if (c->cfg.precision == EH_PRECISION_MIXED) {
@@ -626,9 +659,6 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   ALLOC(c->Usave, (size_t)S * n);
   ALLOC(c->U, (size_t)S * n);
   ALLOC(c->W, (size_t)S * n);
-  ALLOC(c->trace_lsym, nnz);
-  ALLOC(c->trace_upass, (size_t)n * SP);
-  ALLOC(c->trace_pre, (size_t)n * SP);
 #undef ALLOC
   w.st = c->st;
   auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
@@ -770,6 +800,7 @@ eh_status eh_stage(eh_ctx *c, double tau, double *tau_used) {
   if (st) return st;
   CUDA_TRY(c, cudaSetDevice(c->device));
   if ((st = check_device_error(c))) return st;
+  if ((st = ensure_trace_buffers(c))) return st;
   enqueue_stage_any(c, tau);
   CUDA_TRY(c, cudaGetLastError());
   c->last_stage_traced = true;
@@ -1339,6 +1370,18 @@ int32_t eh_launches_per_step(const eh_ctx *c) {
   return 3 * (7 + (c->cfg.limiter_passes - 1) + 2 * c->cfg.limiter_passes + (c->mv.n_nonreflecting > 0 ? 1 : 0));
 }
 
+eh_status eh_get_mesh_index(eh_ctx *c, int64_t *row_ptr, int32_t *col, int32_t *transpose) {
+  if (!c) return EH_ERR_INVALID_ARG;
+  if (!c->have_mesh) return fail(c, EH_ERR_STATE, "no mesh uploaded");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (row_ptr)
+    CUDA_TRY(c, cudaMemcpy(row_ptr, c->mv.row_ptr, sizeof(int64_t) * (c->n + 1), cudaMemcpyDeviceToHost));
+  if (col) CUDA_TRY(c, cudaMemcpy(col, c->mv.col, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToHost));
+  if (transpose) CUDA_TRY(c, cudaMemcpy(transpose, c->mv.tr, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToHost));
+  return EH_OK;
+}
+
 eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {
   eh_status st = require_ready(c);
   if (st) return st;
@@ -1406,6 +1449,15 @@ eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {
       return plain(c->trace_lsym, nnz);
     case EH_TRACE_U_PASS1:
       return aos_to_soa(c->cfg.limiter_passes >= 2 ? c->trace_upass : c->trace_pre, SP, S);
+    case EH_TRACE_P_PASS1: {
+      if (count != S * nnz) return fail(c, EH_ERR_INVALID_ARG, "count must be %lld", (long long)(S * nnz));
+      std::vector<double> tmp((size_t)nnz * SP);
+      CUDA_TRY(c, cudaMemcpy(tmp.data(), c->trace_P, sizeof(double) * nnz * SP, cudaMemcpyDeviceToHost));
+      for (int64_t k = 0; k < nnz; ++k)
+        for (int s = 0; s < S; ++s) host_out[s * nnz + k] = tmp[k * SP + s];
+      return EH_OK;
+    }
+    case EH_TRACE_L_LAST: return plain(c->trace_llast, nnz);
     case EH_TRACE_TAU:
       if (count != 1) return EH_ERR_INVALID_ARG;
       host_out[0] = c->st_host->tau;

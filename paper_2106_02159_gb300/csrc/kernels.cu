@@ -98,6 +98,24 @@ template <int S> __device__ __forceinline__ void store_slot(float *p, const floa
   q[1] = make_float4(v[4], v[5], v[6], v[7]);
 }
 
+// the entry k of an edge between equal states: w = 0, a = 0, and d
+template <int DIM, typename T> __device__ __forceinline__ void store_zero_edge(const Work &w, int64_t k, T d) {
+  constexpr int S = DIM + 2;
+  if constexpr (!EdgeLayout<DIM, T>::packed) {
+    store_sector((double *)w_slot<DIM, T>(w, k), 0.0, 0.0, 0.0, 0.0);
+    *a_ptr<DIM, T>(w, k) = T(0);
+    *d_ptr<DIM, T>(w, k) = d;
+  } else if constexpr (sizeof(T) == 8) {  // FP64 3D: two sectors [w0..w3], [w4, a, d, 0]
+    store_sector((double *)w_slot<DIM, T>(w, k), 0.0, 0.0, 0.0, 0.0);
+    store_sector((double *)w_slot<DIM, T>(w, k) + 4, 0.0, 0.0, (double)d, 0.0);
+  } else {
+    T z[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) z[s] = T(0);
+    store_slot<S>(w_slot<DIM, T>(w, k), z, T(0), d);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // roots and powers for gamma = 7/5 (division-free Newton iterations from an
 // FP32 seed; two steps take the ~2^-21 seed error below double rounding)
@@ -442,11 +460,13 @@ __device__ __forceinline__ void node_flux(const T *mv, const T *v, T pr, T H, T 
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB_MAX) k_prep(MeshView m, Params p, const double *__restrict__ U,
-                                              double *__restrict__ rec, T *__restrict__ vrec, const DevStatus *st) {
+                                              double *__restrict__ rec, T *__restrict__ vrec,
+                                              unsigned char *__restrict__ rough, const DevStatus *st) {
   constexpr int S = DIM + 2;
   using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || st->err) return;
+  rough[i] = 0;  // set by k_visc where a neighbour's state differs
   double u[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) u[s] = U[(int64_t)s * m.n + i];
@@ -542,12 +562,48 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
     for (int q = 0; q < DIM; ++q) qi[q] = vi[q] * etai;
   }
   const bool bi = m.isb[i] != 0;
+  // the FP64 state of node i as bit patterns (the identical-state test below
+  // compares FP64 bits in either precision)
+  long long ubi[S];
+  {
+    const double *Ri64 = w.rec + (int64_t)i * R::SIZE;
+#pragma unroll
+    for (int s = 0; s < S; ++s) ubi[s] = dbits(Ri64[s]);
+  }
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
   for (int64_t k = k0; k < k1; ++k) {
     const int j = m.col[k];
     if (j <= i) continue;  // each unique edge once, from the row of min(i, j)
     const T *Rj = rec + (int64_t)j * RS;
     const int32_t kt = m.tr[k];
+    {
+      // U_j = U_i bit for bit: the flux and entropy-flux differences vanish,
+      // w_ij = a_ij = 0 exactly, and the two-rarefaction bound of Sec. 3.1
+      // reduces to lambda_max = |v.n_ij| + a (p_tr = p, both outer waves
+      // rarefactions), so d_ij = |v.c_ij| + a |c_ij| with no division, power
+      // or root. Any other edge marks both of its nodes rough.
+      const double *Rj64 = w.rec + (int64_t)j * R::SIZE;
+      bool same = true;
+#pragma unroll
+      for (int s = 0; s < S; ++s) same &= dbits(Rj64[s]) == ubi[s];
+      if (same) {
+        T vc = T(0);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) vc += vi[q] * cij[(int64_t)q * m.nnz + k];
+        T dij = abs_bits(vc) + ai * cn[k];
+        if (bi && m.isb[j]) {  // c_ji != -c_ij: the max over both directions
+          T vct = T(0);
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) vct += vi[q] * cij[(int64_t)q * m.nnz + kt];
+          dij = max_nonneg(dij, abs_bits(vct) + ai * cn[kt]);
+        }
+        store_zero_edge<DIM, T>(w, k, dij);
+        store_zero_edge<DIM, T>(w, kt, dij);
+        continue;
+      }
+      w.rough[i] = 1;
+      w.rough[j] = 1;
+    }
     T vj[DIM], mj[DIM], c[DIM];
     const T pj = Rj[R::P], etaj = Rj[R::ETA], Hj = Rj[R::H];
 #pragma unroll
@@ -719,6 +775,10 @@ __global__ void __launch_bounds__(TPB_MAX) k_alpha(MeshView m, Params p, Work w)
   using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || w.st->err) return;
+  if (!w.rough[i]) {  // every w_ij and a_ij of the row is 0: N_i = D_i = 0
+    w.alpha[i] = 0.0;
+    return;
+  }
   const T *Ri = (const T *)w.vrec + (int64_t)i * vrec_stride<DIM, T>();
   // eta'(U_i)
   T deta[S];
@@ -751,104 +811,152 @@ __global__ void __launch_bounds__(TPB_MAX) k_alpha(MeshView m, Params p, Work w)
   w.alpha[i] = D > T(0) ? 0.5 * (double)(fabs(N) / D) : 0.0;  // alpha_i / 2 (exact): d^H_ij = (a_i/2 + a_j/2) d_ij
 }
 
+// Algorithm 1 steps 2-3 for one row; returns the row's CFL bound
+// c_cfl m_i / (2 sum_{j != i} d_ij)
+template <int DIM, typename T>
+__device__ __forceinline__ double low_row(const MeshView &m, const Params &p, const Work &w, int i) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  using R = Rec<DIM>;
+  const double *Ri = w.rec + (int64_t)i * R::SIZE;
+  double ui[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) ui[s] = Ri[s];
+  const double alphai = w.alpha[i];
+
+  // U^L increment and the bounds in FP64; F^H in the viscosity precision T
+  double inc[S], wsum[S];  // U^L increment in FP64 (also in mixed mode)
+  T fh[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    inc[s] = 0.0;
+    wsum[s] = 0.0;
+    fh[s] = T(0);
+  }
+  // bar-state densities rho_bar = num / den, den = 2 d_ij > 0; the running
+  // minimum / maximum is kept as a fraction and compared by cross-multiplication
+  double nmin = ui[0], dmin = 1.0, nmax = ui[0], dmax = 1.0;
+  double phimin = Ri[R::PHI], dsum = 0.0;
+  int64_t kd = -1;
+  const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
+  for (int64_t k = k0; k < k1; ++k) {
+    const int j = m.col[k];
+    if (j == i) {
+      kd = k;
+      continue;
+    }
+    const double *Rj = w.rec + (int64_t)j * R::SIZE;
+    const T *wk = w_slot<DIM, T>(w, k);
+    const T dkT = *d_ptr<DIM, T>(w, k);
+    const double dk = (double)dkT;
+    const T dH = T(alphai + w.alpha[j]) * dkT;  // w.alpha holds alpha / 2
+    double w0 = 0.0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const T wsT = wk[s];
+      const double ws = (double)wsT;
+      if (s == 0) w0 = ws;
+      const double du = Rj[s] - ui[s];
+      inc[s] += dk * du;  // sum_j d_ij (U_j - U_i); the sum of w_ij is subtracted once
+      fh[s] += dH * (T)du;
+      wsum[s] += ws;
+    }
+    if (dbits(dk) > 0) {  // dk >= 0
+      const double num = dk * (ui[0] + Rj[0]) - w0;
+      const double den = 2.0 * dk;
+      const long long knew_min = order_key(num * dmin), kmin = order_key(nmin * den);
+      const long long knew_max = order_key(num * dmax), kmax = order_key(nmax * den);
+      if (knew_min < kmin) {
+        nmin = num;
+        dmin = den;
+      }
+      if (knew_max > kmax) {
+        nmax = num;
+        dmax = den;
+      }
+    }
+    // Phi > 0: the integer order of the bit patterns is the numeric order
+    const long long pj = __double_as_longlong(Rj[R::PHI]), pm = __double_as_longlong(phimin);
+    phimin = __longlong_as_double(pj < pm ? pj : pm);
+    dsum += dk;
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    inc[s] -= wsum[s];
+    fh[s] -= (T)wsum[s];
+  }
+  *d_ptr<DIM, T>(w, kd) = (T)(-dsum);
+  double *inci = w.inc + (int64_t)i * SP;
+  T *fhi = (T *)w.vFH + (int64_t)i * SP;  // stored as F^H_i / m_i
+  const T imi = T(m.inv_mi[i]);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    inci[s] = inc[s];
+    fhi[s] = fh[s] * imi;
+  }
+  const double rmin = dmin == 1.0 ? nmin : nmin / dmin;
+  const double rmax = dmax == 1.0 ? nmax : nmax / dmax;
+  const double r = m.relax[i];
+  double *bi = w.bounds + (int64_t)i * 4;
+  bi[0] = (1.0 - r) * rmin;
+  bi[1] = (1.0 + r) * rmax;
+  bi[2] = (1.0 - r) * phimin;
+  w.rough2[i] = 1;
+  return p.cfl * m.mi[i] / (2.0 * dsum);
+}
+
+// The same for a row whose neighbours all carry U_i bit for bit (rough[i] =
+// 0): every w_ij is 0 and U_j - U_i = 0, so the increment and F^H vanish,
+// every bar state is U_i (rho_min = rho_max = rho_i) and Phi_min = Phi_i --
+// the values the general row gives, bit for bit. Only sum_j d_ij remains
+// (same order). rough2[i] records whether a neighbour is rough.
+template <int DIM, typename T>
+__device__ __forceinline__ double low_row_smooth(const MeshView &m, const Params &p, const Work &w, int i) {
+  constexpr int S = DIM + 2;
+  constexpr int SP = Layout<DIM>::SP;
+  using R = Rec<DIM>;
+  double dsum = 0.0;
+  int64_t kd = -1;
+  unsigned char r2 = 0;
+  const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
+  for (int64_t k = k0; k < k1; ++k) {
+    const int j = m.col[k];
+    if (j == i) {
+      kd = k;
+      continue;
+    }
+    dsum += (double)*d_ptr<DIM, T>(w, k);
+    r2 |= w.rough[j];
+  }
+  *d_ptr<DIM, T>(w, kd) = (T)(-dsum);
+  double *inci = w.inc + (int64_t)i * SP;
+  T *fhi = (T *)w.vFH + (int64_t)i * SP;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    inci[s] = 0.0;
+    fhi[s] = T(0);
+  }
+  const double *Ri = w.rec + (int64_t)i * R::SIZE;
+  const double rho = Ri[0];
+  const double r = m.relax[i];
+  double *bi = w.bounds + (int64_t)i * 4;
+  bi[0] = (1.0 - r) * rho;
+  bi[1] = (1.0 + r) * rho;
+  bi[2] = (1.0 - r) * Ri[R::PHI];
+  w.rough2[i] = r2;
+  return p.cfl * m.mi[i] / (2.0 * dsum);
+}
+
 // ---------------------------------------------------------------------------
 // k_low: Algorithm 1 steps 2-3 -- d_ii, CFL bound, low-order increment, local
 // bounds and high-order fluxes
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB_MAX) k_low(MeshView m, Params p, Work w) {
-  constexpr int S = DIM + 2;
-  constexpr int SP = Layout<DIM>::SP;
-  using R = Rec<DIM>;
   __shared__ double smin[TPB_MAX / 32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double bound = INFINITY;
-  if (i < m.n && !w.st->err) {
-    const double *Ri = w.rec + (int64_t)i * R::SIZE;
-    double ui[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) ui[s] = Ri[s];
-    const double alphai = w.alpha[i];
-
-    // U^L increment and the bounds in FP64; F^H in the viscosity precision T
-    double inc[S], wsum[S];  // U^L increment in FP64 (also in mixed mode)
-    T fh[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      inc[s] = 0.0;
-      wsum[s] = 0.0;
-      fh[s] = T(0);
-    }
-    // bar-state densities rho_bar = num / den, den = 2 d_ij > 0; the running
-    // minimum / maximum is kept as a fraction and compared by cross-multiplication
-    double nmin = ui[0], dmin = 1.0, nmax = ui[0], dmax = 1.0;
-    double phimin = Ri[R::PHI], dsum = 0.0;
-    int64_t kd = -1;
-    const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
-    for (int64_t k = k0; k < k1; ++k) {
-      const int j = m.col[k];
-      if (j == i) {
-        kd = k;
-        continue;
-      }
-      const double *Rj = w.rec + (int64_t)j * R::SIZE;
-      const T *wk = w_slot<DIM, T>(w, k);
-      const T dkT = *d_ptr<DIM, T>(w, k);
-      const double dk = (double)dkT;
-      const T dH = T(alphai + w.alpha[j]) * dkT;  // w.alpha holds alpha / 2
-      double w0 = 0.0;
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const T wsT = wk[s];
-        const double ws = (double)wsT;
-        if (s == 0) w0 = ws;
-        const double du = Rj[s] - ui[s];
-        inc[s] += dk * du;  // sum_j d_ij (U_j - U_i); the sum of w_ij is subtracted once
-        fh[s] += dH * (T)du;
-        wsum[s] += ws;
-      }
-      if (dbits(dk) > 0) {  // dk >= 0
-        const double num = dk * (ui[0] + Rj[0]) - w0;
-        const double den = 2.0 * dk;
-        const long long knew_min = order_key(num * dmin), kmin = order_key(nmin * den);
-        const long long knew_max = order_key(num * dmax), kmax = order_key(nmax * den);
-        if (knew_min < kmin) {
-          nmin = num;
-          dmin = den;
-        }
-        if (knew_max > kmax) {
-          nmax = num;
-          dmax = den;
-        }
-      }
-      // Phi > 0: the integer order of the bit patterns is the numeric order
-      const long long pj = __double_as_longlong(Rj[R::PHI]), pm = __double_as_longlong(phimin);
-      phimin = __longlong_as_double(pj < pm ? pj : pm);
-      dsum += dk;
-    }
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      inc[s] -= wsum[s];
-      fh[s] -= (T)wsum[s];
-    }
-    *d_ptr<DIM, T>(w, kd) = (T)(-dsum);
-    bound = p.cfl * m.mi[i] / (2.0 * dsum);
-    double *inci = w.inc + (int64_t)i * SP;
-    T *fhi = (T *)w.vFH + (int64_t)i * SP;  // stored as F^H_i / m_i
-    const T imi = T(m.inv_mi[i]);
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      inci[s] = inc[s];
-      fhi[s] = fh[s] * imi;
-    }
-    const double rmin = dmin == 1.0 ? nmin : nmin / dmin;
-    const double rmax = dmax == 1.0 ? nmax : nmax / dmax;
-    const double r = m.relax[i];
-    double *bi = w.bounds + (int64_t)i * 4;
-    bi[0] = (1.0 - r) * rmin;
-    bi[1] = (1.0 + r) * rmax;
-    bi[2] = (1.0 - r) * phimin;
-  }
+  if (i < m.n && !w.st->err) bound = w.rough[i] ? low_row<DIM, T>(m, p, w, i) : low_row_smooth<DIM, T>(m, p, w, i);
   // per-instance minimum of the CFL bound (exact and order independent: the
   // bit patterns of positive doubles order like their values). A block whose
   // rows lie in one instance reduces first and issues one atomic.
@@ -916,10 +1024,28 @@ __global__ void __launch_bounds__(256) k_tau(MeshView m, Work w, int stage, doub
 // k_lim1: Algorithm 1 step 4 -- U^L, P_ij and the first line search
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
-__device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, const Work &w, int i) {
+__device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, const Work &w, double *P_trace, int i) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
   using R = Rec<DIM>;
+  if (!w.rough2[i]) {
+    // row and neighbours without a differing neighbour state: the increment
+    // is 0 (U^L = U_i) and every P_ij = (tc m_ij/m_i)(0 - 0) + (.)(U_j - U_i)
+    // is 0, so every search returns 1 (reading R5b) -- as the general row
+    const double *Ri = w.rec + (int64_t)i * R::SIZE;
+    double *ULi = w.UL + (int64_t)i * SP;
+#pragma unroll
+    for (int s = 0; s < S; ++s) ULi[s] = Ri[s];
+    const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
+    for (int64_t k = k0; k < k1; ++k) {
+      w.la[k] = 1.0;
+      if (P_trace) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) P_trace[k * SP + s] = 0.0;
+      }
+    }
+    return;
+  }
   const double tau = w.tau_inst[m.inst ? m.inst[i] : 0];
   const double *Ri = w.rec + (int64_t)i * R::SIZE;
   double ui[S], ul[S], gi[S];
@@ -965,6 +1091,10 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
     if (j == i) {
 #pragma unroll
       for (int s = 0; s < S; ++s) Pk[s] = 0.0;
+      if (P_trace) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) P_trace[k * SP + s] = 0.0;
+      }
       w.la[k] = 1.0;
       continue;
     }
@@ -979,6 +1109,10 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
       P[s] = cm * (gi[s] - (double)Gj[s]) + cd * (Rj[s] - ui[s]);
       Pk[s] = P[s];
     }
+    if (P_trace) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) P_trace[k * SP + s] = P[s];
+    }
     if (line_search_at_one<DIM>(p, ul, P, rmin, rmax, phimin5))
       w.la[k] = 1.0;
     else if (k - k0 < 64)
@@ -992,10 +1126,10 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
 // rows i, i + grid size, ... (the grid may be capped to limit the rows in
 // flight; one row per thread otherwise)
 template <int DIM, typename T>
-__global__ void __launch_bounds__(TPB_MAX) k_lim1(MeshView m, Params p, Work w) {
+__global__ void __launch_bounds__(TPB_MAX) k_lim1(MeshView m, Params p, Work w, double *P_trace) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.n; i += gridDim.x * blockDim.x) {
     if (w.st->err) return;
-    lim1_row<DIM, T>(m, p, w, i);
+    lim1_row<DIM, T>(m, p, w, P_trace, i);
   }
 }
 
@@ -1021,6 +1155,16 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
   const double *Ui = Uin + (int64_t)i * SP;
 #pragma unroll
   for (int s = 0; s < S; ++s) u[s] = Ui[s];
+  if (!w.rough2[i]) {  // every P_ij is 0 (see lim1_row): the state stays, every next search returns 1
+    double *Uo = Uout + (int64_t)i * SP;
+#pragma unroll
+    for (int s = 0; s < S; ++s) Uo[s] = u[s];
+    for (int64_t k = k0; k < k1; ++k) {
+      lout[k] = 1.0;
+      if (lsym_trace) lsym_trace[k] = m.col[k] == i ? 1.0 : lmin(lin[k], lin[m.tr[k]]);
+    }
+    return;
+  }
   for (int64_t k = k0; k < k1; ++k) {
     if (m.col[k] == i) {
       if (lsym_trace) lsym_trace[k] = 1.0;
@@ -1373,7 +1517,7 @@ __device__ __forceinline__ bool admissible(const double *u) {
 template <int DIM>
 __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, const Work &w, const double *__restrict__ Uin,
                                           const double *__restrict__ lin, const double *U0, double coef, double *out,
-                                          double *Upre_trace, int i) {
+                                          double *Upre_trace, double *lsym_trace, int i) {
   constexpr int S = DIM + 2;
   constexpr int SP = Layout<DIM>::SP;
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
@@ -1382,12 +1526,20 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
   const double *Ui = Uin + (int64_t)i * SP;
 #pragma unroll
   for (int s = 0; s < S; ++s) u[s] = Ui[s];
-  for (int64_t k = k0; k < k1; ++k) {
-    if (m.col[k] == i) continue;
-    const double l = lmin(lin[k], lin[m.tr[k]]);
-    const double *Pk = w.P + k * SP;
+  if (w.rough2[i]) {  // else every P_ij is 0 (see lim1_row) and the update adds nothing
+    for (int64_t k = k0; k < k1; ++k) {
+      if (m.col[k] == i) {
+        if (lsym_trace) lsym_trace[k] = 1.0;
+        continue;
+      }
+      const double l = lmin(lin[k], lin[m.tr[k]]);
+      if (lsym_trace) lsym_trace[k] = l;
+      const double *Pk = w.P + k * SP;
 #pragma unroll
-    for (int s = 0; s < S; ++s) u[s] += lambda_i * l * Pk[s];
+      for (int s = 0; s < S; ++s) u[s] += lambda_i * l * Pk[s];
+    }
+  } else if (lsym_trace) {
+    for (int64_t k = k0; k < k1; ++k) lsym_trace[k] = m.col[k] == i ? 1.0 : lmin(lin[k], lin[m.tr[k]]);
   }
   if (Upre_trace) {
 #pragma unroll
@@ -1421,10 +1573,10 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
 template <int DIM>
 __global__ void __launch_bounds__(TPB_MAX) k_final(MeshView m, Params p, Work w, const double *__restrict__ Uin,
                                                const double *__restrict__ lin, const double *U0, double coef,
-                                               double *out, double *Upre_trace) {
+                                               double *out, double *Upre_trace, double *lsym_trace) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.n; i += gridDim.x * blockDim.x) {
     if (w.st->err) return;
-    final_row<DIM>(m, p, w, Uin, lin, U0, coef, out, Upre_trace, i);
+    final_row<DIM>(m, p, w, Uin, lin, U0, coef, out, Upre_trace, lsym_trace, i);
   }
 }
 
@@ -1493,7 +1645,7 @@ template <int DIM> __global__ void k_count_not_admissible(int n, const double *U
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
 void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, int tpb, cudaStream_t s) {
-  k_prep<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, U, w.rec, (T *)w.vrec, w.st);
+  k_prep<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, U, w.rec, (T *)w.vrec, w.rough, w.st);
 }
 template <int DIM, typename T>
 void launch_visc(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s) {
@@ -1518,8 +1670,9 @@ inline unsigned capped_grid(int64_t n, int tpb, int max_blocks) {
   return (max_blocks > 0 && g > (unsigned)max_blocks) ? (unsigned)max_blocks : g;
 }
 template <int DIM, typename T>
-void launch_lim1(const MeshView &m, const Params &p, const Work &w, int tpb, int max_blocks, cudaStream_t s) {
-  k_lim1<DIM, T><<<capped_grid(m.n, tpb, max_blocks), tpb, 0, s>>>(m, p, w);
+void launch_lim1(const MeshView &m, const Params &p, const Work &w, double *P_trace, int tpb, int max_blocks,
+                 cudaStream_t s) {
+  k_lim1<DIM, T><<<capped_grid(m.n, tpb, max_blocks), tpb, 0, s>>>(m, p, w, P_trace);
 }
 template <int DIM>
 void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
@@ -1536,9 +1689,10 @@ void launch_ls_deferred(const MeshView &m, const Params &p, const Work &w, const
 }
 template <int DIM>
 void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,
-                  const double *U0, double coef, double *out, double *Upre_trace, int tpb, int max_blocks,
-                  cudaStream_t s) {
-  k_final<DIM><<<capped_grid(m.n, tpb, max_blocks), tpb, 0, s>>>(m, p, w, Uin, lin, U0, coef, out, Upre_trace);
+                  const double *U0, double coef, double *out, double *Upre_trace, double *lsym_trace, int tpb,
+                  int max_blocks, cudaStream_t s) {
+  k_final<DIM><<<capped_grid(m.n, tpb, max_blocks), tpb, 0, s>>>(m, p, w, Uin, lin, U0, coef, out, Upre_trace,
+                                                                 lsym_trace);
   if (m.n_nonreflecting > 0)
     k_final_nonreflecting<DIM><<<nblocks(m.n_bnd, 256), 256, 0, s>>>(m, p, w, U0, coef, out);
 }
@@ -1614,7 +1768,7 @@ template <int DIM> void launch_count_not_admissible(int n, const double *U, DevS
   template void launch_visc<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);               \
   template void launch_alpha<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);              \
   template void launch_low<DIM, T>(const MeshView &, const Params &, const Work &, int, cudaStream_t);                \
-  template void launch_lim1<DIM, T>(const MeshView &, const Params &, const Work &, int, int, cudaStream_t);
+  template void launch_lim1<DIM, T>(const MeshView &, const Params &, const Work &, double *, int, int, cudaStream_t);
 
 EH_INSTANTIATE_T(2, double)
 EH_INSTANTIATE_T(3, double)
@@ -1627,7 +1781,7 @@ EH_INSTANTIATE_T(3, float)
   template void launch_ls_deferred<DIM>(const MeshView &, const Params &, const Work &, const double *, int, double *, \
                                         int, cudaStream_t);                                                          \
   template void launch_final<DIM>(const MeshView &, const Params &, const Work &, const double *, const double *,     \
-                                  const double *, double, double *, double *, int, int, cudaStream_t);                \
+                                  const double *, double, double *, double *, double *, int, int, cudaStream_t);      \
   template void launch_apply_bc<DIM>(const MeshView &, const Params &, double *, cudaStream_t);                       \
   template void launch_count_not_admissible<DIM>(int, const double *, DevStatus *, cudaStream_t);            \
   template void launch_state_stats<DIM>(int, const double *, const double *, double *, double *, cudaStream_t);

@@ -113,6 +113,12 @@ struct Params {
 struct Work {
   double *rec;     // [n][Rec<DIM>::SIZE]
   double *alpha;   // [n]      alpha_i / 2 (so that d^H_ij = (alpha_i/2 + alpha_j/2) d_ij, exactly as 0.5 (alpha_i + alpha_j) d_ij)
+  // identical-state stencils (exact shortcuts, see k_visc): rough[i] = 1 when
+  // some neighbour's state differs from U_i in any bit (zeroed by k_prep, set
+  // by k_visc); rough2[i] = 1 when row i or one of its neighbours is rough
+  // (written by k_low). A row with rough2 = 0 has P_ij = 0 on every entry.
+  unsigned char *rough;   // [n]
+  unsigned char *rough2;  // [n]
   double *w;       // [nnz][SP]  (f(U_j) - f(U_i)) c_ij
   double *d;       // [nnz]      d^L_ij (diagonal: d_ii)
   double *inc;     // [n][SP]    sum_{j != i} d_ij (U_j - U_i) - w_ij
@@ -177,8 +183,10 @@ void launch_tau(const MeshView &m, const Work &w, int stage, double dt_given, do
 // lim1, pass and final loop over rows with a grid stride; max_blocks > 0 caps
 // their grid (fewer rows in flight: less cache pressure from the gathers of
 // long rows), 0 runs one thread per row
+// P_trace (or NULL): P_ij of the pass, [nnz][SP], 0 on the diagonal
 template <int DIM, typename T>
-void launch_lim1(const MeshView &m, const Params &p, const Work &w, int tpb, int max_blocks, cudaStream_t s);
+void launch_lim1(const MeshView &m, const Params &p, const Work &w, double *P_trace, int tpb, int max_blocks,
+                 cudaStream_t s);
 template <int DIM>
 void launch_pass(const MeshView &m, const Params &p, const Work &w, const double *Uin, double *Uout, const double *lin,
                  double *lout, double *lsym_trace, int slot, int tpb, int max_blocks, cudaStream_t s);
@@ -191,8 +199,8 @@ void launch_ls_deferred(const MeshView &m, const Params &p, const Work &w, const
 // else out = U0 + coef (BC(...) - U0). U0 / out are component-major [S][n].
 template <int DIM>
 void launch_final(const MeshView &m, const Params &p, const Work &w, const double *Uin, const double *lin,
-                  const double *U0, double coef, double *out, double *Upre_trace, int tpb, int max_blocks,
-                  cudaStream_t s);
+                  const double *U0, double coef, double *out, double *Upre_trace, double *lsym_trace, int tpb,
+                  int max_blocks, cudaStream_t s);
 template <int DIM> void launch_apply_bc(const MeshView &m, const Params &p, double *U, cudaStream_t s);
 template <int DIM> void launch_count_not_admissible(int n, const double *U, DevStatus *st, cudaStream_t s);
 // out[0] = min rho, out[1] = min specific internal energy, out[2 + s] =

@@ -10,6 +10,7 @@
 // arrays: its one piece of scratch memory, the per-block minima of the
 // reduction, is the file-scope array below, sized for EH_CFL_NOALLOC_MAX_ROWS
 // rows and kept by every GPU that loads the library until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,8 +27,15 @@ constexpr int kMaxDevices = 64;
 // The scratch: one double per block of kThreads rows (512 KiB).
 static __device__ __align__(256) double g_cfl_block_min[kMaxBlocks];
 
-// Device address of g_cfl_block_min, looked up once per device.
-double *g_scratch_addr[kMaxDevices] = {nullptr};
+// Device address of g_cfl_block_min, looked up once per device and context:
+// the address belongs to the module loaded into one CUDA context, so the cache
+// is keyed on that context's process-unique id (a device reset or a new
+// primary context gets a new id, and the address is looked up again).
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  double *addr;
+};
+ScratchEntry g_scratch[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
 struct Prim {
@@ -91,6 +99,11 @@ __device__ inline double graph_viscosity(int lo, int hi, int64_t k_lohi, int64_t
   return d;
 }
 
+// min(a, b) that keeps a NaN: a row whose state is not admissible (rho <= 0 or
+// internal energy <= 0) gives a NaN bound, which must reach dt_out instead of
+// being dropped by the reduction
+__device__ __forceinline__ double nan_min(double a, double b) { return (a < b || a != a) ? a : b; }
+
 template <int DIM>
 __global__ void __launch_bounds__(kThreads) k_cfl_rows(int n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
                                                        const double *cij, const double *mi, const unsigned char *isb,
@@ -119,15 +132,22 @@ __global__ void __launch_bounds__(kThreads) k_cfl_rows(int n, int64_t nnz, const
                     : graph_viscosity<DIM>(j, i, kt, k, cij, nnz, n, U, isb, gamma);
     }
     bound = cfl * mi[i] / (2.0 * dsum);
+    // the row's own state must be admissible (rho > 0, internal energy > 0):
+    // otherwise the wave speeds are undefined and the step is NaN
+    double m2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) m2 += U[(int64_t)(1 + q) * n + i] * U[(int64_t)(1 + q) * n + i];
+    const double rho = U[i];
+    if (!(rho > 0.0 && U[(int64_t)(DIM + 1) * n + i] - m2 / (2.0 * rho) > 0.0)) bound = NAN;
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) bound = fmin(bound, __shfl_xor_sync(0xffffffffu, bound, off));
+  for (int off = 16; off > 0; off >>= 1) bound = nan_min(bound, __shfl_xor_sync(0xffffffffu, bound, off));
   if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = bound;
   __syncthreads();
   if (threadIdx.x == 0) {
     double b = smin[0];
 #pragma unroll
-    for (int q = 1; q < kThreads / 32; ++q) b = fmin(b, smin[q]);
+    for (int q = 1; q < kThreads / 32; ++q) b = nan_min(b, smin[q]);
     block_min[blockIdx.x] = b;
   }
 }
@@ -135,36 +155,73 @@ __global__ void __launch_bounds__(kThreads) k_cfl_rows(int n, int64_t nnz, const
 __global__ void __launch_bounds__(1024) k_cfl_reduce(const double *block_min, int nb, double *dt_out) {
   __shared__ double sm[32];
   double b = INFINITY;
-  for (int q = threadIdx.x; q < nb; q += blockDim.x) b = fmin(b, block_min[q]);
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) b = nan_min(b, block_min[q]);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) b = fmin(b, __shfl_xor_sync(0xffffffffu, b, off));
+  for (int off = 16; off > 0; off >>= 1) b = nan_min(b, __shfl_xor_sync(0xffffffffu, b, off));
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = b;
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = sm[0];
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) m = fmin(m, sm[q]);
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) m = nan_min(m, sm[q]);
     *dt_out = m;
   }
 }
 
-// The scratch's device address for the current device (looked up on first use).
+// The id of the CUDA context current on the calling thread, through driver
+// entry points fetched by the runtime (the library does not link libcuda).
+// Called with g_scratch_mutex held.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+eh_status current_context_id(unsigned long long *id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+      cudaGetLastError();
+      return EH_ERR_CUDA;
+    }
+    get_current = (CtxGetCurrentFn)f1;
+    get_id = (CtxGetIdFn)f2;
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, id) != CUDA_SUCCESS) return EH_ERR_CUDA;
+  return EH_OK;
+}
+
+// The scratch's device address in the current device's current context. The
+// lookup (cudaGetSymbolAddress, which allocates nothing) runs on the first
+// call in each context and is cached for the later ones.
 eh_status scratch_for_current_device(double **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return EH_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
+  // makes the device's primary context current if no context is yet
+  if (cudaSetDevice(dev) != cudaSuccess) {
+    cudaGetLastError();
+    return EH_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);  // also guards the entry points cached below
+  unsigned long long ctx_id = 0;
+  if (current_context_id(&ctx_id) != EH_OK) return EH_ERR_CUDA;
+  ScratchEntry &e = g_scratch[dev];
+  if (!e.addr || e.ctx_id != ctx_id) {
     void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_cfl_block_min);
-    if (e != cudaSuccess || !p) {
+    cudaError_t err = cudaGetSymbolAddress(&p, g_cfl_block_min);
+    if (err != cudaSuccess || !p) {
       cudaGetLastError();
       return EH_ERR_CUDA;
     }
-    g_scratch_addr[dev] = (double *)p;
+    e.addr = (double *)p;
+    e.ctx_id = ctx_id;
   }
-  *out = g_scratch_addr[dev];
+  *out = e.addr;
   return EH_OK;
 }
 
@@ -178,6 +235,9 @@ extern "C" eh_status eh_cfl_dt_noalloc(int32_t dim, double gamma, double cfl, in
     return EH_ERR_INVALID_ARG;
   if (n <= 0 || n > EH_CFL_NOALLOC_MAX_ROWS || nnz <= 0 || !row_ptr || !col || !cij || !mi || !U || !dt_out)
     return EH_ERR_INVALID_ARG;
+  // an error left by earlier work of the caller is reported, not consumed:
+  // the caller still finds it with its own cudaGetLastError
+  if (cudaPeekAtLastError() != cudaSuccess) return EH_ERR_CUDA;
   double *scratch = nullptr;
   eh_status st = scratch_for_current_device(&scratch);
   if (st != EH_OK) return st;
@@ -187,6 +247,7 @@ extern "C" eh_status eh_cfl_dt_noalloc(int32_t dim, double gamma, double cfl, in
     k_cfl_rows<2><<<nb, kThreads, 0, s>>>(n, nnz, row_ptr, col, cij, mi, is_boundary, U, gamma, cfl, scratch);
   else
     k_cfl_rows<3><<<nb, kThreads, 0, s>>>(n, nnz, row_ptr, col, cij, mi, is_boundary, U, gamma, cfl, scratch);
+  if (cudaGetLastError() != cudaSuccess) return EH_ERR_CUDA;  // this launch's error only (none was pending)
   k_cfl_reduce<<<1, 1024, 0, s>>>(scratch, nb, dt_out);
   if (cudaGetLastError() != cudaSuccess) return EH_ERR_CUDA;
   return EH_OK;

@@ -3,6 +3,9 @@ transpose index, the dependency-closure submesh used for sampled parity at
 full size, and an SSPRK(3,3) stage loop that exposes every stage's trace."""
 from __future__ import annotations
 
+import json
+import os
+
 import numpy as np
 
 from paper_2106_02159_gb300 import meshes as M
@@ -98,3 +101,62 @@ def submesh(mesh, seeds, radius, bnd_state=None):
         bnd_normal_full=np.ascontiguousarray(mesh.bnd_normal_full[:, bsel]))
     bs = None if bnd_state is None else np.ascontiguousarray(bnd_state[:, bsel])
     return sm, old, new_of_old[seeds], bs
+
+
+# ---------------------------------------------------------------------------
+# parity tolerances (GPU against the oracle)
+# ---------------------------------------------------------------------------
+
+STEP_TOL = 1e-12  # relative L1 per step
+RUN_TOL = 1e-9    # relative L1 after 100 steps
+
+# Runs whose limiter decisions hinge on roundoff (strict local bounds, shocks)
+# are held to SPREAD_FACTOR x the oracle's own spread: the largest relative L1
+# change of the oracle's result under SPREAD_SAMPLES other valid roundings of
+# the same computation (one-ulp noise on the input, and the same source built
+# with fused multiply-adds). The GPU's result is one more such rounding; the
+# factor and its measured basis are stated in the design notes (section 5).
+SPREAD_FACTOR = 10.0
+SPREAD_SAMPLES = 3  # input-noise samples (plus the contracted build)
+
+
+def rel_l1(a, b):
+    """Relative L1 difference per component. A component that is zero or
+    nearly zero everywhere (e.g. the transverse momentum of a 1D problem) is
+    measured against 1e-3 of the largest component's L1 norm instead."""
+    norms = np.abs(b).sum(axis=-1)
+    floor = 1e-3 * norms.max(axis=-1, keepdims=True) if norms.ndim else 0.0
+    return np.abs(a - b).sum(axis=-1) / np.maximum(norms, np.maximum(floor, 1e-300))
+
+
+def oracle_spread(fn, U0, samples=SPREAD_SAMPLES, seed=0, fn_fma=None):
+    """Largest relative L1 change of the oracle's output fn(U0) when U0 is
+    perturbed by one ulp (``samples`` seeded draws), or (fn_fma) when the
+    oracle is the contracted build."""
+    rng = np.random.default_rng(seed)
+    ref = fn(U0)
+    worst = 0.0
+    for _ in range(samples):
+        Up = U0 * (1.0 + 2.2e-16 * rng.choice([-1.0, 0.0, 1.0], U0.shape))
+        worst = max(worst, rel_l1(fn(Up), ref).max())
+    if fn_fma is not None:
+        worst = max(worst, rel_l1(fn_fma(U0), ref).max())
+    return worst
+
+
+def tolerance(target, spread):
+    return max(target, SPREAD_FACTOR * spread)
+
+
+def record(case, err, spread=None, tol=None, **extra):
+    """Appends one parity measurement (error, oracle spread, their ratio and
+    the tolerance applied) to the JSON-lines file named by $EH_PARITY_LOG, if
+    set, so that the achieved ratios are kept with the run's output."""
+    path = os.environ.get("EH_PARITY_LOG")
+    if not path:
+        return
+    row = dict(case=case, err=float(err), spread=None if spread is None else float(spread),
+               ratio=None if not spread else float(err) / float(spread), tol=None if tol is None else float(tol))
+    row.update(extra)
+    with open(path, "a") as f:
+        f.write(json.dumps(row) + "\n")

@@ -470,11 +470,11 @@ def test_indicator_properties():
 
 def _riemann_errors(case, sizes=(100, 200, 400), relax=False):
     errs = []
+    data = W.RIEMANN_CASES[case] if isinstance(case, str) else case
     for nx in sizes:
         mesh = W.riemann_strip(nx)
         orc = oracle.Oracle(mesh, bound_relaxation=relax)
-        data = W.RIEMANN_CASES[case]
-        U, t, _ = orc.run_to(W.riemann_initial(mesh, case), data[-1])
+        U, t, _ = orc.run_to(W.riemann_initial(mesh, data), data[-1])
         rho, _, _ = RE.sample(mesh.coords[:, 0], t, *data[:6])
         errs.append((mesh.mi * np.abs(U[0] - rho)).sum() / (mesh.mi * rho).sum())
         assert orc.count_not_admissible(U) == 0
@@ -483,12 +483,47 @@ def _riemann_errors(case, sizes=(100, 200, 400), relax=False):
 
 @pytest.mark.parametrize("case", sorted(W.RIEMANN_CASES))
 def test_riemann_problems_converge_to_exact_solution(case):
-    """L1 density error on a quasi-1D strip decreases at a rate >= 0.6 (the
-    rate of contacts and shocks is between 1/2 and 1 for this scheme)."""
+    """L1 density error on a quasi-1D strip decreases at a rate >= 0.6. Three
+    of the four problems carry a contact discontinuity, which no
+    characteristic compresses: a scheme of order p smears it over
+    O(h^(p/(p+1))) cells (Harten's estimate for linear discontinuities), so
+    the L1 rate there tends to 2/3 for a second-order scheme, and 0.6 leaves
+    room for the pre-asymptotic range. Shocks alone converge at rate 1 (see
+    the single-shock test below)."""
     e = _riemann_errors(case)
     rates = np.log2(e[:-1] / e[1:])
     assert np.all(rates >= 0.6), (e, rates)
     assert e[-1] < {"sod": 0.01, "lax": 0.02, "strong_shock": 0.05, "double_rarefaction": 0.01}[case]
+
+
+def _single_shock_case(mach=2.0, gamma=GAMMA, t_end=0.12):
+    """A right-moving shock of Mach number ``mach`` into gas at rest (rho = 1,
+    p = 1), the left state from the Rankine-Hugoniot relations, so that the
+    exact solution is the shock alone (no contact, no rarefaction)."""
+    rho1, p1 = 1.0, 1.0
+    a1 = math.sqrt(gamma * p1 / rho1)
+    m2 = mach * mach
+    rho2 = rho1 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p2 = p1 * (1.0 + 2.0 * gamma / (gamma + 1.0) * (m2 - 1.0))
+    s = mach * a1
+    u2 = s * (1.0 - rho1 / rho2)
+    # start left of the centre so that the shock stays inside the strip
+    return (rho2, u2, p2, rho1, 0.0, p1, t_end), s
+
+
+def test_single_shock_converges_at_first_order():
+    """A lone shock is self-steepening: the scheme keeps it a fixed number of
+    cells wide, so the L1 density error falls like h (rate >= 0.8, the rate
+    the survey of the method asks of discontinuities), and the exact solution
+    the error is measured against is the shock alone (checked)."""
+    case, s = _single_shock_case()
+    rl, ul, pl, rr, ur, pr, t_end = case
+    rho_ex, u_ex, p_ex = RE.sample(np.array([0.5 + s * t_end - 1e-9, 0.5 + s * t_end + 1e-9]), t_end,
+                                   rl, ul, pl, rr, ur, pr)
+    assert np.allclose(rho_ex, [rl, rr], rtol=1e-10) and np.allclose(p_ex, [pl, pr], rtol=1e-10)
+    e = _riemann_errors(case)
+    rates = np.log2(e[:-1] / e[1:])
+    assert np.all(rates >= 0.8), (e, rates)
 
 
 def _vortex_errors(relax, sizes=(32, 64, 128), t_final=2.0):

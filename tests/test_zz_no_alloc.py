@@ -1,5 +1,5 @@
 """The allocation-free CFL step (eh_cfl_dt_noalloc) against the context-based
-one (eh_cfl_dt).
+one (eh_cfl_dt) and against the oracle's CFL step (eq. dtCfl).
 
 eh_cfl_dt_noalloc serves callers that may not allocate device memory (a host
 framework that owns all device memory, a real-time loop); its only scratch is a
@@ -11,6 +11,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2106_02159_gb300 import binding as B
 from paper_2106_02159_gb300 import meshes as M
 from paper_2106_02159_gb300 import workloads as W
@@ -51,16 +52,40 @@ def test_noalloc_cfl_step_matches_context_path_twice(case):
     dm = _device_mesh(torch, mesh)
     solver = B.Solver(dim=mesh.dim, cfl=0.5)
     solver.upload_mesh(mesh, bs)
+    orc = oracle.Oracle(mesh, cfl=0.5, bnd_state=bs)
     dt_out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
     for U in states:  # two calls in a row share the scratch array
         solver.set_state(U)
         expect = solver.cfl_dt()
+        ref = orc.cfl_dt(U)
         Ud = torch.as_tensor(np.ascontiguousarray(U), device="cuda")
         B.cfl_dt_noalloc(mesh.dim, 1.4, 0.5, dm["row_ptr"], dm["col"], dm["cij"], dm["mi"], dm["is_boundary"], Ud,
                          dt_out)
         torch.cuda.synchronize()
         got = float(dt_out.item())
         assert abs(got - expect) <= DT_TOL * expect, (got, expect)
+        assert abs(got - ref) <= DT_TOL * ref, (got, ref)
+
+
+def test_noalloc_reports_a_non_admissible_row_as_nan():
+    """A row whose internal energy is negative has no wave speed: the step is
+    NaN, not the minimum over the other rows."""
+    torch = pytest.importorskip("torch")
+    B.build()
+    mesh, _, _ = W.cylinder_problem(10)
+    U = W.perturbed_state(mesh, 3)
+    dm = _device_mesh(torch, mesh)
+    dt_out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    Ud = torch.as_tensor(np.ascontiguousarray(U), device="cuda")
+    B.cfl_dt_noalloc(2, 1.4, 0.5, dm["row_ptr"], dm["col"], dm["cij"], dm["mi"], dm["is_boundary"], Ud, dt_out)
+    torch.cuda.synchronize()
+    assert np.isfinite(float(dt_out.item()))
+    bad = U.copy()
+    bad[3, mesh.n // 2] = 0.25 * (bad[1, mesh.n // 2] ** 2 + bad[2, mesh.n // 2] ** 2) / bad[0, mesh.n // 2]
+    Ud = torch.as_tensor(np.ascontiguousarray(bad), device="cuda")
+    B.cfl_dt_noalloc(2, 1.4, 0.5, dm["row_ptr"], dm["col"], dm["cij"], dm["mi"], dm["is_boundary"], Ud, dt_out)
+    torch.cuda.synchronize()
+    assert np.isnan(float(dt_out.item()))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
