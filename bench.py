@@ -13,11 +13,18 @@ e2e     : the same metric through the C ABI with host buffers: every step
           copies the state from pinned host memory in (eh_set_state) and back
           out (eh_get_state), inside the timed region.
 roofline: the kernel with the largest share of the step time (CUDA events
-          around each kernel on the solver's stream): its algorithmic FP64 flops
-          per launch over its mean duration against the FP64 peak (every kernel
-          of this path is bound by FP64 issue on GB300); its algorithmic bytes
-          against the measured HBM copy rate are reported beside it.
-cpu_baseline : the FP64 oracle on the host cores, on a window of the same mesh.
+          around each kernel on the solver's stream): its FP64 operations,
+          counted once from the method's formulas (method_fp64_flops), over
+          its mean duration against the FP64 peak (the path is bound by FP64
+          issue on GB300); beside it the HBM fraction by the planned
+          schedule's per-unit bytes (survey_bytes) and the whole step's
+          minimum-bytes fraction (survey_min_bytes_per_stage).
+developed_flow: the same mesh from a seeded perturbed state (no identical-
+          state edge, so no kernel takes the exact identical-state shortcut):
+          time per step and the same roofline -- the FP64 fraction of the
+          kernels doing all of their work.
+cpu_baseline : the FP64 oracle on the host cores (all threads, and one
+          thread), on a window of the same mesh, from the inflow state.
 
 --impl reference runs the oracle (the CPU reference of this repository) for
 the same workload and metric. Multi-GPU (torchrun): independent replicas, one
@@ -64,6 +71,11 @@ def parse_args():
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds-single", type=float, default=10.0,
+                    help="seconds of the single-thread oracle leg of cpu_baseline (0: skip)")
+    ap.add_argument("--repeats", type=int, default=4, help="repeats of the K timed steps (median of 1 + repeats)")
+    ap.add_argument("--no-perturbed", action="store_true",
+                    help="skip the measurement on the perturbed state of the same mesh")
     ap.add_argument("--precision", choices=("fp64", "mixed"), default="fp64",
                     help="fp64: everything in FP64; mixed: FP32 c_ij, lambda_max, d_ij, high-order fluxes")
     return ap.parse_args()
@@ -165,78 +177,72 @@ def make_workload(args):
     return w, desc
 
 
-def algorithmic_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
-    """Bytes each kernel must move at least once per launch (every array it
-    reads or writes, each element once; neighbour gathers counted once).
-    S = dim + 2 state components, SP = padded stride, REC = node record."""
+def survey_bytes(kernel: str, n: int, nnz: int, dim: int) -> float:
+    """Algorithmic HBM bytes of one launch by the per-unit figures of the
+    method's planned schedule (the scope table's measurement section): the
+    viscosity and low-order passes each read col + c_ij and write or read d_ij
+    (12 + 8 dim B per entry), the first limiter pass reads col, m_ij, d_ij and
+    writes l (28 B), the symmetrising pass and the final pass read col, m_ij,
+    d_ij, l, the transpose index and l_ji (48 B); per node, every state-sized
+    vector (S = dim + 2 doubles) the pass reads or writes, once."""
     S = dim + 2
-    SP = 4 if dim == 2 else 6
-    rec = 8 * (2 * dim + 12)           # node record fields written by prep
-    per = {
-        "prep": (8 * S + rec, 0),
-        # k_visc (c_ij, |c_ij|, 1/|c_ij| and the transpose index of the j > i half;
-        # w_ij, a_ij, d_ij written once per entry) + k_alpha (w_ij, a_ij read; alpha written)
-        "visc": (8 + rec + 1 + 8 * (S + 4) + 8, 4 + (4 + 8 * dim + 16) / 2 + 8 * S + 16 + 4 + 8 * S + 8),
-        "low": (8 + 8 * (S + 1) + 8 * 3 + 8 * SP * 2 + 8 * 4, 4 + 8 + 8 * S),
-        "lim1": (8 + 8 * S + 8 * SP * 2 + 8 + 8 * 4 + 8 + 8 * SP, 4 + 8 * 2 + 8 * SP + 8),
-        "pass": (8 + 8 * SP * 2 + 8 * 4, 4 + 4 + 8 + 8 * SP * 2 + 8),
-        "final": (8 + 8 * SP + 8 * S * 2 + 4, 4 + 4 + 8 + 8 * SP),
+    v = 8 * S
+    per_entry, per_node = {
+        "prep": (0, 2 * v),
+        "visc": (12 + 8 * dim, v),
+        "low": (12 + 8 * dim, v + 2 * v + 24),  # U read; U^L, F^H written; bounds
+        "lim1": (28, 2 * v + 24),               # U^L, F^H read; bounds read
+        "pass": (48, 2 * v),
+        "final": (48, 3 * v),                   # limited state and U0 read, result written
         "tau": (0, 0),
-        "lsearch": (0, 0),  # data dependent: the queued searches only
+        "lsearch": (0, 0),
     }[kernel]
-    return per[0] * n + per[1] * nnz
+    return per_entry * nnz + per_node * n
 
 
-# DRAM bytes (read + write) per CSR entry of each kernel kind, from the ncu
-# capture in profiles/all_kernels_cylinder500k.md (2D Q1 cylinder, FP64,
-# developed flow); a launch moves about this times nnz. Only valid for the
-# kernels as captured there, and only for the 2D FP64 cylinder workload.
-NCU_DRAM_BYTES_PER_ENTRY_2D_FP64 = {
-    "prep": 5.6, "visc": 180.6, "low": 75.5, "lim1": 121.1, "pass": 86.8, "final": 56.9,
-}
-# FP64 pipe activity (sm__pipe_fp64_cycles_active, % of peak) on the same capture:
-# how busy the issue-bound kernels keep the FP64 units (k_visc and k_alpha
-# time-weighted as "visc")
-NCU_FP64_PIPE_ACTIVE_2D_FP64 = {
-    "prep": 0.837, "visc": 0.825, "low": 0.862, "lim1": 0.839, "pass": 0.610, "final": 0.630,
-}
-
-
-def algorithmic_fp64_flops(kernel: str, n: int, nnz: int, dim: int) -> float:
-    """FP64 floating-point operations each kernel performs per launch on the
-    common path (+, -, *, /, sqrt = 1; fused multiply-add = 2; comparisons,
-    min/max and the data-dependent branches -- shock sqrt terms, the density
-    division when l = 1 is infeasible, the entropy iteration -- not counted),
-    from the formulas of each kernel: a count per off-diagonal entry times
-    nnz - n plus a count per node times n."""
+def survey_min_bytes_per_stage(n: int, nnz: int, dim: int) -> float:
+    """The minimum the method must move per forward-Euler stage: static edge
+    data read once (c_ij 8 dim + m_ij 8 + col 4 B per entry), the state read and
+    written once (2 x 8 S per node), m_i (8) and row_ptr (4) per node (C2:
+    328 B per node, C3: 1064)."""
     S = dim + 2
+    return (8 * dim + 8 + 4) * nnz + (2 * 8 * S + 8 + 4) * n
+
+
+def method_fp64_flops(kernel: str, n: int, nnz: int, dim: int) -> float:
+    """FP64 operations of one launch counted ONCE from the method's formulas
+    (Algorithm 1 with the readings of the scope table), independently of how
+    the kernels evaluate them: +, -, x, /, sqrt and each elementary function
+    (pow, log) = 1; comparisons, min/max and |x| = 0; data-dependent branches
+    (shock square roots, the density division, the entropy iteration) not
+    counted. Per node: primitives v, eps, p, a (3d + 7), a p^-z (2), Phi (2),
+    eta (3), q (d), f(U) (d^2 + 2d + 1), eta'(U) (3d + 10). Per unique edge:
+    n_ij (3d), the normal velocities (4d - 2), p_tr (7), the two outer wave
+    speeds (14), d_ij (1). Per off-diagonal entry: (f_j - f_i) c_ij (S(3d - 1)),
+    (q_j - q_i).c_ij (3d - 1), eta'.(.) (2S - 1), N and D (4); bar states and
+    the low-order sum (7S + 1), d^H and F^H (4S + 3); P_ij (6S + 3); the l = 1
+    check of each pass (S + 2d + 6); the limited updates (3S each) and the
+    shrink (S + 1). Per node also: U^L (2S + 2), P's prefactor (2), the CFL
+    bound (3), the SSP combination (3S)."""
+    d, S = dim, dim + 2
     e = nnz - n
-    per_entry = {
-        "prep": 0,
-        # k_visc once per unique edge (v.c_ij of both nodes, w_ij from them, a_ij,
-        # the normal velocities, lambda_max, d_ij) + k_alpha per entry
-        "visc": (12 * dim + 21) / 2.0 + 2 * S + 4,
-        "low": 7 * S + 12,
-        "lim1": 9 * S + 2 * dim + 18,
-        "pass": 5 * S + 2 * dim + 16,
-        "final": 2 * S + 1,
-        "tau": 0,
-        "lsearch": 0,
-    }[kernel]
-    per_node = {
-        "prep": 4 * dim + 46,
-        "visc": 2 * dim + 12,
-        "low": 11,
-        "lim1": 2 * S + 6,
-        "pass": 3,
-        "final": 4 * dim + 3 * S,
-        "tau": 0,
-        "lsearch": 0,
+    check = S + 2 * d + 6
+    per_entry, per_node = {
+        "prep": (0.0, d * d + 9 * d + 25),
+        "visc": ((7 * d + 20) / 2.0 + S * (3 * d - 1) + (3 * d - 1) + (2 * S - 1) + 4, 1),
+        "low": ((7 * S + 1) + (4 * S + 3) + 1, 3),
+        "lim1": ((6 * S + 3) + check, (2 * S + 2) + 2),
+        "pass": (3 * S + (S + 1) + check, 0),
+        "final": (3 * S, 3 * S),
+        "tau": (0.0, 0),
+        "lsearch": (0.0, 0),
     }[kernel]
     return per_entry * e + per_node * n
 
 
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# FP64 peak: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (the recipe's
+# 1.25 TFLOP/s; a throughput probe of independent FMA chains measured 1.01)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def peaks():
@@ -277,18 +283,17 @@ def window_sample(mesh, U0, bs, x0=0.35, x1=0.85):
 
 class OracleSample:
     """The oracle as it stands, on a sample of the workload (a window of the
-    same mesh for large meshes, the full mesh otherwise), from the state U
-    (default: the workload's initial state)."""
+    same mesh for large meshes, the full mesh otherwise), from the workload's
+    initial state. ``threads`` OpenMP threads (0: all host cores)."""
 
-    def __init__(self, w, U=None):
+    def __init__(self, w, threads=0):
         import oracle
-        self.threads = oracle.set_threads(0)
-        U = w.U0 if U is None else U
+        self.threads = oracle.set_threads(threads)
         if w.mesh.n > 200_000:
-            mesh, U0, bs = window_sample(w.mesh, U, w.bnd_state)
+            mesh, U0, bs = window_sample(w.mesh, w.U0, w.bnd_state)
             self.sample = f"rows with x in [0.35, 0.85] of the same mesh ({mesh.n} vertices)"
         else:
-            mesh, U0, bs = w.mesh, U, w.bnd_state
+            mesh, U0, bs = w.mesh, w.U0, w.bnd_state
             self.sample = f"the full mesh ({mesh.n} vertices)"
         self.n = mesh.n
         self.orc = oracle.Oracle(mesh, cfl=w.cfl, bnd_state=bs)
@@ -298,10 +303,13 @@ class OracleSample:
         self.U, _, _ = self.orc.ssprk3_step(self.U)
 
 
-def cpu_baseline(w, seconds: float, U=None, state_desc="the inflow state"):
+STATE_NOTE = "from the inflow state (the same start as the reference arm)"
+
+
+def cpu_baseline(w, seconds: float, threads=0):
     """Times the oracle: SSPRK(3,3) steps on the sample for ~``seconds``,
-    starting from U (default: the workload's initial state)."""
-    smp = OracleSample(w, U)
+    from the workload's initial state."""
+    smp = OracleSample(w, threads)
     steps = 0
     t0 = time.perf_counter()
     while True:
@@ -312,8 +320,8 @@ def cpu_baseline(w, seconds: float, U=None, state_desc="the inflow state"):
             break
     value = smp.n * 3 * steps / el
     return {"value": value, "unit": UNIT, "cores": smp.threads, "kind": "oracle",
-            "sample": f"{steps} SSPRK(3,3) steps on {smp.sample}, from {state_desc}, FP64 C oracle, "
-                      f"{smp.threads} OpenMP threads, {el:.1f} s"}
+            "sample": f"{steps} SSPRK(3,3) steps on {smp.sample}, {STATE_NOTE}, FP64 C oracle, "
+                      f"{smp.threads} OpenMP thread(s), {el:.1f} s"}
 
 
 # ---------------------------------------------------------------------------
@@ -335,8 +343,7 @@ def run_reference(args, dist):
     el = time.perf_counter() - t0
     value = smp.n * 3 * args.steps / el
     cb = {"value": value, "unit": UNIT, "cores": smp.threads, "kind": "oracle",
-          "sample": f"{args.steps} SSPRK(3,3) steps on {smp.sample}, from the inflow state (the developed "
-                    f"state of the GPU arm's window needs a GPU to prepare), FP64 C oracle, "
+          "sample": f"{args.steps} SSPRK(3,3) steps on {smp.sample}, {STATE_NOTE}, FP64 C oracle, "
                     f"{smp.threads} OpenMP threads"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -347,9 +354,99 @@ def run_reference(args, dist):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) per CSR entry of each kernel kind, from one ncu
+# capture of the kernels as they stand (dram__bytes_read.sum +
+# dram__bytes_write.sum, 2D Q1 cylinder, FP64, developed flow, 4.0M vertices,
+# the bench's own timed window); a launch moves about this times nnz. None
+# where a kernel changed after the capture.
+NCU_DRAM_BYTES_PER_ENTRY_2D_FP64 = {
+    "prep": 6.0, "visc": 147.1, "low": 59.7, "lim1": 68.0, "pass": 51.4, "final": 34.2,
+}
+NCU_CAPTURE_NOTE = "ncu capture of the 501,402-vertex cylinder (developed flow), per entry, scaled by nnz"
+
+
+def kernel_profile(solver, steps):
+    """Per-kernel CUDA-event times (eager launches, events on the solver's
+    stream) over ``steps`` steps: {kind: (total ms, launches)}."""
+    solver.profile(True)
+    solver.run(steps)
+    prof = solver.profile_read()
+    solver.profile(False)
+    return prof
+
+
+def roofline_of(prof, mesh, ms_per_step, hbm, hbm_src, precision):
+    """The dominant kernel's FP64 fraction (method-fixed operation count over
+    its mean CUDA-event time, against the FP64 peak) with its HBM fraction by
+    the schedule's per-unit bytes, and the whole step's minimum-bytes HBM
+    fraction."""
+    total = sum(v[0] for v in prof.values())
+    shares = {k: v[0] / total for k, v in prof.items() if v[1]}
+    top = max((k for k in shares if k != "lsearch"), key=shares.get)
+    top_ms = prof[top][0] / prof[top][1]
+    flops = method_fp64_flops(top, mesh.n, mesh.nnz, mesh.dim)
+    achieved = flops / (top_ms * 1e-3) / 1e12
+    kbytes = survey_bytes(top, mesh.n, mesh.nnz, mesh.dim)
+    step_bytes = 3 * survey_min_bytes_per_stage(mesh.n, mesh.nnz, mesh.dim)
+    traffic = None
+    if mesh.dim == 2 and precision == "fp64" and NCU_DRAM_BYTES_PER_ENTRY_2D_FP64.get(top) is not None:
+        traffic = NCU_DRAM_BYTES_PER_ENTRY_2D_FP64[top] * mesh.nnz
+    per_kernel = {}
+    for k, (ms, cnt) in prof.items():
+        if not cnt or k in ("tau", "lsearch"):
+            continue
+        t = ms / cnt * 1e-3
+        per_kernel[k] = {"mean_launch_ms": round(ms / cnt, 4), "share": round(shares[k], 4),
+                         "fp64_frac": round(method_fp64_flops(k, mesh.n, mesh.nnz, mesh.dim) / t / 1e12
+                                            / FP64_PEAK_TFLOPS, 4),
+                         "hbm_frac": round(survey_bytes(k, mesh.n, mesh.nnz, mesh.dim) / t / 1e9 / hbm, 4)}
+    return {"bound": "alu", "kernel": f"k_{top}", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+            "traffic_source": NCU_CAPTURE_NOTE if traffic else None,
+            "peak_source": "FP64 nominal: 152 SMs x 2 FMA/clk x 2 flops x 2.07 GHz (the recipe's 1.25 TFLOP/s)",
+            "count": "method-fixed FP64 operations per launch from the method's formulas (method_fp64_flops)",
+            "method_fp64_flops_per_launch": flops, "mean_launch_ms": top_ms,
+            "hbm": {"achieved": kbytes / (top_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": kbytes / (top_ms * 1e-3) / 1e9 / hbm, "peak_source": hbm_src,
+                    "bytes_per_launch": kbytes, "bytes": "the planned schedule's per-unit figures (survey_bytes)"},
+            "step_hbm_min": {"achieved": step_bytes / (ms_per_step * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                             "frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm, "bytes_per_step": step_bytes,
+                             "bytes": "minimum per stage x 3 (survey_min_bytes_per_stage)"},
+            "kernel_shares": {k: round(v, 4) for k, v in sorted(shares.items(), key=lambda t: -t[1])},
+            "per_kernel": per_kernel,
+            "note": "the count is the method's for every entry; entries between bit-identical states are "
+                    "evaluated by the exact identical-state shortcut (see identical_edge_share), so where that "
+                    "share is large a fraction can exceed what the executed arithmetic alone would give -- "
+                    "developed_flow has none of them"}
+
+
+def timed_steps(solver, stream, steps):
+    """Device time of ``steps`` steps (one CUDA-graph replay each), CUDA events
+    on the solver's stream, synchronised on both sides."""
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.run(steps)
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def identical_edge_share(mesh, U):
+    """Share of off-diagonal entries whose two states are equal bit for bit
+    (the edges the kernels evaluate by the exact identical-state shortcut)."""
+    rows = mesh.row_of_entry()
+    off = mesh.col != rows
+    same = np.all(U[:, mesh.col[off]] == U[:, rows[off]], axis=0)
+    return float(same.mean())
+
+
 def run_ours(args, dist):
     import torch
-    from paper_2106_02159_gb300 import binding
+    from paper_2106_02159_gb300 import binding, workloads
     torch.cuda.set_device(dist.local_rank)
     binding.build()
     w, desc = make_workload(args)
@@ -372,62 +469,53 @@ def run_ours(args, dist):
     solver.synchronize()
     d_start = solver.diagnostics()
     t_window = d_start["t"]
+    same_share = identical_edge_share(mesh, solver.get_state())
 
-    # ---- device-timed steps ----
+    # ---- device-timed steps (the contract's K steps) ----
     clocks = Clocks(dist.local_rank)
     dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    solver.run(args.steps)
-    e1.record(stream)
-    stream.synchronize()
-    torch.cuda.synchronize()
+    ms = timed_steps(solver, stream, args.steps)
+    # repeats of the same K steps (the flow keeps developing): median and range
+    repeats = [timed_steps(solver, stream, args.steps) for _ in range(args.repeats)]
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
     solver.synchronize()
     diag = solver.diagnostics()
     # share of the limiter line searches (one per off-diagonal entry, pass and
     # stage) that the l = 1 check did not settle, over the timed steps
     deferred = (diag["line_searches_deferred"] - d_start["line_searches_deferred"]) / (
-        args.steps * 3 * 2 * (mesh.nnz - mesh.n))
+        (args.steps * (1 + args.repeats)) * 3 * 2 * (mesh.nnz - mesh.n))
     dist.barrier()
     ms = dist.max(ms)
     per_step_ms = ms / args.steps
     value = mesh.n * 3 * args.steps * dist.world / (ms * 1e-3)
+    rep_values = [mesh.n * 3 * args.steps / (r * 1e-3) for r in [ms] + repeats]
 
     # ---- per-kernel event timing (same kernels, eager launches) ----
-    solver.profile(True)
-    solver.run(args.profile_steps)
-    prof = solver.profile_read()
-    solver.profile(False)
-    total = sum(v[0] for v in prof.values())
-    shares = {k: v[0] / total for k, v in prof.items() if v[1]}
-    # the dominant row kernel (the queued line searches have no per-entry model)
-    top = max((k for k in shares if k != "lsearch"), key=shares.get)
-    top_ms = prof[top][0] / prof[top][1]
     hbm, hbm_src = peaks()
-    bytes_top = algorithmic_bytes(top, mesh.n, mesh.nnz, mesh.dim)
-    flops_top = algorithmic_fp64_flops(top, mesh.n, mesh.nnz, mesh.dim)
-    achieved = flops_top / (top_ms * 1e-3) / 1e12
-    hbm_achieved = bytes_top / (top_ms * 1e-3) / 1e9
-    # every kernel of the step is bound by FP64 issue on GB300 (ncu: FP64 pipe
-    # 83-86% of peak, DRAM <= 1 TB/s), so the roofline is the FP64 ALU one
-    traffic = None
-    if mesh.dim == 2 and args.precision == "fp64" and top in NCU_DRAM_BYTES_PER_ENTRY_2D_FP64:
-        traffic = NCU_DRAM_BYTES_PER_ENTRY_2D_FP64[top] * mesh.nnz
-    roofline = {"bound": "alu", "kernel": f"k_{top}", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per entry on the 500k-vertex "
-                                  "capture, scaled by nnz" if traffic else None,
-                "fp64_pipe_active_ncu": NCU_FP64_PIPE_ACTIVE_2D_FP64.get(top) if traffic else None,
-                "peak_source": "nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz); probe-measured FMA rate 1.01",
-                "algorithmic_fp64_flops_per_launch": flops_top, "mean_launch_ms": top_ms,
-                "hbm": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
-                        "peak_source": hbm_src, "algorithmic_bytes_per_launch": bytes_top},
-                "kernel_shares": {k: round(v, 4) for k, v in sorted(shares.items(), key=lambda t: -t[1])}}
+    prof = kernel_profile(solver, args.profile_steps)
+    roofline = roofline_of(prof, mesh, per_step_ms, hbm, hbm_src, args.precision)
+
+    # ---- the same mesh with no identical-state edge: a seeded perturbed
+    # state, so that every kernel evaluates every entry in full ----
+    developed = None
+    if args.workload == "cylinder" and not args.no_perturbed:
+        U_keep = solver.get_state()
+        Up = workloads.perturbed_state(mesh, 2106)
+        solver.set_state(Up)
+        solver.apply_boundary_conditions()
+        same_p = identical_edge_share(mesh, solver.get_state())
+        solver.run(args.warmup)
+        pms = timed_steps(solver, stream, args.steps)
+        pprof = kernel_profile(solver, args.profile_steps)
+        developed = {"workload": "same mesh, seeded perturbed state (smooth density, pressure and velocity bumps "
+                                 "on the inflow state), strict bounds: every entry evaluated in full",
+                     "identical_edge_share": round(same_p, 4), "ms_per_step": pms / args.steps,
+                     "value": mesh.n * 3 * args.steps / (pms * 1e-3), "unit": UNIT,
+                     "roofline": roofline_of(pprof, mesh, pms / args.steps, hbm, hbm_src, args.precision)}
+        developed["roofline"]["traffic"] = None
+        developed["roofline"]["traffic_source"] = None
+        solver.set_state(U_keep)
 
     # ---- end to end through the C ABI with host buffers ----
     host_in = torch.empty((S, mesh.n), dtype=torch.float64, pin_memory=True).numpy()
@@ -445,10 +533,10 @@ def run_ours(args, dist):
 
     cb = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        U_now = solver.get_state() if start > 0 else None
-        cb = cpu_baseline(w, args.cpu_seconds, U_now,
-                          f"the GPU run's state after {start + args.warmup + args.steps} steps" if start > 0
-                          else "the inflow state")
+        cb = cpu_baseline(w, args.cpu_seconds)
+        if args.cpu_seconds_single > 0:
+            cb1 = cpu_baseline(w, args.cpu_seconds_single, threads=1)
+            cb["single_thread"] = {k: cb1[k] for k in ("value", "unit", "cores", "sample")}
     if dist.rank == 0:
         launches = solver.launches_per_step()
         line = {
@@ -461,14 +549,19 @@ def run_ours(args, dist):
                            mesh.nnz * 150 / 1e9),
                        "timed_steps": f"{start + args.warmup}..{start + args.warmup + args.steps} of the run "
                                       f"from the inflow state (t = {t_window:.4g} at the first timed step)",
+                       "identical_edge_share": round(same_share, 4),
                        "line_searches_not_settled_at_l1": round(deferred, 4),
                        "invariant_violations": diag["not_admissible"],
                        "cfl_violations": diag["cfl_violations"]},
+            "runs": {"what": f"the timed K steps and {args.repeats} repeats of K steps right after them",
+                     "values": [round(v, 1) for v in rep_values], "median": float(np.median(rep_values)),
+                     "min": float(min(rep_values)), "max": float(max(rep_values))},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * S * mesh.n,
                     "d2h_bytes_per_step": 8 * S * mesh.n},
             "gpu_launches": launches * args.steps,
             "roofline": roofline,
+            "developed_flow": developed,
             "cpu_baseline": cb,
         }
         print(json.dumps(line), flush=True)

@@ -374,15 +374,95 @@ __device__ double line_search_iterate(const Params &p, const double *ub, const d
   return lL;
 }
 
+// FP32 pre-decision of the entropy test at l = 1 (gamma = 7/5): with
+// u = ub + P, does (rho E - |m|^2/2)^5 >= Phi_min^5 rho^12 hold, for the FP64
+// inputs, in exact arithmetic? The FP32 evaluation carries error bounds built
+// from the inputs' magnitudes (every conversion and operation rounds by at most
+// 2^-24 relative): +1 = holds with a margin that covers them, -1 = fails with
+// such a margin, 0 = too close to call (or outside the range where the FP32
+// powers can neither overflow nor underflow). Every error term is
+// over-estimated by a third or more (3 units for a chain that rounds twice, 8
+// and 16 for chains of 3 and 6 roundings, B scaled by 1.01), so a decided
+// outcome holds with a relative margin of at least ~1e-7 -- far beyond the
+// FP64 test's own rounding (~1e-15): it is the outcome the FP64 test reaches,
+// and the FP64 test runs only where this returns 0.
+struct RowF32 {
+  float u[5];   // ub rounded to FP32
+  float phi5;   // Phi_min^5 rounded to FP32 (0 when out of range)
+};
+// The row's FP32 data of the pre-decision. Rows whose density bounds are
+// within 1e-4 of each other (near-uniform neighbourhoods) skip it: there psi(1)
+// sits within the FP32 error of 0 almost always, and a warp with one
+// undecided lane pays for both tests.
+template <int DIM>
+__device__ __forceinline__ RowF32 row_f32(const double *ub, double rmin, double rmax, double phimin5) {
+  RowF32 r;
+#pragma unroll
+  for (int s = 0; s < DIM + 2; ++s) r.u[s] = 0.0f;
+  r.phi5 = 0.0f;
+  // 2^-40 <= Phi_min^5 <= 2^40 (else no pre-decision)
+  if (!(gt_pos(rmax - rmin, 1e-4 * rmax) && gt_pos(phimin5, 9.094947017729282e-13) &&
+        lt_pos(phimin5, 1.099511627776e12)))
+    return r;
+#pragma unroll
+  for (int s = 0; s < DIM + 2; ++s) r.u[s] = (float)ub[s];
+  r.phi5 = (float)phimin5;
+  return r;
+}
+
+template <int DIM> __device__ __forceinline__ int entropy_at_one_f32(const RowF32 &r, const double *P) {
+  constexpr int S = DIM + 2;
+  constexpr float u24 = 5.9604645e-8f;  // 2^-24
+  if (r.phi5 == 0.0f) return 0;
+  float u[S], e[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const float pf = (float)P[s];
+    u[s] = r.u[s] + pf;
+    // |u_f - u| <= 2^-24 (|ub| + |P| + |u_f|) (two conversions, one add)
+    e[s] = 3.0f * u24 * (fabsf(r.u[s]) + fabsf(pf));
+  }
+  const float rho = u[0], E = u[S - 1];
+  // 2^-6 <= rho <= 2^6 with its error: rho^12 stays within FP32's range
+  if (!(rho - e[0] >= 0.015625f && rho + e[0] <= 64.0f)) return 0;
+  float m2h = 0.0f, em = 0.0f;
+#pragma unroll
+  for (int q = 0; q < DIM; ++q) {
+    m2h += u[1 + q] * u[1 + q];
+    em += fabsf(u[1 + q]) * e[1 + q] + 0.5f * e[1 + q] * e[1 + q];
+  }
+  m2h *= 0.5f;
+  const float rE = rho * E;
+  const float er = rE - m2h;
+  // |er_f - er| <= propagated input errors + 8 roundings of the magnitudes
+  const float B = 1.01f * (rho * e[S - 1] + fabsf(E) * e[0] + e[0] * e[S - 1] + em +
+                           8.0f * u24 * (fabsf(rE) + m2h));
+  const float elo = er - B, ehi = er + B;
+  // 2^-24 <= er <= 2^24 with its error: er^5 stays within FP32's range
+  if (!(elo >= 5.9604645e-8f && ehi <= 16777216.0f)) return 0;
+  const float rlo = rho - e[0], rhi = rho + e[0];
+  const float l2 = elo * elo, h2 = ehi * ehi;
+  const float lhs_lo = l2 * l2 * elo * (1.0f - 8.0f * u24);
+  const float lhs_hi = h2 * h2 * ehi * (1.0f + 8.0f * u24);
+  const float a2 = rlo * rlo, a4 = a2 * a2, b2 = rhi * rhi, b4 = b2 * b2;
+  const float rhs_lo = r.phi5 * (a4 * a4 * a4) * (1.0f - 16.0f * u24);
+  const float rhs_hi = r.phi5 * (b4 * b4 * b4) * (1.0f + 16.0f * u24);
+  if (lhs_lo > rhs_hi) return 1;
+  if (lhs_hi < rhs_lo) return -1;
+  return 0;
+}
+
 // The common outcome of the line search, decided with a short branch-free
 // sequence: P = 0, or l = 1 inside the density bounds and (gamma = 7/5) inside
 // the entropy bound. Returns true exactly where line_search returns 1 through
 // one of these exits; false leaves the entry to the full search. (A warp whose
 // lanes took the search's other exits -- density clipping, psi evaluations,
 // the secant/Newton loop -- inline would issue each of them for all 32 lanes.)
+// The entropy test is pre-decided in FP32 (entropy_at_one_f32) and evaluated
+// in FP64 only where that is too close to call.
 template <int DIM>
 __device__ __forceinline__ bool line_search_at_one(const Params &p, const double *ub, const double *P, double rmin,
-                                                   double rmax, double phimin5) {
+                                                   double rmax, double phimin5, const RowF32 &rf) {
   constexpr int S = DIM + 2;
   bool zero = true;
 #pragma unroll
@@ -398,6 +478,8 @@ __device__ __forceinline__ bool line_search_at_one(const Params &p, const double
   } else if (dbits(rp) < 0) {
     if (lt_pos(rb + rp, rmin)) return false;
   }
+  const int pre = entropy_at_one_f32<DIM>(rf, P);
+  if (pre != 0) return pre > 0;
   double u[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) u[s] = ub[s] + P[s];
@@ -1076,6 +1158,7 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
   const double *bi = w.bounds + (int64_t)i * 4;
   const double rmin = bi[0], rmax = bi[1], phimin = bi[2];
   const double phimin2 = phimin * phimin, phimin5 = phimin2 * phimin2 * phimin;
+  const RowF32 rf = row_f32<DIM>(ul, rmin, rmax, phimin5);
   const double alphai = w.alpha[i];
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
   // P_ij = tau/(m_i lambda_i) (b_ij F^H_j - b_ji F^H_i + (d^H_ij - d_ij)(U_j - U_i))
@@ -1113,7 +1196,7 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
 #pragma unroll
       for (int s = 0; s < S; ++s) P_trace[k * SP + s] = P[s];
     }
-    if (line_search_at_one<DIM>(p, ul, P, rmin, rmax, phimin5))
+    if (line_search_at_one<DIM>(p, ul, P, rmin, rmax, phimin5, rf))
       w.la[k] = 1.0;
     else if (k - k0 < 64)
       defer |= 1ull << (k - k0);
@@ -1191,6 +1274,7 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
   const double *bi = w.bounds + (int64_t)i * 4;
   const double rmin = bi[0], rmax = bi[1], phimin = bi[2];
   const double phimin2 = phimin * phimin, phimin5 = phimin2 * phimin2 * phimin;
+  const RowF32 rf = row_f32<DIM>(u, rmin, rmax, phimin5);
   uint64_t defer = 0;
   for (int64_t k = k0; k < k1; ++k) {
     if (m.col[k] == i) {
@@ -1210,7 +1294,7 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
         Pk[s] = P[s];
       }
     }
-    if (line_search_at_one<DIM>(p, u, P, rmin, rmax, phimin5))
+    if (line_search_at_one<DIM>(p, u, P, rmin, rmax, phimin5, rf))
       lout[k] = 1.0;
     else if (k - k0 < 64)
       defer |= 1ull << (k - k0);
