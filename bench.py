@@ -61,7 +61,10 @@ def parse_args():
     ap.add_argument("--workload", choices=("cylinder", "vortex", "batch", "serve", "cylinder3d", "nrbc", "adaptive",
                                            "ns"),
                     default="cylinder")
-    ap.add_argument("--requests", type=int, default=48, help="serve workload: requests in the trace")
+    ap.add_argument("--requests", type=int, default=128, help="serve workload: requests in the trace")
+    ap.add_argument("--serve-t-final", type=float, default=0.005, help="serve workload: t_final of every request")
+    ap.add_argument("--serve-max-vertices", type=float, default=4e6,
+                    help="serve workload: largest vertex count of the trace")
     ap.add_argument("--instances", type=int, default=256, help="batch workload: number of instances")
     ap.add_argument("--vertices", type=int, default=4_000_000)
     ap.add_argument("--start-step", type=int, default=1000,
@@ -651,56 +654,82 @@ def run_batch(args, dist):
 
 
 def run_serve(args, dist):
-    """Served stream: a seeded Poisson trace (mean 50 requests/s) of 2D Euler
-    solves on P1/Q1 cylinder meshes (vertices log-uniform in [1e4, 2.5e5],
-    Mach uniform in [1.5, 4]) to t_final = 0.25, served with continuous
-    batching in mixed precision; against the same requests solved one after
-    another with the plain FP64 path (their service times replayed against the
-    same arrivals)."""
+    """Served stream: a seeded Poisson trace (mean 50 requests/s, seed 5) of 2D
+    Euler solves on P1/Q1 cylinder meshes (vertices log-uniform in [1e4, 4e6],
+    snapped to 16 log-spaced sizes; Mach uniform in [1.5, 4]) to a common
+    t_final, served with continuous batching -- merged mode (all running
+    requests are the instances of one batched context, repacked as they come
+    and go) in mixed precision and in FP64, and the per-request-stream mode --
+    against the same requests solved one after another with the plain FP64
+    path (their service times replayed against the same arrivals). Every run
+    is timed with clock samples."""
     import torch
     from paper_2106_02159_gb300 import binding, serve
     torch.cuda.set_device(dist.local_rank)
     binding.build()
     if dist.rank != 0:
         return
-    reqs = serve.poisson_trace(args.requests, rate=50.0, seed=5, n_range=(1e4, 2.5e5), t_final=0.25)
+    reqs = serve.poisson_trace(args.requests, rate=50.0, seed=5, n_range=(1e4, args.serve_max_vertices),
+                               t_final=args.serve_t_final, size_grid=16, workers=16)
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.5 * free)
-    precision = binding.EH_PRECISION_MIXED if args.precision == "mixed" else binding.EH_PRECISION_FP64
     # warm the library and the caches once
-    serve.solve_alone(reqs[0], precision)
-    t0 = time.perf_counter()
-    results = serve.SolveServer(budget, precision=precision, device=dist.local_rank).run(reqs)
-    makespan = time.perf_counter() - t0
-    tts = np.array([r.time_to_solution for r in results])
-    dof = sum(r.n * 3 * r.steps for r in results)
+    serve.solve_alone(reqs[0], binding.EH_PRECISION_MIXED)
+    total_vertices = sum(r.mesh.n for r in reqs)
+
+    def served(mode, precision):
+        clocks = Clocks(dist.local_rank)
+        clocks.start()
+        t0 = time.perf_counter()
+        results = serve.SolveServer(budget, precision=precision, device=dist.local_rank, mode=mode).run(reqs)
+        makespan = time.perf_counter() - t0
+        clk = clocks.stop()
+        tts = np.array([r.time_to_solution for r in results])
+        dof = sum(r.n * 3 * r.steps for r in results)
+        return {"p50_s": float(np.percentile(tts, 50)), "p99_s": float(np.percentile(tts, 99)),
+                "aggregate": dof / makespan, "unit": UNIT, "makespan_s": makespan,
+                "served_requests_per_s": len(results) / makespan, "steps": int(sum(r.steps for r in results)),
+                "clocks": clk}
+
+    runs = {
+        "merged_mixed": served(binding.EH_BATCH_MERGED, binding.EH_PRECISION_MIXED),
+        "merged_fp64": served(binding.EH_BATCH_MERGED, binding.EH_PRECISION_FP64),
+        "streams_mixed": served(binding.EH_BATCH_PER_REQUEST_STREAMS, binding.EH_PRECISION_MIXED),
+    }
     # sequential plain FP64 baseline: each solve alone, then queueing replayed
+    clocks = Clocks(dist.local_rank)
+    clocks.start()
     service = []
     for r in reqs:
         a = time.perf_counter()
         _, steps = serve.solve_alone(r, binding.EH_PRECISION_FP64)
         service.append((time.perf_counter() - a, steps))
+    clk = clocks.stop()
     finish, seq_tts = 0.0, []
     for r, (svc, _) in zip(reqs, service):
         finish = max(finish, r.arrival) + svc
         seq_tts.append(finish - r.arrival)
     seq_tts = np.array(seq_tts)
     seq_dof = sum(r.mesh.n * 3 * st for r, (_, st) in zip(reqs, service))
+    runs["sequential_plain_fp64"] = {"p50_s": float(np.percentile(seq_tts, 50)),
+                                     "p99_s": float(np.percentile(seq_tts, 99)),
+                                     "aggregate": seq_dof / sum(x for x, _ in service), "unit": UNIT,
+                                     "makespan_s": finish, "clocks": clk}
+    main = runs["merged_mixed"]
     line = {
-        "metric": "p50/p99 time-to-solution (served)", "value": float(np.percentile(tts, 99)), "unit": "s",
-        "p50_s": float(np.percentile(tts, 50)), "p99_s": float(np.percentile(tts, 99)),
-        "n_gpus": 1, "steps": int(sum(r.steps for r in results)), "warmup": 1, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/f64",
-        "data": "synthetic",
-        "aggregate": {"value": dof / makespan, "unit": UNIT, "makespan_s": makespan},
-        "load": {"offered_requests_per_s": 50.0, "served_requests_per_s": len(results) / makespan},
-        "config": {"workload": f"served stream: {len(reqs)} requests, Poisson arrivals (mean 50/s, seed 5), "
-                               "P1/Q1 cylinder meshes, vertices log-uniform in [1e4, 2.5e5], Mach uniform in "
-                               "[1.5, 4], t_final 0.25, continuous batching (admission by free device memory, "
-                               "one context and stream per request, states resident)",
-                   "hbm_budget_bytes": budget, "precision": args.precision},
-        "sequential_plain_fp64": {"p50_s": float(np.percentile(seq_tts, 50)), "p99_s": float(np.percentile(seq_tts, 99)),
-                                  "aggregate": seq_dof / sum(x for x, _ in service), "unit": UNIT},
+        "metric": "p50/p99 time-to-solution (served)", "value": main["p99_s"], "unit": "s",
+        "p50_s": main["p50_s"], "p99_s": main["p99_s"], "n_gpus": 1, "steps": main["steps"], "warmup": 1,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "aggregate": {"value": main["aggregate"], "unit": UNIT, "makespan_s": main["makespan_s"]},
+        "load": {"offered_requests_per_s": 50.0, "served_requests_per_s": main["served_requests_per_s"]},
+        "clocks": main["clocks"],
+        "config": {"workload": f"served stream: {len(reqs)} requests, Poisson arrivals (mean 50/s, seed 5), P1/Q1 "
+                               f"cylinder meshes, vertices log-uniform in [1e4, {args.serve_max_vertices:.0e}] "
+                               f"(16 log-spaced sizes), Mach uniform in [1.5, 4], t_final {args.serve_t_final:g}, "
+                               "admission by device memory, states resident, merged continuous batching",
+                   "requests": len(reqs), "total_vertices": total_vertices,
+                   "distinct_sizes": sorted({r.mesh.n for r in reqs}), "hbm_budget_bytes": budget},
+        "runs": runs,
     }
     print(json.dumps(line), flush=True)
 

@@ -309,6 +309,11 @@ eh_status eh_set_instances(eh_ctx *ctx, int32_t ninst, const int64_t *row_offset
  * NULL). Synchronises. */
 eh_status eh_get_instances(eh_ctx *ctx, double *t, double *last_dt, double *stage_bound);
 
+/* Per-instance number of SSPRK(3,3) steps taken with tau > 0 since
+ * eh_set_instances (a finished instance stops counting), steps[ninst] (host).
+ * Synchronises. */
+eh_status eh_get_instance_steps(eh_ctx *ctx, int64_t *steps);
+
 /* Launch-shape autotuner: runs 'steps_per_candidate' SSPRK(3,3) steps for
  * every candidate -- 64, 128 and 256 rows per block, and for the grid-stride
  * kernels (EH_KERNEL_LIM1, _PASS, _FINAL) one thread per row or at most 256,
@@ -336,15 +341,31 @@ eh_status eh_set_launch_shape(eh_ctx *ctx, int32_t kernel, int32_t threads_per_b
 int32_t eh_launches_per_step(const eh_ctx *ctx);
 
 /* ------------------------------------------------------------------------
- * Served stream of independent solves (continuous batching, one device).
+ * Served stream of independent solves (continuous batching, one device; the
+ * paper has no counterpart -- it serves the method's many-solve use).
  * A batch admits requests first come, first served while their device memory
- * fits a budget next to the requests already running (the first request is
- * always admitted); each admitted request keeps its mesh and state resident in
- * a context of its own, on that context's own stream, configured as cfg. The
- * caller owns the batch and frees it with eh_batch_destroy; the batch owns the
- * requests' contexts. Not thread-safe: one host thread per batch.
+ * fits a budget next to the requests already running and the device's free
+ * memory; each admitted request keeps its mesh and state resident on the
+ * device. Two modes (eh_batch_set_mode):
+ *  - EH_BATCH_MERGED (default): the running requests are the instances of ONE
+ *    batched context (as eh_set_instances on their block-diagonal union), so
+ *    a step of the batch is a single set of kernel launches -- one CUDA-graph
+ *    replay -- covering all of them, each with its own CFL step and final
+ *    time. Requests join and leave between eh_batch_advance calls: the union
+ *    is rebuilt on the device ("repacked") from the requests' resident data and
+ *    current states; a request that reached its final time inside an advance
+ *    stays frozen (tau = 0) until the next repack. Each request's result is the
+ *    same, bit for bit, as solving it alone (per-row arithmetic, per-instance
+ *    tau). One context steps every member: a device-side failure (e.g. a
+ *    non-admissible state) stops every request in the batch at that advance.
+ *  - EH_BATCH_PER_REQUEST_STREAMS: every request has a context of its own on
+ *    its own stream, and an advance launches one step of each request in turn
+ *    (their launches overlap on the device); a request's failure stops only it.
+ * The caller owns the batch and frees it with eh_batch_destroy; the batch owns
+ * the requests' device data. Not thread-safe: one host thread per batch.
  * ------------------------------------------------------------------------ */
 typedef struct eh_batch eh_batch;
+enum { EH_BATCH_MERGED = 0, EH_BATCH_PER_REQUEST_STREAMS = 1 };
 
 /* Device bytes a context needs for a mesh of n nodes and nnz CSR entries in
  * dimension dim and precision EH_PRECISION_* (the estimate admission uses:
@@ -353,37 +374,58 @@ typedef struct eh_batch eh_batch;
  * nnz < n. */
 eh_status eh_estimate_device_bytes(int32_t dim, int32_t precision, int32_t n, int64_t nnz, uint64_t *bytes);
 
-/* Creates an empty batch. cfg as for eh_create, with cfg->stream NULL (every
- * request runs on a stream of its own); hbm_budget_bytes > 0 is the device
+/* Device bytes the admission of a batch in 'mode' (EH_BATCH_*) counts for a
+ * request of n nodes, nnz CSR entries and n_bnd boundary nodes: the
+ * eh_estimate_device_bytes estimate, plus in merged mode the request's own
+ * resident copy of its mesh data and state. Host only. EH_ERR_INVALID_ARG for
+ * bad sizes, dimension, precision or mode. */
+eh_status eh_estimate_request_bytes(int32_t dim, int32_t precision, int32_t mode, int32_t n, int64_t nnz,
+                                    int32_t n_bnd, uint64_t *bytes);
+
+/* Creates an empty batch in merged mode. cfg as for eh_create, with
+ * cfg->stream NULL (the batch's context, and in per-request mode every
+ * request, runs on a stream of its own); hbm_budget_bytes > 0 is the device
  * memory the running requests may hold together. EH_ERR_INVALID_ARG
  * otherwise; *out is NULL on error. */
 eh_status eh_batch_create(const eh_config *cfg, uint64_t hbm_budget_bytes, eh_batch **out);
+
+/* Selects EH_BATCH_MERGED or EH_BATCH_PER_REQUEST_STREAMS; only while the
+ * batch holds no request (EH_ERR_STATE otherwise, EH_ERR_INVALID_ARG for an
+ * unknown mode). */
+eh_status eh_batch_set_mode(eh_batch *b, int32_t mode);
+
+/* Number of times a merged batch rebuilt its context so far. */
+eh_status eh_batch_repacks(const eh_batch *b, int64_t *repacks);
 
 /* Admits one request: a mesh (arguments as eh_upload_mesh, host pointers,
  * copied), its initial state U0[S][n] (host, copied; the boundary
  * post-processing of Sec. 4 is applied to it) and its end time t_final > 0
  * (the last step is shortened to land on it, as eh_set_instances). *ticket
- * receives the request's identifier. EH_ERR_OOM: the request does not fit the
- * budget now (nothing changed; admit it after a poll has freed memory);
- * errors of eh_upload_mesh / eh_set_state otherwise (nothing kept). */
+ * receives the request's identifier. The request's device bytes (the
+ * admission estimate; in merged mode also the request's own copy of its mesh)
+ * must fit next to the running requests in the budget and in the device's
+ * free memory: EH_ERR_OOM means "not now" (nothing changed; admit it after a
+ * poll has freed memory); a request larger than the whole budget is refused
+ * with EH_ERR_INVALID_ARG. Errors of eh_upload_mesh / eh_set_state otherwise
+ * (nothing kept). */
 eh_status eh_batch_admit(eh_batch *b, int32_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
                          const double *cij, const double *mij, const double *mi, int32_t n_bnd,
                          const int32_t *bnd_node, const int32_t *bnd_kind, const double *bnd_normal,
                          const double *bnd_state, const double *U0, double t_final, int64_t *ticket);
 
-/* Launches 'steps' >= 1 SSPRK(3,3) steps (CUDA-graph replays) for every
- * running request, one step of each request in turn, each on its own stream
- * (the requests overlap on the device); then synchronises every running
- * request and marks those that reached t_final, or failed, as finished.
- * *n_finished (may be NULL) receives the number of finished requests not yet
- * polled. A request's failure does not stop the others: eh_batch_poll returns
- * its status. */
+/* Advances every running request by 'steps' >= 1 SSPRK(3,3) steps. Merged
+ * mode: first rebuilds the batch's context if requests joined or finished
+ * since the last advance, then replays its CUDA graph 'steps' times (one set
+ * of launches per step for all requests). Per-request mode: one step of each
+ * request in turn, on its own stream. Then synchronises and marks the
+ * requests that reached t_final, or failed, as finished. *n_finished (may be
+ * NULL) receives the number of finished requests not yet polled. */
 eh_status eh_batch_advance(eh_batch *b, int32_t steps, int32_t *n_finished);
 
 /* *done = 0 while the request runs. Once it has finished: *done = 1, U_out
  * (host, [S][n], or NULL) receives its state, t (may be NULL) its simulated
- * time, steps (may be NULL) the steps launched for it; its context is freed
- * and its ticket retired. Returns the status that stopped the request
+ * time, steps (may be NULL) the steps it took (tau > 0); its device data is
+ * freed and its ticket retired. Returns the status that stopped the request
  * (EH_OK when it reached t_final); EH_ERR_INVALID_ARG for an unknown ticket. */
 eh_status eh_batch_poll(eh_batch *b, int64_t ticket, int32_t *done, double *U_out, double *t, int64_t *steps);
 

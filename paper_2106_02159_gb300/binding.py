@@ -26,6 +26,7 @@ EH_OK, EH_ERR_INVALID_ARG, EH_ERR_OOM, EH_ERR_BAD_MESH = 0, 1, 2, 3
 EH_ERR_NOT_ADMISSIBLE, EH_ERR_CFL, EH_ERR_CUDA, EH_ERR_STATE = 4, 5, 6, 7
 EH_BC_SLIP, EH_BC_DIRICHLET, EH_BC_DO_NOTHING, EH_BC_CHARACTERISTIC, EH_BC_GODUNOV = 1, 2, 3, 4, 5
 EH_PRECISION_FP64, EH_PRECISION_MIXED = 0, 1
+EH_BATCH_MERGED, EH_BATCH_PER_REQUEST_STREAMS = 0, 1
 (EH_TRACE_D_IJ, EH_TRACE_ALPHA, EH_TRACE_U_LOW, EH_TRACE_F_HIGH, EH_TRACE_BOUNDS, EH_TRACE_L_PASS1,
  EH_TRACE_U_PASS1, EH_TRACE_TAU, EH_TRACE_TAU_BOUND, EH_TRACE_P_PASS1, EH_TRACE_L_LAST) = range(11)
 
@@ -37,7 +38,8 @@ EXPORTS = ("eh_config_default", "eh_create", "eh_upload_mesh", "eh_set_state", "
            "eh_get_instances", "eh_autotune", "eh_get_block_sizes", "eh_get_rows_per_sm", "eh_set_launch_shape",
            "eh_step_adaptive", "eh_set_viscosity", "eh_parabolic_step", "eh_step_ns",
            "eh_estimate_device_bytes", "eh_batch_create", "eh_batch_admit", "eh_batch_advance", "eh_batch_poll",
-           "eh_batch_active", "eh_batch_last_error", "eh_batch_destroy")
+           "eh_batch_active", "eh_batch_last_error", "eh_batch_destroy", "eh_batch_set_mode", "eh_batch_repacks",
+           "eh_get_instance_steps", "eh_estimate_request_bytes")
 CFL_NOALLOC_MAX_ROWS = 1 << 23
 KERNEL_NAMES = ("prep", "visc", "low", "tau", "lim1", "pass", "final", "lsearch")
 
@@ -138,6 +140,10 @@ def load(path: str | None = None):
     lib.eh_batch_last_error.argtypes = [vp]
     lib.eh_batch_last_error.restype = ctypes.c_char_p
     lib.eh_batch_destroy.argtypes = [vp]
+    lib.eh_batch_set_mode.argtypes = [vp, i32]
+    lib.eh_estimate_request_bytes.argtypes = [i32, i32, i32, i32, i64, i32, ctypes.POINTER(u64)]
+    lib.eh_batch_repacks.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.eh_get_instance_steps.argtypes = [vp, vp]
     lib.eh_batch_destroy.restype = None
     for name in EXPORTS:
         if name not in ("eh_config_default", "eh_destroy", "eh_launches_per_step", "eh_last_error",
@@ -188,11 +194,22 @@ def estimate_device_bytes(dim, precision, n, nnz, lib=None) -> int:
     return int(out.value)
 
 
+def estimate_request_bytes(dim, precision, mode, n, nnz, n_bnd, lib=None) -> int:
+    """Device bytes a batch in ``mode`` counts for a request (eh_estimate_request_bytes)."""
+    lib = lib or load()
+    out = ctypes.c_uint64(0)
+    st = lib.eh_estimate_request_bytes(int(dim), int(precision), int(mode), int(n), int(nnz), int(n_bnd),
+                                       ctypes.byref(out))
+    if st != EH_OK:
+        raise EulerError(st, "eh_estimate_request_bytes: invalid arguments")
+    return int(out.value)
+
+
 class Batch:
     """A served stream of independent solves (eh_batch_create ... eh_batch_destroy)."""
 
     def __init__(self, hbm_budget_bytes, dim=2, gamma=1.4, cfl=0.5, limiter_passes=2, bound_relaxation=False,
-                 device=0, precision=EH_PRECISION_FP64, lib=None):
+                 device=0, precision=EH_PRECISION_FP64, mode=EH_BATCH_MERGED, lib=None):
         self.lib = lib or load()
         cfg = Config()
         self.lib.eh_config_default(ctypes.byref(cfg))
@@ -206,6 +223,13 @@ class Batch:
             raise EulerError(st, f"eh_batch_create failed: {self.lib.eh_status_string(st).decode()}")
         self.b = b
         self.n_of = {}
+        self._check(self.lib.eh_batch_set_mode(self.b, int(mode)), "eh_batch_set_mode")
+
+    def repacks(self) -> int:
+        """Times a merged batch rebuilt its context."""
+        r = ctypes.c_int64(0)
+        self._check(self.lib.eh_batch_repacks(self.b, ctypes.byref(r)), "eh_batch_repacks")
+        return int(r.value)
 
     def _check(self, st, what):
         if st != EH_OK:
@@ -450,7 +474,9 @@ class Solver:
         k = getattr(self, "ninst", 1)
         t, dt, b = np.empty(k), np.empty(k), np.empty((3, k))
         self._check(self.lib.eh_get_instances(self.ctx, _p(t), _p(dt), _p(b)), "eh_get_instances")
-        return dict(t=t, last_dt=dt, stage_bound=b)
+        steps = np.empty(k, dtype=np.int64)
+        self._check(self.lib.eh_get_instance_steps(self.ctx, _p(steps)), "eh_get_instance_steps")
+        return dict(t=t, last_dt=dt, stage_bound=b, steps=steps)
 
     def autotune(self, steps_per_candidate=2) -> dict:
         chosen = np.zeros(len(KERNEL_NAMES), dtype=np.int32)

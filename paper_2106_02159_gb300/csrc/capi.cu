@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/euler_hyp.h"
+#include "internal.cuh"
 #include "kernels.cuh"
 #include "parabolic.cuh"
 
@@ -75,6 +76,11 @@ struct eh_ctx {
   double *host_scal = nullptr;  // pinned, two doubles
   int *host_ctl = nullptr;      // pinned, the CG control pair
   int cg_last[3] = {8, 8, 8};   // iterations of the last velocity, energy and low-order solves
+  // a request of a merged served batch: mesh data and state on the device, no
+  // work arrays (it is stepped inside the batch's own context)
+  bool static_only = false;
+  // a merged batch's context: the sizes its arrays were allocated for
+  int64_t cap_n = 0, cap_nnz = 0, cap_bnd = 0;
 };
 
 namespace {
@@ -305,13 +311,15 @@ eh_status setup_instances(eh_ctx *c, int ninst, const int64_t *off, const double
     return EH_OK;
   };
   eh_status st;
-  void *p_off, *p_tau, *p_bound, *p_t, *p_tf, *p_bits, *p_inst = nullptr;
+  void *p_off, *p_tau, *p_bound, *p_t, *p_tf, *p_bits, *p_steps, *p_inst = nullptr;
   if ((st = ialloc(&p_off, sizeof(int64_t) * (ninst + 1)))) return st;
   if ((st = ialloc(&p_tau, sizeof(double) * ninst))) return st;
   if ((st = ialloc(&p_bound, sizeof(double) * 3 * ninst))) return st;
   if ((st = ialloc(&p_t, sizeof(double) * ninst))) return st;
   if ((st = ialloc(&p_tf, sizeof(double) * ninst))) return st;
   if ((st = ialloc(&p_bits, sizeof(unsigned long long) * ninst))) return st;
+  if ((st = ialloc(&p_steps, sizeof(unsigned long long) * ninst))) return st;
+  CUDA_TRY(c, cudaMemset(p_steps, 0, sizeof(unsigned long long) * ninst));
   std::vector<unsigned long long> inf_bits(ninst, 0x7FF0000000000000ull);
   CUDA_TRY(c, cudaMemcpy(p_bits, inf_bits.data(), sizeof(unsigned long long) * ninst, cudaMemcpyHostToDevice));
   std::vector<double> tfinal(ninst, INFINITY);
@@ -351,10 +359,137 @@ eh_status setup_instances(eh_ctx *c, int ninst, const int64_t *off, const double
   c->wk.t_inst = (double *)p_t;
   c->wk.tfinal_inst = (double *)p_tf;
   c->wk.bound_bits = (unsigned long long *)p_bits;
+  c->wk.steps_inst = (unsigned long long *)p_steps;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
+  return EH_OK;
+}
+
+// Device arrays of the static mesh data for (up to) n nodes, nnz entries and
+// n_bnd boundary nodes; sets the MeshView pointers (contents not written).
+eh_status alloc_static(eh_ctx *c, int64_t n, int64_t nnz, int64_t n_bnd) {
+  const int dim = c->cfg.dim, S = S_of(c);
+  MeshView &m = c->mv;
+  eh_status st;
+  int64_t *row = nullptr;
+  int32_t *col = nullptr, *tr = nullptr, *bidx = nullptr, *bnode = nullptr, *bkind = nullptr;
+  double *cij = nullptr, *cn = nullptr, *cinv = nullptr, *betat = nullptr, *mi = nullptr, *imi = nullptr,
+         *relax = nullptr, *lam = nullptr, *bnorm = nullptr, *bstate = nullptr;
+  unsigned char *isb = nullptr;
+  if ((st = dalloc(c, &row, (size_t)n + 1)) || (st = dalloc(c, &col, (size_t)nnz)) ||
+      (st = dalloc(c, &tr, (size_t)nnz)) || (st = dalloc(c, &cij, (size_t)dim * nnz)) ||
+      (st = dalloc(c, &cn, (size_t)nnz)) || (st = dalloc(c, &cinv, (size_t)nnz)) ||
+      (st = dalloc(c, &betat, (size_t)nnz)) || (st = dalloc(c, &mi, (size_t)n)) || (st = dalloc(c, &imi, (size_t)n)) ||
+      (st = dalloc(c, &relax, (size_t)n)) || (st = dalloc(c, &lam, (size_t)n)) || (st = dalloc(c, &isb, (size_t)n)) ||
+      (st = dalloc(c, &bidx, (size_t)n)) || (st = dalloc(c, &bnode, (size_t)n_bnd)) ||
+      (st = dalloc(c, &bkind, (size_t)n_bnd)) || (st = dalloc(c, &bnorm, (size_t)dim * n_bnd)) ||
+      (st = dalloc(c, &bstate, (size_t)S * n_bnd)))
+    return st;
+  m.row_ptr = row;
+  m.col = col;
+  m.tr = tr;
+  m.cij = cij;
+  m.cn = cn;
+  m.cinv = cinv;
+  m.betat = betat;
+  m.mi = mi;
+  m.inv_mi = imi;
+  m.relax = relax;
+  m.lam = lam;
+  m.isb = isb;
+  m.bnd_index = bidx;
+  m.bnd_node = bnode;
+  m.bnd_kind = bkind;
+  m.bnd_normal = bnorm;
+  m.bnd_state = bstate;
+  m.vcij = cij;
+  m.vcn = cn;
+  m.vcinv = cinv;
+  if (mixed(c)) {  // FP32 c_ij, |c_ij|, 1/|c_ij|
+    float *fc = nullptr, *fn = nullptr, *fi = nullptr;
+    if ((st = dalloc(c, &fc, (size_t)dim * nnz)) || (st = dalloc(c, &fn, (size_t)nnz)) ||
+        (st = dalloc(c, &fi, (size_t)nnz)))
+      return st;
+    m.vcij = fc;
+    m.vcn = fn;
+    m.vcinv = fi;
+  }
+  return EH_OK;
+}
+
+// The per-stage work arrays for (up to) n nodes and nnz entries, and the
+// state buffers. A static-only context (a request of a merged served batch)
+// gets the state only: it is stepped as part of the batch's context.
+eh_status alloc_work(eh_ctx *c, int64_t n, int64_t nnz) {
+  const int dim = c->cfg.dim, S = S_of(c), SP = SP_of(c);
+  Work &w = c->wk;
+  eh_status st;
+#define ALLOC(ptr, cnt) \
+  if ((st = dalloc(c, &ptr, (size_t)(cnt))) != EH_OK) return st;
+  ALLOC(c->U, (size_t)S * n);
+  w.st = c->st;
+  if (c->static_only) return EH_OK;
+  ALLOC(w.rec, (size_t)n * REC_MAX);
+  ALLOC(c->stat_part, (size_t)7 * STAT_BLOCKS);
+  ALLOC(c->stat_out, 8);
+  ALLOC(w.alpha, n);
+  ALLOC(w.rough, n);
+  ALLOC(w.rough2, n);
+  ALLOC(w.inc, (size_t)n * SP);
+  if (mixed(c)) {
+    // FP32 node record, packed w_ij/a_ij/d_ij slots and F^H
+    float *f_rec, *f_w, *f_fh;
+    ALLOC(f_rec, (size_t)n * VREC_MAX);
+    ALLOC(f_fh, (size_t)n * SP);
+    static_assert(EdgeLayout<2, float>::packed && EdgeLayout<3, float>::packed, "FP32 edge slots are packed");
+    constexpr int spw_f = EdgeLayout<2, float>::SPW;
+    ALLOC(f_w, (size_t)nnz * spw_f);
+    w.va = nullptr;
+    w.vrec = f_rec;
+    w.vw = f_w;
+    w.vd = nullptr;
+    w.vFH = f_fh;
+  } else {
+    ALLOC(w.FH, (size_t)n * SP);
+    double *d_a = nullptr;
+    if (dim == 3) {  // packed slots [w (5), a, d, 0]
+      constexpr int spw3 = EdgeLayout<3, double>::SPW;
+      ALLOC(w.w, (size_t)nnz * spw3);
+      w.d = nullptr;
+    } else {
+      constexpr int spw2 = EdgeLayout<2, double>::SPW;
+      ALLOC(w.w, (size_t)nnz * spw2);
+      ALLOC(w.d, nnz);
+      ALLOC(d_a, nnz);
+    }
+    w.va = d_a;
+    w.vrec = w.rec;
+    w.vw = w.w;
+    w.vd = w.d;
+    w.vFH = w.FH;
+  }
+  ALLOC(w.bounds, (size_t)n * 4);
+  ALLOC(w.UL, (size_t)n * SP);
+  ALLOC(w.Ua, (size_t)n * SP);
+  ALLOC(w.Ub, (size_t)n * SP);
+  ALLOC(w.P, (size_t)nnz * SP);
+  ALLOC(w.la, nnz);
+  ALLOC(w.lb, nnz);
+  ALLOC(w.lsq, nnz);  // every entry can be queued once per pass
+  ALLOC(w.lsq_count, LSQ_SLOTS);
+  w.lsq_cap = (unsigned)nnz;
+  // iterations: a small share of the searches; a full queue falls back to
+  // iterating in k_ls_deferred
+  w.lsq2_cap = (unsigned)std::max<int64_t>(nnz / 8, 4096);
+  ALLOC(w.lsq2, w.lsq2_cap);
+  ALLOC(w.lsq2_count, LSQ_SLOTS);
+  ALLOC(c->Usave, (size_t)S * n);
+  ALLOC(c->W, (size_t)S * n);
+#undef ALLOC
+  CUDA_TRY(c, cudaMemset(w.lsq_count, 0, sizeof(unsigned) * LSQ_SLOTS));
+  CUDA_TRY(c, cudaMemset(w.lsq2_count, 0, sizeof(unsigned) * LSQ_SLOTS));
   return EH_OK;
 }
 
@@ -565,166 +700,60 @@ eh_status eh_upload_mesh(eh_ctx *c, int32_t n, int64_t nnz, const int64_t *row_p
   }
   // ---- device arrays ----
   eh_status st;
-  MeshView &m = c->mv;
-  m.n = n;
-  m.nnz = nnz;
-  m.n_bnd = n_bnd;
-  int64_t *d_row = nullptr;
-  int32_t *d_col = nullptr, *d_tr = nullptr, *d_bidx = nullptr, *d_bkind = nullptr;
-  double *d_cij, *d_cn, *d_cinv, *d_betat, *d_mi, *d_imi, *d_relax, *d_lam, *d_bnorm = nullptr,
-      *d_bstate = nullptr;
-  unsigned char *d_isb;
-#define ALLOC(ptr, cnt) \
-  if ((st = dalloc(c, &ptr, (size_t)(cnt))) != EH_OK) { free_mesh(c); return st; }
-  ALLOC(d_row, n + 1);
-  ALLOC(d_col, nnz);
-  ALLOC(d_tr, nnz);
-  ALLOC(d_cij, (size_t)dim * nnz);
-  ALLOC(d_cn, nnz);
-  ALLOC(d_cinv, nnz);
-  ALLOC(d_betat, nnz);
-  ALLOC(d_mi, n);
-  ALLOC(d_imi, n);
-  ALLOC(d_relax, n);
-  ALLOC(d_lam, n);
-  ALLOC(d_isb, n);
-  ALLOC(d_bidx, n);
-  int32_t *d_bnode = nullptr;
-  ALLOC(d_bnode, n_bnd);
-  ALLOC(d_bkind, n_bnd);
-  ALLOC(d_bnorm, (size_t)dim * n_bnd);
-  ALLOC(d_bstate, (size_t)S * n_bnd);
-  const int SP = SP_of(c);
-  Work &w = c->wk;
-  ALLOC(w.rec, (size_t)n * REC_MAX);
-  ALLOC(c->stat_part, (size_t)7 * STAT_BLOCKS);
-  ALLOC(c->stat_out, 8);
-  ALLOC(w.alpha, n);
-  ALLOC(w.rough, n);
-  ALLOC(w.rough2, n);
-  ALLOC(w.inc, (size_t)n * SP);
-  float *f_cij = nullptr, *f_cn = nullptr, *f_cinv = nullptr;
-  if (c->cfg.precision == EH_PRECISION_MIXED) {
-    // FP32 c_ij, |c_ij|, 1/|c_ij|, node record, w_ij, d_ij and F^H
-    float *f_rec, *f_w, *f_d, *f_fh, *f_a;
-    ALLOC(f_cij, (size_t)dim * nnz);
-    ALLOC(f_cn, nnz);
-    ALLOC(f_cinv, nnz);
-    ALLOC(f_rec, (size_t)n * VREC_MAX);
-    ALLOC(f_fh, (size_t)n * SP);
-    // packed slots [w (S), a, d, 0...] in both dimensions
-    static_assert(EdgeLayout<2, float>::packed && EdgeLayout<3, float>::packed, "FP32 edge slots are packed");
-    constexpr int spw_f = EdgeLayout<2, float>::SPW;
-    ALLOC(f_w, (size_t)nnz * spw_f);
-    f_d = f_a = nullptr;
-    w.va = f_a;
-    w.vrec = f_rec;
-    w.vw = f_w;
-    w.vd = f_d;
-    w.vFH = f_fh;
-  } else {
-    ALLOC(w.FH, (size_t)n * SP);
-    double *d_a = nullptr;
-    if (dim == 3) {  // packed slots [w (5), a, d, 0]
-      constexpr int spw3 = EdgeLayout<3, double>::SPW;
-      ALLOC(w.w, (size_t)nnz * spw3);
-      w.d = nullptr;
-    } else {
-      constexpr int spw2 = EdgeLayout<2, double>::SPW;
-      ALLOC(w.w, (size_t)nnz * spw2);
-      ALLOC(w.d, nnz);
-      ALLOC(d_a, nnz);
-    }
-    w.va = d_a;
-    w.vrec = w.rec;
-    w.vw = w.w;
-    w.vd = w.d;
-    w.vFH = w.FH;
+  if ((st = alloc_static(c, n, nnz, n_bnd)) != EH_OK) {
+    free_mesh(c);
+    return st;
   }
-  ALLOC(w.bounds, (size_t)n * 4);
-  ALLOC(w.UL, (size_t)n * SP);
-  ALLOC(w.Ua, (size_t)n * SP);
-  ALLOC(w.Ub, (size_t)n * SP);
-  ALLOC(w.P, (size_t)nnz * SP);
-  ALLOC(w.la, nnz);
-  ALLOC(w.lb, nnz);
-  ALLOC(w.lsq, nnz);  // every entry can be queued once per pass
-  ALLOC(w.lsq_count, LSQ_SLOTS);
-  w.lsq_cap = (unsigned)nnz;
-  // iterations: a small share of the searches; a full queue falls back to
-  // iterating in k_ls_deferred
-  w.lsq2_cap = (unsigned)std::max<int64_t>(nnz / 8, 4096);
-  ALLOC(w.lsq2, w.lsq2_cap);
-  ALLOC(w.lsq2_count, LSQ_SLOTS);
-  ALLOC(c->Usave, (size_t)S * n);
-  ALLOC(c->U, (size_t)S * n);
-  ALLOC(c->W, (size_t)S * n);
-#undef ALLOC
-  w.st = c->st;
-  auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+  MeshView &m = c->mv;
+  auto up = [&](const void *dst, const void *src, size_t bytes) -> cudaError_t {
     if (bytes == 0) return cudaSuccess;
-    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    return cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice);
   };
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = up(d_row, row_ptr, sizeof(int64_t) * (n + 1));
-  if (e == cudaSuccess) e = up(d_col, col, sizeof(int32_t) * nnz);
-  if (e == cudaSuccess) e = up(d_tr, tr.data(), sizeof(int32_t) * nnz);
-  if (e == cudaSuccess) e = up(d_cij, cij, sizeof(double) * dim * nnz);
-  if (e == cudaSuccess) e = up(d_cn, cn.data(), sizeof(double) * nnz);
-  if (e == cudaSuccess) e = up(d_cinv, cinv.data(), sizeof(double) * nnz);
-  if (e == cudaSuccess) e = up(d_betat, betat.data(), sizeof(double) * nnz);
-  if (e == cudaSuccess) e = up(d_mi, mi, sizeof(double) * n);
-  if (e == cudaSuccess) e = up(d_imi, inv_mi.data(), sizeof(double) * n);
-  if (e == cudaSuccess) e = up(d_relax, relax.data(), sizeof(double) * n);
-  if (e == cudaSuccess) e = up(d_lam, lam.data(), sizeof(double) * n);
-  if (e == cudaSuccess) e = up(d_isb, isb.data(), n);
-  if (e == cudaSuccess) e = up(d_bidx, bidx.data(), sizeof(int32_t) * n);
-  if (e == cudaSuccess) e = up(d_bnode, bnd_node, sizeof(int32_t) * n_bnd);
-  if (e == cudaSuccess) e = up(d_bkind, bnd_kind, sizeof(int32_t) * n_bnd);
-  if (e == cudaSuccess) e = up(d_bnorm, bnd_normal, sizeof(double) * dim * n_bnd);
-  if (e == cudaSuccess && bnd_state) e = up(d_bstate, bnd_state, sizeof(double) * S * n_bnd);
-  if (e == cudaSuccess) e = cudaMemset(w.lsq_count, 0, sizeof(unsigned) * LSQ_SLOTS);
-  if (e == cudaSuccess) e = cudaMemset(w.lsq2_count, 0, sizeof(unsigned) * LSQ_SLOTS);
-  if (e == cudaSuccess && f_cij) {
+  if (e == cudaSuccess) e = up(m.row_ptr, row_ptr, sizeof(int64_t) * (n + 1));
+  if (e == cudaSuccess) e = up(m.col, col, sizeof(int32_t) * nnz);
+  if (e == cudaSuccess) e = up(m.tr, tr.data(), sizeof(int32_t) * nnz);
+  if (e == cudaSuccess) e = up(m.cij, cij, sizeof(double) * dim * nnz);
+  if (e == cudaSuccess) e = up(m.cn, cn.data(), sizeof(double) * nnz);
+  if (e == cudaSuccess) e = up(m.cinv, cinv.data(), sizeof(double) * nnz);
+  if (e == cudaSuccess) e = up(m.betat, betat.data(), sizeof(double) * nnz);
+  if (e == cudaSuccess) e = up(m.mi, mi, sizeof(double) * n);
+  if (e == cudaSuccess) e = up(m.inv_mi, inv_mi.data(), sizeof(double) * n);
+  if (e == cudaSuccess) e = up(m.relax, relax.data(), sizeof(double) * n);
+  if (e == cudaSuccess) e = up(m.lam, lam.data(), sizeof(double) * n);
+  if (e == cudaSuccess) e = up(m.isb, isb.data(), n);
+  if (e == cudaSuccess) e = up(m.bnd_index, bidx.data(), sizeof(int32_t) * n);
+  if (e == cudaSuccess) e = up(m.bnd_node, bnd_node, sizeof(int32_t) * n_bnd);
+  if (e == cudaSuccess) e = up(m.bnd_kind, bnd_kind, sizeof(int32_t) * n_bnd);
+  if (e == cudaSuccess) e = up(m.bnd_normal, bnd_normal, sizeof(double) * dim * n_bnd);
+  if (e == cudaSuccess && bnd_state) e = up(m.bnd_state, bnd_state, sizeof(double) * S * n_bnd);
+  if (e == cudaSuccess && mixed(c)) {
     std::vector<float> tmp((size_t)dim * nnz);
     for (size_t q = 0; q < tmp.size(); ++q) tmp[q] = (float)cij[q];
-    e = up(f_cij, tmp.data(), sizeof(float) * tmp.size());
+    e = up(m.vcij, tmp.data(), sizeof(float) * tmp.size());
     tmp.resize(nnz);
     for (int64_t k = 0; e == cudaSuccess && k < nnz; ++k) tmp[k] = (float)cn[k];
-    if (e == cudaSuccess) e = up(f_cn, tmp.data(), sizeof(float) * nnz);
+    if (e == cudaSuccess) e = up(m.vcn, tmp.data(), sizeof(float) * nnz);
     for (int64_t k = 0; e == cudaSuccess && k < nnz; ++k) tmp[k] = (float)cinv[k];
-    if (e == cudaSuccess) e = up(f_cinv, tmp.data(), sizeof(float) * nnz);
+    if (e == cudaSuccess) e = up(m.vcinv, tmp.data(), sizeof(float) * nnz);
   }
   if (e != cudaSuccess) {
     free_mesh(c);
     return fail(c, EH_ERR_CUDA, "mesh upload: %s", cudaGetErrorString(e));
   }
-  m.row_ptr = d_row;
-  m.col = d_col;
-  m.tr = d_tr;
-  m.cij = d_cij;
-  m.cn = d_cn;
-  m.cinv = d_cinv;
-  m.betat = d_betat;
-  m.mi = d_mi;
-  m.inv_mi = d_imi;
-  m.relax = d_relax;
-  m.lam = d_lam;
-  m.isb = d_isb;
-  m.vcij = f_cij ? (const void *)f_cij : (const void *)d_cij;
-  m.vcn = f_cn ? (const void *)f_cn : (const void *)d_cn;
-  m.vcinv = f_cinv ? (const void *)f_cinv : (const void *)d_cinv;
-  m.bnd_index = d_bidx;
-  m.bnd_node = d_bnode;
+  m.n = n;
+  m.nnz = nnz;
+  m.n_bnd = n_bnd;
   m.n_nonreflecting = 0;
   for (int b = 0; b < n_bnd; ++b)
     if (bnd_kind[b] == EH_BC_CHARACTERISTIC || bnd_kind[b] == EH_BC_GODUNOV) ++m.n_nonreflecting;
-  m.bnd_kind = d_bkind;
-  m.bnd_normal = d_bnorm;
-  m.bnd_state = d_bstate;
   c->n = n;
   c->nnz = nnz;
   c->n_bnd = n_bnd;
+  if ((st = alloc_work(c, n, nnz)) != EH_OK) {
+    free_mesh(c);
+    return st;
+  }
   const int64_t one[2] = {0, (int64_t)n};
   if ((st = setup_instances(c, 1, one, nullptr)) != EH_OK) {
     free_mesh(c);
@@ -869,8 +898,10 @@ eh_status eh_step_adaptive(eh_ctx *c, double cfl_max, double *dt_used, double *c
   if ((st = check_device_error(c))) return st;
   const size_t bytes = sizeof(double) * S_of(c) * c->n;
   double t0 = 0.0;
+  unsigned long long steps0 = 0;
   CUDA_TRY(c, cudaMemcpyAsync(c->Usave, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpy(&t0, c->wk.t_inst, sizeof(double), cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(&steps0, c->wk.steps_inst, sizeof(steps0), cudaMemcpyDeviceToHost));
   double cfl = cfl_max;
   int32_t r = 0;
   for (;;) {
@@ -892,6 +923,7 @@ eh_status eh_step_adaptive(eh_ctx *c, double cfl_max, double *dt_used, double *c
     // put the state and the time back; clear the failure
     CUDA_TRY(c, cudaMemcpyAsync(c->U, c->Usave, bytes, cudaMemcpyDeviceToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->wk.t_inst, &t0, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->wk.steps_inst, &steps0, sizeof(steps0), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(&c->st->err, 0, sizeof(int), c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (cfl <= 1.0) {  // cannot happen for an admissible state: U^L is then invariant-domain preserving
@@ -1256,6 +1288,18 @@ eh_status eh_get_instances(eh_ctx *c, double *t, double *last_dt, double *stage_
   return check_device_error(c);
 }
 
+eh_status eh_get_instance_steps(eh_ctx *c, int64_t *steps) {
+  eh_status st = require_ready(c);
+  if (st) return st;
+  if (!steps) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  std::vector<unsigned long long> tmp(c->ninst);
+  CUDA_TRY(c, cudaMemcpy(tmp.data(), c->wk.steps_inst, sizeof(unsigned long long) * c->ninst, cudaMemcpyDeviceToHost));
+  for (int k = 0; k < c->ninst; ++k) steps[k] = (int64_t)tmp[k];
+  return EH_OK;
+}
+
 eh_status eh_autotune(eh_ctx *c, int32_t steps_per_candidate, int32_t *chosen) {
   eh_status st = require_ready(c);
   if (st) return st;
@@ -1265,8 +1309,11 @@ eh_status eh_autotune(eh_ctx *c, int32_t steps_per_candidate, int32_t *chosen) {
   const size_t bytes = sizeof(double) * S_of(c) * c->n;
   const size_t tb = sizeof(double) * c->ninst;
   std::vector<double> t_saved(c->ninst);
+  std::vector<unsigned long long> steps_saved(c->ninst);
   CUDA_TRY(c, cudaMemcpyAsync(c->Usave, c->U, bytes, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpy(t_saved.data(), c->wk.t_inst, tb, cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(steps_saved.data(), c->wk.steps_inst, sizeof(unsigned long long) * c->ninst,
+                         cudaMemcpyDeviceToHost));
   // candidates: block sizes 64/128/256, each with the grid-stride kernels
   // (lim1, pass, final) at one thread per row or 8/16/24 warps in flight per SM
   const int cands[3] = {64, 128, 256};
@@ -1307,6 +1354,9 @@ eh_status eh_autotune(eh_ctx *c, int32_t steps_per_candidate, int32_t *chosen) {
   // put the state and the instance times back
   CUDA_TRY(c, cudaMemcpyAsync(c->U, c->Usave, bytes, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->wk.t_inst, t_saved.data(), tb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->wk.steps_inst, steps_saved.data(), sizeof(unsigned long long) * c->ninst,
+                              cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
@@ -1471,3 +1521,149 @@ eh_status eh_trace(eh_ctx *c, int what, double *host_out, int64_t count) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// merged served batch (internal.cuh)
+// ---------------------------------------------------------------------------
+namespace ehi {
+
+cudaStream_t stream_of(const eh_ctx *c) { return c->stream; }
+
+uint64_t part_bytes(int dim, int precision, int64_t n, int64_t nnz, int64_t n_bnd) {
+  const int64_t S = dim + 2;
+  int64_t per_entry = 4 + 4 + 8 * dim + 8 * 3, per_node = 8 + 8 * 4 + 1 + 4 + 8 * S + 8 * 4;
+  if (precision == EH_PRECISION_MIXED) per_entry += 4 * (dim + 2);
+  return (uint64_t)(per_entry * nnz + per_node * n + (8 + 8 * dim + 8 * S) * n_bnd) + (1u << 16);
+}
+
+eh_status create_part(const eh_config *cfg, cudaStream_t stream, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                      const int32_t *col, const double *cij, const double *mij, const double *mi, int32_t n_bnd,
+                      const int32_t *bnd_node, const int32_t *bnd_kind, const double *bnd_normal,
+                      const double *bnd_state, const double *U0, eh_ctx **out) {
+  *out = nullptr;
+  eh_config c2 = *cfg;
+  c2.stream = (void *)stream;
+  eh_ctx *p = nullptr;
+  eh_status st = eh_create(&c2, &p);
+  if (st) return st;
+  p->static_only = true;
+  if (!st) st = eh_upload_mesh(p, n, nnz, row_ptr, col, cij, mij, mi, n_bnd, bnd_node, bnd_kind, bnd_normal, bnd_state);
+  if (!st) st = eh_set_state(p, U0, 0);
+  if (!st) st = eh_apply_boundary_conditions(p);
+  if (!st) st = eh_synchronize(p);
+  if (st) {
+    eh_destroy(p);
+    return st;
+  }
+  *out = p;
+  return EH_OK;
+}
+
+eh_status assemble(eh_ctx *uni, eh_ctx *const *parts, int count, const double *t, const double *t_final) {
+  if (!uni || count < 1) return EH_ERR_INVALID_ARG;
+  CUDA_TRY(uni, cudaSetDevice(uni->device));
+  CUDA_TRY(uni, cudaStreamSynchronize(uni->stream));
+  const int dim = uni->cfg.dim, S = S_of(uni);
+  int64_t N = 0, NNZ = 0, NB = 0;
+  for (int k = 0; k < count; ++k) {
+    N += parts[k]->n;
+    NNZ += parts[k]->nnz;
+    NB += parts[k]->n_bnd;
+  }
+  if (N > INT32_MAX || NNZ >= ((int64_t)1 << 31)) return fail(uni, EH_ERR_INVALID_ARG, "merged batch too large");
+  eh_status st;
+  if (!uni->have_mesh || N > uni->cap_n || NNZ > uni->cap_nnz || NB > uni->cap_bnd) {
+    free_mesh(uni);
+    // room to grow: the next arrivals are placed without reallocating
+    uni->cap_n = std::min<int64_t>(INT32_MAX, N + N / 4 + 1024);
+    uni->cap_nnz = std::min<int64_t>(((int64_t)1 << 31) - 1, NNZ + NNZ / 4 + 16384);
+    uni->cap_bnd = NB + NB / 4 + 256;
+    if ((st = alloc_static(uni, uni->cap_n, uni->cap_nnz, uni->cap_bnd)) ||
+        (st = alloc_work(uni, uni->cap_n, uni->cap_nnz))) {
+      free_mesh(uni);
+      uni->cap_n = uni->cap_nnz = uni->cap_bnd = 0;
+      return st;
+    }
+  }
+  MeshView &m = uni->mv;
+  cudaStream_t s = uni->stream;
+  auto cp = [&](const void *dst, const void *src, size_t bytes) {
+    if (bytes) cudaMemcpyAsync(const_cast<void *>(dst), src, bytes, cudaMemcpyDeviceToDevice, s);
+  };
+  const size_t vsz = mixed(uni) ? sizeof(float) : sizeof(double);
+  int64_t ro = 0, eo = 0, bo = 0;
+  int nonrefl = 0;
+  for (int k = 0; k < count; ++k) {
+    const eh_ctx *p = parts[k];
+    const MeshView &pm = p->mv;
+    const int64_t n = p->n, nnz = p->nnz, nb = p->n_bnd;
+    launch_offset_copy<int64_t>(const_cast<int64_t *>(m.row_ptr) + ro, pm.row_ptr, n, eo, false, s);
+    launch_offset_copy<int32_t>(const_cast<int32_t *>(m.col) + eo, pm.col, nnz, (int32_t)ro, false, s);
+    launch_offset_copy<int32_t>(const_cast<int32_t *>(m.tr) + eo, pm.tr, nnz, (int32_t)eo, false, s);
+    for (int q = 0; q < dim; ++q) {
+      cp(m.cij + (int64_t)q * NNZ + eo, pm.cij + (int64_t)q * nnz, sizeof(double) * nnz);
+      cp((const char *)m.vcij + vsz * ((int64_t)q * NNZ + eo), (const char *)pm.vcij + vsz * (int64_t)q * nnz,
+         vsz * nnz);
+    }
+    cp(m.cn + eo, pm.cn, sizeof(double) * nnz);
+    cp(m.cinv + eo, pm.cinv, sizeof(double) * nnz);
+    cp(m.betat + eo, pm.betat, sizeof(double) * nnz);
+    if (mixed(uni)) {
+      cp((const char *)m.vcn + vsz * eo, pm.vcn, vsz * nnz);
+      cp((const char *)m.vcinv + vsz * eo, pm.vcinv, vsz * nnz);
+    }
+    cp(m.mi + ro, pm.mi, sizeof(double) * n);
+    cp(m.inv_mi + ro, pm.inv_mi, sizeof(double) * n);
+    cp(m.relax + ro, pm.relax, sizeof(double) * n);
+    cp(m.lam + ro, pm.lam, sizeof(double) * n);
+    cp(m.isb + ro, pm.isb, n);
+    launch_offset_copy<int32_t>(const_cast<int32_t *>(m.bnd_index) + ro, pm.bnd_index, n, (int32_t)bo, true, s);
+    launch_offset_copy<int32_t>(const_cast<int32_t *>(m.bnd_node) + bo, pm.bnd_node, nb, (int32_t)ro, false, s);
+    cp(m.bnd_kind + bo, pm.bnd_kind, sizeof(int32_t) * nb);
+    for (int q = 0; q < dim; ++q) cp(m.bnd_normal + (int64_t)q * NB + bo, pm.bnd_normal + (int64_t)q * nb, 8 * nb);
+    for (int c = 0; c < S; ++c) cp(m.bnd_state + (int64_t)c * NB + bo, pm.bnd_state + (int64_t)c * nb, 8 * nb);
+    for (int c = 0; c < S; ++c) cp(uni->U + (int64_t)c * N + ro, p->U + (int64_t)c * n, 8 * n);
+    nonrefl += pm.n_nonreflecting;
+    ro += n;
+    eo += nnz;
+    bo += nb;
+  }
+  CUDA_TRY(uni, cudaGetLastError());
+  CUDA_TRY(uni, cudaMemcpyAsync(const_cast<int64_t *>(m.row_ptr) + N, &NNZ, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(uni, cudaStreamSynchronize(s));
+  m.n = (int)N;
+  m.nnz = NNZ;
+  m.n_bnd = (int)NB;
+  m.n_nonreflecting = nonrefl;
+  uni->n = (int)N;
+  uni->nnz = NNZ;
+  uni->n_bnd = (int)NB;
+  std::vector<int64_t> off(count + 1, 0);
+  for (int k = 0; k < count; ++k) off[k + 1] = off[k] + parts[k]->n;
+  if ((st = setup_instances(uni, count, off.data(), t_final))) return st;
+  CUDA_TRY(uni, cudaMemcpy(uni->wk.t_inst, t, sizeof(double) * count, cudaMemcpyHostToDevice));
+  if ((st = reset_status(uni))) return st;
+  CUDA_TRY(uni, cudaStreamSynchronize(s));
+  uni->have_mesh = uni->have_state = true;
+  uni->steps = 0;
+  uni->last_stage_traced = false;
+  return EH_OK;
+}
+
+eh_status scatter(eh_ctx *uni, eh_ctx *const *parts, int count) {
+  CUDA_TRY(uni, cudaSetDevice(uni->device));
+  const int S = S_of(uni);
+  const int64_t N = uni->n;
+  int64_t ro = 0;
+  for (int k = 0; k < count; ++k) {
+    const int64_t n = parts[k]->n;
+    for (int c = 0; c < S; ++c)
+      CUDA_TRY(uni, cudaMemcpyAsync(parts[k]->U + (int64_t)c * n, uni->U + (int64_t)c * N + ro, 8 * n,
+                                    cudaMemcpyDeviceToDevice, uni->stream));
+    ro += n;
+  }
+  CUDA_TRY(uni, cudaStreamSynchronize(uni->stream));
+  return EH_OK;
+}
+
+}  // namespace ehi

@@ -16,6 +16,7 @@
 #include <cooperative_groups.h>
 #include <cooperative_groups/scan.h>
 
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -1098,7 +1099,10 @@ __global__ void __launch_bounds__(256) k_tau(MeshView m, Work w, int stage, doub
     if (k == 0) st->tau = tau;
   } else {
     if (w.tau_inst[k] > limit) atomicAdd(&st->cfl_violations, 1ull);
-    if (advance_time && stage == 2) w.t_inst[k] += w.tau_inst[k];
+    if (advance_time && stage == 2) {
+      w.t_inst[k] += w.tau_inst[k];
+      if (w.tau_inst[k] > 0.0) w.steps_inst[k] += 1ull;
+    }
   }
 }
 
@@ -1846,6 +1850,23 @@ void launch_state_stats(int n, const double *U, const double *mi, double *part, 
 template <int DIM> void launch_count_not_admissible(int n, const double *U, DevStatus *st, cudaStream_t s) {
   k_count_not_admissible<DIM><<<nblocks(n, 256), 256, 0, s>>>(n, U, st);
 }
+
+// dst[i] = src[i] + add (nonneg_only: only where src[i] >= 0; -1 entries
+// stay): the index arrays of one instance placed into a block-diagonal union
+template <typename I> __global__ void k_offset_copy(I *dst, const I *src, int64_t count, I add, int nonneg_only) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x) {
+    const I v = src[q];
+    dst[q] = (nonneg_only && v < 0) ? v : v + add;
+  }
+}
+template <typename I>
+void launch_offset_copy(I *dst, const I *src, int64_t count, I add, bool nonneg_only, cudaStream_t s) {
+  if (count <= 0) return;
+  const unsigned grid = (unsigned)std::min<int64_t>((count + 255) / 256, 152 * 16);
+  k_offset_copy<I><<<grid, 256, 0, s>>>(dst, src, count, add, nonneg_only ? 1 : 0);
+}
+template void launch_offset_copy<int32_t>(int32_t *, const int32_t *, int64_t, int32_t, bool, cudaStream_t);
+template void launch_offset_copy<int64_t>(int64_t *, const int64_t *, int64_t, int64_t, bool, cudaStream_t);
 
 #define EH_INSTANTIATE_T(DIM, T)                                                                                     \
   template void launch_prep<DIM, T>(const MeshView &, const Params &, const double *, const Work &, int, cudaStream_t); \

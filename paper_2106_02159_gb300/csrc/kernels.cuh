@@ -136,6 +136,7 @@ struct Work {
   double *bound_inst;  // [3][ninst] CFL bound of each stage and instance
   double *t_inst;   // [ninst]   simulated time of each instance
   double *tfinal_inst; // [ninst] end time of each instance (+inf: none)
+  unsigned long long *steps_inst;  // [ninst] steps taken with tau > 0
   DevStatus *st;
   // viscosity / flux precision arrays (aliases of rec, w, d, FH in FP64 mode;
   // float arrays in mixed mode)
@@ -209,5 +210,10 @@ template <int DIM> void launch_count_not_admissible(int n, const double *U, DevS
 constexpr int STAT_BLOCKS = 304;
 template <int DIM>
 void launch_state_stats(int n, const double *U, const double *mi, double *part, double *out, cudaStream_t s);
+
+// dst[i] = src[i] + add over count entries (nonneg_only: negative entries
+// copied unchanged); int32_t and int64_t
+template <typename I>
+void launch_offset_copy(I *dst, const I *src, int64_t count, I add, bool nonneg_only, cudaStream_t s);
 
 }  // namespace eh

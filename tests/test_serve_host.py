@@ -21,7 +21,7 @@ class FakeBatch:
     finishes after a number of steps proportional to its size."""
     log = []
 
-    def __init__(self, budget, dim=2, device=0, precision=0, lib=None):
+    def __init__(self, budget, dim=2, device=0, precision=0, mode=0, lib=None):
         self.budget, self.used, self.next, self.running = budget, 0, 1, {}
         FakeBatch.log = []
 
