@@ -66,6 +66,9 @@ def parse_args():
     ap.add_argument("--serve-max-vertices", type=float, default=4e6,
                     help="serve workload: largest vertex count of the trace")
     ap.add_argument("--instances", type=int, default=256, help="batch workload: number of instances")
+    ap.add_argument("--batch-small", action="store_true", help="batch workload: 32x8 to 64x16-cell instances only")
+    ap.add_argument("--start3d", type=int, default=100,
+                    help="cylinder3d workload: untimed steps from the inflow state before the warm-up")
     ap.add_argument("--vertices", type=int, default=4_000_000)
     ap.add_argument("--start-step", type=int, default=1000,
                     help="cylinder workload: untimed steps from the inflow state before the warm-up, so that the "
@@ -572,43 +575,52 @@ def run_ours(args, dist):
 
 
 def run_batch(args, dist):
-    """Batched sweep: independent Q1 cylinder instances (m log-uniform in
+    """Batched sweep (C4): independent Q1 cylinder instances (m log-uniform in
     [8, 256], i.e. 32x8 to 1024x256 cells; Mach uniform in [1.5, 4]; seed 4) in
     one context -- every kernel launch covers all instances, each with its own
-    CFL step -- against a per-instance launch loop of the plain FP64 path."""
+    CFL step -- in FP64 and in mixed precision, against a per-instance launch
+    loop of the plain FP64 path: the batching gain (batched FP64 / loop FP64)
+    and the precision gain (batched mixed / batched FP64) separately.
+    --batch-small: instances of 32x8 to 64x16 cells only (launch-bound)."""
     import torch
     from paper_2106_02159_gb300 import binding, meshes, workloads
     torch.cuda.set_device(dist.local_rank)
     binding.build()
-    sweep = workloads.batch_sweep(args.instances)
+    m_range = (8, 16) if args.batch_small else (8, 256)
+    sweep = workloads.batch_sweep(args.instances, m_range=m_range)
     inst = [workloads.cylinder_instance(m, mach) for m, mach in sweep]
     mesh, off, bs = meshes.concatenate([x[0] for x in inst], [x[2] for x in inst])
     U0 = np.concatenate([x[1] for x in inst], axis=1)
-    precision = binding.EH_PRECISION_MIXED if args.precision == "mixed" else binding.EH_PRECISION_FP64
     stream = torch.cuda.Stream()
-    s = binding.Solver(dim=2, precision=precision, device=dist.local_rank, stream=stream.cuda_stream)
-    s.upload_mesh(mesh, bs)
-    s.set_instances(off)
-    s.set_state(U0)
-    s.apply_boundary_conditions()
-    chosen = s.autotune(1)
-    rows_cap = s.rows_per_sm()
-    s.run(args.warmup)
-    s.synchronize()
-    clocks = Clocks(dist.local_rank)
-    dist.barrier()
-    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.run(args.steps)
-    e1.record(stream)
-    stream.synchronize()
-    clk = clocks.stop()
-    s.synchronize()
-    ms = dist.max(e0.elapsed_time(e1))
-    value = mesh.n * 3 * args.steps * dist.world / (ms * 1e-3)
-    diag = s.diagnostics()
-    s.close()
+    out = {}
+    for prec_name, precision in (("fp64", binding.EH_PRECISION_FP64), ("mixed", binding.EH_PRECISION_MIXED)):
+        s = binding.Solver(dim=2, precision=precision, device=dist.local_rank, stream=stream.cuda_stream)
+        s.upload_mesh(mesh, bs)
+        s.set_instances(off)
+        s.set_state(U0)
+        s.apply_boundary_conditions()
+        chosen = s.autotune(1)
+        rows_cap = s.rows_per_sm()
+        s.run(args.warmup)
+        s.synchronize()
+        clocks = Clocks(dist.local_rank)
+        dist.barrier()
+        clocks.start()
+        e0.record(stream)
+        s.run(args.steps)
+        e1.record(stream)
+        stream.synchronize()
+        clk = clocks.stop()
+        s.synchronize()
+        ms = dist.max(e0.elapsed_time(e1))
+        prof = kernel_profile(s, 2)
+        kernel_ms = sum(v[0] for v in prof.values()) / 2
+        out[prec_name] = {"value": mesh.n * 3 * args.steps * dist.world / (ms * 1e-3), "ms_per_step": ms / args.steps,
+                          "eager_kernel_ms_per_step": kernel_ms,
+                          "block_sizes": chosen, "rows_per_sm": rows_cap, "clocks": clk,
+                          "invariant_violations": s.diagnostics()["not_admissible"]}
+        s.close()
     # the baseline: a loop over instances, one plain FP64 context each
     loop = []
     for m, u, b in inst:
@@ -621,34 +633,38 @@ def run_batch(args, dist):
         q.run(args.warmup)
     torch.cuda.synchronize()
     loop_steps = max(1, args.steps // 4)
+    clocks = Clocks(dist.local_rank)
+    clocks.start()
     e0.record(stream)
     for _ in range(loop_steps):
         for q in loop:
             q.step(sync=False)
     e1.record(stream)
     stream.synchronize()
+    loop_clk = clocks.stop()
     loop_ms = dist.max(e0.elapsed_time(e1))
     loop_value = mesh.n * 3 * loop_steps * dist.world / (loop_ms * 1e-3)
     for q in loop:
         q.close()
     if dist.rank == 0:
         cells = [4 * m * m for m, _ in sweep]
+        main = out["mixed"]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/f64", "data": "synthetic",
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic", "clocks": main["clocks"],
             "config": {"workload": f"batched sweep: {len(inst)} independent Q1 cylinder instances, n_y = m cells "
-                                   f"(m log-uniform in [8, 256]), Mach uniform in [1.5, 4], seed 4, CFL 0.5, "
-                                   f"{args.precision}, one launch per kernel for all instances (CUDA graph)",
+                                   f"(m log-uniform in [{m_range[0]}, {m_range[1]}]), Mach uniform in [1.5, 4], "
+                                   "seed 4, CFL 0.5, one launch per kernel for all instances (CUDA graph)",
                        "instances": len(inst), "vertices": mesh.n, "nnz": mesh.nnz,
-                       "cells_min_max": [min(cells), max(cells)], "block_sizes": chosen,
-                       "rows_per_sm": rows_cap,
-                       "invariant_violations": diag["not_admissible"]},
-            "clocks": clk,
+                       "cells_min_max": [min(cells), max(cells)]},
+            "batched": out,
             "per_instance_loop": {"value": loop_value, "unit": UNIT, "steps": loop_steps,
-                                  "ms_per_step": loop_ms / loop_steps, "dtype": "f64",
+                                  "ms_per_step": loop_ms / loop_steps, "dtype": "f64", "clocks": loop_clk,
                                   "what": "one plain FP64 context per instance, eh_step launched instance after instance"},
-            "speedup_vs_loop": value / loop_value,
+            "batching_gain_fp64": out["fp64"]["value"] / loop_value,
+            "precision_gain_batched": out["mixed"]["value"] / out["fp64"]["value"],
+            "speedup_vs_loop": main["value"] / loop_value,
         }
         print(json.dumps(line), flush=True)
 
@@ -759,13 +775,19 @@ def run_cylinder3d(args, dist):
         s.upload_mesh(mesh, bs)
         s.set_state(U0)
         s.apply_boundary_conditions()
-        s.run(args.warmup)
+        # the timed steps start in the middle of the 200-step run (the bow
+        # shock and its wake have formed), not at the uniform inflow state
+        s.run(args.start3d + args.warmup)
         s.synchronize()
+        same = identical_edge_share(mesh, s.get_state())
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = Clocks(dist.local_rank)
+        clocks.start()
         e0.record(stream)
         s.run(args.steps)
         e1.record(stream)
         stream.synchronize()
+        clk = clocks.stop()
         ms = e0.elapsed_time(e1)
         s.synchronize()
         U = s.get_state()
@@ -777,7 +799,29 @@ def run_cylinder3d(args, dist):
         tot = sum(v[0] for v in prof.values())
         shares = {k: round(v[0] / tot, 4) for k, v in sorted(prof.items(), key=lambda t: -t[1][0]) if v[1]}
         out[prec] = dict(value=mesh.n * 3 * args.steps / (ms * 1e-3), ms_per_step=ms / args.steps,
-                         U=U, violations=viol, shares=shares)
+                         U=U, violations=viol, shares=shares, clocks=clk, identical_edge_share=same,
+                         roofline=roofline_of(prof, mesh, ms / args.steps, *peaks(), prec))
+        out[prec]["roofline"]["traffic"] = None
+        out[prec]["roofline"]["traffic_source"] = None
+        if prec == "fp64" and not args.no_perturbed:
+            # the same mesh from a seeded perturbed state: every entry in full
+            Up = workloads.perturbed_state(mesh, 2106, base=dict(rho=1.4, vel=(3.0, 0.0, 0.0), p=1.0))
+            s.set_state(Up)
+            s.apply_boundary_conditions()
+            s.run(2)
+            s.synchronize()
+            e0.record(stream)
+            s.run(args.steps)
+            e1.record(stream)
+            stream.synchronize()
+            pms = e0.elapsed_time(e1)
+            pprof = kernel_profile(s, 1)
+            out["developed"] = {"workload": "same mesh, seeded perturbed state: every entry evaluated in full",
+                                "identical_edge_share": identical_edge_share(mesh, s.get_state()),
+                                "ms_per_step": pms / args.steps, "value": mesh.n * 3 * args.steps / (pms * 1e-3),
+                                "roofline": roofline_of(pprof, mesh, pms / args.steps, *peaks(), prec)}
+            out["developed"]["roofline"]["traffic"] = None
+            out["developed"]["roofline"]["traffic_source"] = None
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -798,6 +842,12 @@ def run_cylinder3d(args, dist):
                           "l1_rel_error_vs_fp64_run": dict(zip(names, err.tolist())),
                           "after_steps": args.warmup + args.steps},
                 "invariant_violations": {"fp64": out["fp64"]["violations"], "mixed": out["mixed"]["violations"]},
+                "clocks": out["fp64"]["clocks"], "clocks_mixed": out["mixed"]["clocks"],
+                "identical_edge_share": out["fp64"]["identical_edge_share"],
+                "timed_steps": f"{args.start3d + args.warmup}..{args.start3d + args.warmup + args.steps} of the run "
+                               "from the inflow state",
+                "developed_flow": out.get("developed"),
+                "roofline": out["fp64"]["roofline"],
                 "kernel_shares": {"fp64": out["fp64"]["shares"], "mixed": out["mixed"]["shares"]}}
         print(json.dumps(line), flush=True)
 
@@ -976,6 +1026,8 @@ def run_ns(args, dist):
     s.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     iters, par_ms = [], 0.0
+    clocks = Clocks(dist.local_rank)
+    clocks.start()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         tau, info = s.step_ns()
@@ -991,6 +1043,7 @@ def run_ns(args, dist):
     e1.record(stream)
     stream.synchronize()
     euler_ms = e0.elapsed_time(e1) / (2 * args.steps)
+    clk = clocks.stop()
     d = s.diagnostics()
     line = {"metric": "DOF-updates/s per RK stage (Navier-Stokes steps)", "unit": UNIT, "n_gpus": 1,
             "value": mesh.n * 2 * 3 * args.steps / ns_wall, "steps": args.steps, "warmup": args.warmup,
@@ -1003,7 +1056,7 @@ def run_ns(args, dist):
             "euler_ms_per_ssprk3_step": euler_ms,
             "cg_iterations_velocity_energy_low": iters[-1],
             "cg_iterations_mean": [float(np.mean([it[q] for it in iters])) for q in range(3)],
-            "not_admissible": d["not_admissible"],
+            "not_admissible": d["not_admissible"], "clocks": clk,
             "timing": "host wall clock around synchronising calls (the CG loops read their control pair once per "
                       "batch of queued iterations)"}
     print(json.dumps(line), flush=True)

@@ -451,6 +451,7 @@ eh_status alloc_work(eh_ctx *c, int64_t n, int64_t nnz) {
     w.vw = f_w;
     w.vd = nullptr;
     w.vFH = f_fh;
+    ALLOC(w.G64, (size_t)n * SP);
   } else {
     ALLOC(w.FH, (size_t)n * SP);
     double *d_a = nullptr;
@@ -469,6 +470,7 @@ eh_status alloc_work(eh_ctx *c, int64_t n, int64_t nnz) {
     w.vw = w.w;
     w.vd = w.d;
     w.vFH = w.FH;
+    w.G64 = w.FH;
   }
   ALLOC(w.bounds, (size_t)n * 4);
   ALLOC(w.UL, (size_t)n * SP);

@@ -145,6 +145,8 @@ struct Work {
   void *vd;        // [nnz]      d_ij (not packed)
   void *va;        // [nnz]      (q(U_j) - q(U_i)) . c_ij of the indicator (not packed)
   void *vFH;       // [n][SP]    F^H_i / m_i
+  double *G64;     // [n][SP]    F^H_i / m_i in FP64 (mixed mode: the FP32 value widened once per node,
+                   //            so that k_lim1 converts nothing per entry; FP64 mode: alias of FH)
   // line searches that the fast check at l = 1 left open, run by
   // k_ls_deferred after each limiter pass (one queue, reused by every pass)
   int2 *lsq;             // [lsq_cap] (row i, entry k)

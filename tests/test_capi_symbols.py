@@ -63,3 +63,22 @@ def test_host_only_calls(lib):
         b2 = binding.Config.from_buffer_copy(bad)
         setattr(b2, field, value)
         assert lib.eh_create(ctypes.byref(b2), ctypes.byref(out)) == binding.EH_ERR_INVALID_ARG, field
+
+
+def test_request_bytes_by_batch_mode(lib):
+    """Merged mode counts a request's resident copy of its mesh on top of the
+    per-context estimate; bad sizes or modes are refused (host only)."""
+    est, merged, streams = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    assert lib.eh_estimate_device_bytes(2, 0, 5000, 45000, ctypes.byref(est)) == binding.EH_OK
+    assert lib.eh_estimate_request_bytes(2, 0, binding.EH_BATCH_PER_REQUEST_STREAMS, 5000, 45000, 300,
+                                         ctypes.byref(streams)) == binding.EH_OK
+    assert lib.eh_estimate_request_bytes(2, 0, binding.EH_BATCH_MERGED, 5000, 45000, 300,
+                                         ctypes.byref(merged)) == binding.EH_OK
+    assert streams.value == est.value
+    assert est.value < merged.value < 2 * est.value
+    for args in ((2, 0, 7, 5000, 45000, 300), (2, 0, 0, 5000, 45000, -1), (3, 9, 0, 10, 10, 0)):
+        assert lib.eh_estimate_request_bytes(*args, ctypes.byref(merged)) == binding.EH_ERR_INVALID_ARG, args
+    assert lib.eh_batch_set_mode(None, 0) == binding.EH_ERR_INVALID_ARG
+    assert lib.eh_batch_repacks(None, None) == binding.EH_ERR_INVALID_ARG
+    assert lib.eh_get_instance_steps(None, None) == binding.EH_ERR_INVALID_ARG
+    assert lib.eh_get_mesh_index(None, None, None, None) == binding.EH_ERR_INVALID_ARG
