@@ -362,13 +362,14 @@ def run_reference(args, dist):
 
 # DRAM bytes (read + write) per CSR entry of each kernel kind, from one ncu
 # capture of the kernels as they stand (dram__bytes_read.sum +
-# dram__bytes_write.sum, 2D Q1 cylinder, FP64, developed flow, 4.0M vertices,
-# the bench's own timed window); a launch moves about this times nnz. None
-# where a kernel changed after the capture.
+# dram__bytes_write.sum, 2D Q1 cylinder, FP64, 4.0M vertices, the bench's own
+# timed window; k_visc + k_alpha as "visc"); a launch moves about this times
+# nnz. None where a kernel changed after the capture.
 NCU_DRAM_BYTES_PER_ENTRY_2D_FP64 = {
-    "prep": 6.0, "visc": 147.1, "low": 59.7, "lim1": 68.0, "pass": 51.4, "final": 34.2,
+    "prep": 16.3, "visc": 144.5, "low": 60.9, "lim1": 61.0, "pass": 50.5, "final": 31.5,
 }
-NCU_CAPTURE_NOTE = "ncu capture of the 501,402-vertex cylinder (developed flow), per entry, scaled by nnz"
+NCU_CAPTURE_NOTE = ("ncu launch list of the 4.0M-vertex cylinder at the bench's timed window "
+                    "(dram__bytes_read.sum + dram__bytes_write.sum per launch, as bytes per CSR entry x nnz)")
 
 
 def kernel_profile(solver, steps):
@@ -882,6 +883,8 @@ def run_nrbc(args, dist):
              "do_nothing": meshes.BC_DO_NOTHING}
     samples = (0.5, 1.0, 1.5, 2.0, 3.0, 4.0)
     results, total_dof, total_ms = {}, 0.0, 0.0
+    clocks = Clocks(dist.local_rank)
+    clocks.start()
     for case in sorted(workloads.NRBC_CASES):
         for kname, kind in kinds.items():
             mesh, U0, bs = workloads.nrbc_vortex_problem(80, case, kind)
@@ -922,7 +925,9 @@ def run_nrbc(args, dist):
                                           "vbar": workloads.NRBC_CASES[case][1], "steps": steps,
                                           "failure": failure, "deltas": series}
             s.close()
+    clk = clocks.stop()
     line = {"metric": "delta_1(t), delta_2(t) of the vortex leaving the box (non-reflecting conditions)",
+            "clocks": clk,
             "value": None, "unit": "1", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
             "dtype": "f64",
             "config": {"workload": "Sec. 6 non-reflecting tests: [-1,1]^2, 80x80 Q1, rho=1, v_inf=(1,0), "
@@ -953,6 +958,8 @@ def run_adaptive(args, dist):
     U0 = workloads.perturbed_state(mesh, 4, base=dict(rho=1.4, vel=(3.0, 0.0), p=1.0), amplitude=0.3)
     stream = torch.cuda.Stream()
     out = {}
+    clocks = Clocks(dist.local_rank)
+    clocks.start()
     for label, cfl_max in (("plain c_cfl=0.5", None), ("adaptive cfl_max=2", 2.0), ("adaptive cfl_max=4", 4.0),
                            ("adaptive cfl_max=8", 8.0)):
         s = binding.Solver(dim=2, cfl=0.5, stream=stream.cuda_stream)
@@ -982,10 +989,11 @@ def run_adaptive(args, dist):
                       "dof_updates_per_s": mesh.n * 3 * attempts / el,
                       "not_admissible": d["not_admissible"]}
         s.close()
+    clk = clocks.stop()
     base = out["plain c_cfl=0.5"]["simulated_time_per_s"]
     for v in out.values():
         v["speedup_vs_plain"] = v["simulated_time_per_s"] / base
-    line = {"metric": "simulated time advanced per second (adaptive CFL vs plain)", "value":
+    line = {"metric": "simulated time advanced per second (adaptive CFL vs plain)", "clocks": clk, "value":
             max(v["speedup_vs_plain"] for v in out.values()), "unit": "x plain", "n_gpus": 1,
             "higher_is_better": True, "data": "synthetic", "dtype": "f64",
             "config": {"workload": f"periodic Q1 channel {nx}x{ny} cells, aspect ratio {aspect:g}:1, slip walls, "
