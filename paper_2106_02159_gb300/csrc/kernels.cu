@@ -1295,7 +1295,9 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
     // from is stored at once, so the second walk over the row reads it back
     // instead of gathering the transposed limiter again. 3D: the second walk
     // forms it (27-entry rows find the first walk's lines of P still in L1,
-    // and storing there in the first walk doubled the kernel's time)
+    // and storing there in the first walk doubled the kernel's time) from l,
+    // which the first walk parks in the row's own slot of lout (only this row
+    // writes there; the second walk or the queued search overwrites it)
     double *Pk = w.P + k * SP;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
@@ -1303,6 +1305,7 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
       u[s] += lambda_i * l * pk;
       if constexpr (DIM == 2) Pk[s] = (1.0 - l) * pk;
     }
+    if constexpr (DIM == 3) lout[k] = l;
   }
   double *Uo = Uout + (int64_t)i * SP;
 #pragma unroll
@@ -1323,7 +1326,7 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
 #pragma unroll
       for (int s = 0; s < S; ++s) P[s] = Pk[s];
     } else {
-      const double l = lmin(lin[k], lin[m.tr[k]]);
+      const double l = lout[k];  // parked by the first walk
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         P[s] = (1.0 - l) * Pk[s];
