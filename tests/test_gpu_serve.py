@@ -101,3 +101,49 @@ def test_merged_batch_repacks_as_requests_come_and_go():
         tiny.admit(reqs[0].mesh, reqs[0].U0, reqs[0].t_final, reqs[0].bnd_state)
     assert e.value.status == B.EH_ERR_INVALID_ARG
     tiny.close()
+
+
+def _alone_requests(kind):
+    from paper_2106_02159_gb300 import meshes as M
+    from paper_2106_02159_gb300 import workloads as W
+    out = []
+    if kind == "3d":
+        for k, (nx, ny, nz) in enumerate(((6, 5, 4), (8, 4, 5))):
+            mesh = M.structured_q1_3d(nx, ny, nz, periodic=(False, False, True))
+            U0 = W.perturbed_state(mesh, 20 + k, base=dict(rho=1.0, vel=(0.4, 0.1, 0.0), p=1.0), amplitude=0.2)
+            out.append(serve.Request(mesh, U0, None, 0.02 + 0.01 * k, 0.0, f"box3d-{k}"))
+    elif kind == "nonreflecting":
+        for k, (case, bc) in enumerate((("i", M.BC_GODUNOV), ("ii", M.BC_CHARACTERISTIC))):
+            mesh, U0, bs = W.nrbc_vortex_problem(16 + 4 * k, case, bc)
+            out.append(serve.Request(mesh, U0, bs, 0.05 + 0.03 * k, 0.0, f"nrbc-{case}"))
+    else:
+        out = serve.poisson_trace(3, rate=1e6, seed=9, n_range=(900, 4000), t_final=0.02)
+    return out
+
+
+@pytest.mark.parametrize("kind", ["mixed", "3d", "nonreflecting"])
+def test_merged_batch_other_configurations(kind):
+    """The merged batch's union assembly with mixed precision, 3D requests
+    (27-entry rows) and the non-reflecting boundary kinds (boundary states,
+    normals and indices placed at offsets): every result equals its solve
+    alone bit for bit, with the same step count."""
+    B.build()
+    reqs = _alone_requests(kind)
+    dim = reqs[0].mesh.dim
+    precision = B.EH_PRECISION_MIXED if kind == "mixed" else B.EH_PRECISION_FP64
+    b = B.Batch(1 << 32, dim=dim, precision=precision)
+    tickets = [b.admit(r.mesh, r.U0, r.t_final, r.bnd_state) for r in reqs]
+    results = {}
+    while len(results) < len(reqs):
+        b.advance(3)
+        for t in tickets:
+            if t not in results:
+                out = b.poll(t)
+                if out is not None:
+                    results[t] = out
+    b.close()
+    for t, req in zip(tickets, reqs):
+        U, tt, steps = results[t]
+        Ua, steps_a = serve.solve_alone(req, precision)
+        assert tt == req.t_final and steps == steps_a, (req.name, steps, steps_a)
+        assert np.array_equal(U, Ua), req.name
