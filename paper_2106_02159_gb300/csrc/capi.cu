@@ -599,8 +599,12 @@ eh_status eh_create(const eh_config *cfg, eh_ctx **out) {
     c->rows_per_sm[EH_KERNEL_PASS] = 512;
     c->rows_per_sm[EH_KERNEL_FINAL] = 768;
   } else {
-    c->rows_per_sm[EH_KERNEL_PASS] = 768;
-    c->rows_per_sm[EH_KERNEL_FINAL] = 1024;
+    // 2D: eh_autotune on the 4.0M cylinder (bench window and a perturbed
+    // state, FP64 and mixed) picks 64 rows per block and no cap on the rows
+    // in flight for the row kernels (1-2% faster than 128 with caps)
+    for (int k = 0; k < EH_KERNEL_COUNT; ++k)
+      if (k != EH_KERNEL_TAU) c->tpb[k] = 64;
+    c->tpb[EH_KERNEL_LSEARCH] = 128;
   }
   Params &p = c->prm;
   p.gamma = cfg->gamma;
