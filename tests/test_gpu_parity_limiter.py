@@ -314,8 +314,8 @@ def test_served_requests_match_oracle():
 
 
 def test_three_dimensional_large_box_matches_oracle():
-    """60^3 periodic Q1 hexes: 216,000 rows of 27 entries, so the limiter's
-    grid-stride loops (at most 384-768 rows in flight per SM) wrap several
+    """60^3 periodic Q1 hexes: 216,000 rows of 27 entries, so k_pass's
+    grid-stride loop (at most 512 rows in flight per SM) wraps several
     times; 2 steps, relaxed bounds at 1e-12 per step, strict bounds against
     the oracle's spread."""
     mesh = M.structured_q1_3d(60, 60, 60, periodic=(True, True, True))
