@@ -492,6 +492,9 @@ eh_status alloc_work(eh_ctx *c, int64_t n, int64_t nnz) {
 #undef ALLOC
   CUDA_TRY(c, cudaMemset(w.lsq_count, 0, sizeof(unsigned) * LSQ_SLOTS));
   CUDA_TRY(c, cudaMemset(w.lsq2_count, 0, sizeof(unsigned) * LSQ_SLOTS));
+  // node records start as all-ones bit patterns (NaN), which k_prep never
+  // takes for a record of the current state
+  CUDA_TRY(c, cudaMemset(w.rec, 0xFF, sizeof(double) * (size_t)n * REC_MAX));
   return EH_OK;
 }
 
