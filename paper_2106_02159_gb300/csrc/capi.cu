@@ -81,6 +81,7 @@ struct eh_ctx {
   bool static_only = false;
   // a merged batch's context: the sizes its arrays were allocated for
   int64_t cap_n = 0, cap_nnz = 0, cap_bnd = 0;
+  int64_t rec_n = 0;  // nodes the record array was allocated for
 };
 
 namespace {
@@ -419,6 +420,16 @@ eh_status alloc_static(eh_ctx *c, int64_t n, int64_t nnz, int64_t n_bnd) {
   return EH_OK;
 }
 
+// Node records as all-ones bit patterns (NaN), which no admissible state
+// matches: k_prep then remakes every record, and k_visc skips no edge (its
+// skip relies on edge values stored from the same states on the same mesh).
+// Called when the arrays are allocated and when a merged batch's context is
+// rebuilt over another set of meshes.
+cudaError_t invalidate_records(eh_ctx *c) {
+  if (!c->wk.rec || c->rec_n <= 0) return cudaSuccess;
+  return cudaMemsetAsync(c->wk.rec, 0xFF, sizeof(double) * (size_t)c->rec_n * REC_MAX, c->stream);
+}
+
 // The per-stage work arrays for (up to) n nodes and nnz entries, and the
 // state buffers. A static-only context (a request of a merged served batch)
 // gets the state only: it is stepped as part of the batch's context.
@@ -437,6 +448,7 @@ eh_status alloc_work(eh_ctx *c, int64_t n, int64_t nnz) {
   ALLOC(w.alpha, n);
   ALLOC(w.rough, n);
   ALLOC(w.rough2, n);
+  ALLOC(w.steady, n);
   ALLOC(w.inc, (size_t)n * SP);
   if (mixed(c)) {
     // FP32 node record, packed w_ij/a_ij/d_ij slots and F^H
@@ -492,9 +504,9 @@ eh_status alloc_work(eh_ctx *c, int64_t n, int64_t nnz) {
 #undef ALLOC
   CUDA_TRY(c, cudaMemset(w.lsq_count, 0, sizeof(unsigned) * LSQ_SLOTS));
   CUDA_TRY(c, cudaMemset(w.lsq2_count, 0, sizeof(unsigned) * LSQ_SLOTS));
-  // node records start as all-ones bit patterns (NaN), which k_prep never
-  // takes for a record of the current state
-  CUDA_TRY(c, cudaMemset(w.rec, 0xFF, sizeof(double) * (size_t)n * REC_MAX));
+  c->rec_n = n;
+  CUDA_TRY(c, invalidate_records(c));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return EH_OK;
 }
 
@@ -1659,6 +1671,7 @@ eh_status assemble(eh_ctx *uni, eh_ctx *const *parts, int count, const double *t
   if ((st = setup_instances(uni, count, off.data(), t_final))) return st;
   CUDA_TRY(uni, cudaMemcpy(uni->wk.t_inst, t, sizeof(double) * count, cudaMemcpyHostToDevice));
   if ((st = reset_status(uni))) return st;
+  CUDA_TRY(uni, invalidate_records(uni));  // other meshes at the same rows
   CUDA_TRY(uni, cudaStreamSynchronize(s));
   uni->have_mesh = uni->have_state = true;
   uni->steps = 0;

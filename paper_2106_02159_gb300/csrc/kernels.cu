@@ -544,11 +544,13 @@ __device__ __forceinline__ void node_flux(const T *mv, const T *v, T pr, T H, T 
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TPB_MAX) k_prep(MeshView m, Params p, const double *__restrict__ U,
                                               double *__restrict__ rec, T *__restrict__ vrec,
-                                              unsigned char *__restrict__ rough, const DevStatus *st) {
+                                              unsigned char *__restrict__ rough,
+                                              unsigned char *__restrict__ steady, const DevStatus *st) {
   constexpr int S = DIM + 2;
   using R = Rec<DIM>;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m.n || st->err) return;
+  const unsigned char was_rough = rough[i];  // as the previous k_visc left it
   rough[i] = 0;  // set by k_visc where a neighbour's state differs
   double u[S];
 #pragma unroll
@@ -563,6 +565,7 @@ __global__ void __launch_bounds__(TPB_MAX) k_prep(MeshView m, Params p, const do
     bool same = true;
 #pragma unroll
     for (int s = 0; s < S; ++s) same &= dbits(Rr[s]) == dbits(u[s]);
+    steady[i] = same ? (unsigned char)(was_rough ? 1 : 3) : (unsigned char)0;
     if (same) return;
   }
   double rho = u[0];
@@ -664,10 +667,19 @@ __global__ void __launch_bounds__(TPB_MAX) k_visc(MeshView m, Params p, Work w) 
 #pragma unroll
     for (int s = 0; s < S; ++s) ubi[s] = dbits(Ri64[s]);
   }
+  const unsigned char sti = w.steady[i];
   const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
   for (int64_t k = k0; k < k1; ++k) {
     const int j = m.col[k];
     if (j <= i) continue;  // each unique edge once, from the row of min(i, j)
+    if (sti & 1) {
+      // both states unchanged since the previous k_visc, which stored this
+      // edge's values from the same bits; they were equal then (one of the
+      // two nodes had no differing neighbour), so they are now: nothing to
+      // store and no rough mark to set
+      const unsigned char stj = w.steady[j];
+      if ((stj & 1) && ((sti | stj) & 2)) continue;
+    }
     const T *Rj = rec + (int64_t)j * RS;
     const int32_t kt = m.tr[k];
     {
@@ -1787,7 +1799,7 @@ template <int DIM> __global__ void k_count_not_admissible(int n, const double *U
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
 void launch_prep(const MeshView &m, const Params &p, const double *U, const Work &w, int tpb, cudaStream_t s) {
-  k_prep<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, U, w.rec, (T *)w.vrec, w.rough, w.st);
+  k_prep<DIM, T><<<nblocks(m.n, tpb), tpb, 0, s>>>(m, p, U, w.rec, (T *)w.vrec, w.rough, w.steady, w.st);
 }
 template <int DIM, typename T>
 void launch_visc(const MeshView &m, const Params &p, const Work &w, int tpb, cudaStream_t s) {

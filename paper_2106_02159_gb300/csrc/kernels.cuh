@@ -119,6 +119,12 @@ struct Work {
   // (written by k_low). A row with rough2 = 0 has P_ij = 0 on every entry.
   unsigned char *rough;   // [n]
   unsigned char *rough2;  // [n]
+  // steady[i] (written by k_prep): bit 0 = U_i has the bits it had at the
+  // previous k_prep (its record was kept), bit 1 = that, and node i was not
+  // rough at the previous k_visc. An edge between two kept nodes one of
+  // which also has bit 1 joins equal states whose edge values k_visc already
+  // stored: it is skipped.
+  unsigned char *steady;  // [n]
   double *w;       // [nnz][SP]  (f(U_j) - f(U_i)) c_ij
   double *d;       // [nnz]      d^L_ij (diagonal: d_ii)
   double *inc;     // [n][SP]    sum_{j != i} d_ij (U_j - U_i) - w_ij
