@@ -392,9 +392,10 @@ struct RowF32 {
   float phi5;   // Phi_min^5 rounded to FP32 (0 when out of range)
 };
 // The row's FP32 data of the pre-decision. Rows whose density bounds are
-// within 1e-4 of each other (near-uniform neighbourhoods) skip it: there psi(1)
-// sits within the FP32 error of 0 almost always, and a warp with one
-// undecided lane pays for both tests.
+// within 1e-6 of each other (near-uniform neighbourhoods) skip it: there psi(1)
+// sits within the FP32 error of 0 almost always (on the Mach-3 cylinder most
+// such rows differ from their neighbours by a few ulps, and psi(1) is within
+// 1e-13 of 0), and a warp with one undecided lane pays for both tests.
 template <int DIM>
 __device__ __forceinline__ RowF32 row_f32(const double *ub, double rmin, double rmax, double phimin5) {
   RowF32 r;
@@ -402,7 +403,7 @@ __device__ __forceinline__ RowF32 row_f32(const double *ub, double rmin, double 
   for (int s = 0; s < DIM + 2; ++s) r.u[s] = 0.0f;
   r.phi5 = 0.0f;
   // 2^-40 <= Phi_min^5 <= 2^40 (else no pre-decision)
-  if (!(gt_pos(rmax - rmin, 1e-4 * rmax) && gt_pos(phimin5, 9.094947017729282e-13) &&
+  if (!(gt_pos(rmax - rmin, 1e-6 * rmax) && gt_pos(phimin5, 9.094947017729282e-13) &&
         lt_pos(phimin5, 1.099511627776e12)))
     return r;
 #pragma unroll
