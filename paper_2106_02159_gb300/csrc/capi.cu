@@ -489,6 +489,7 @@ eh_status alloc_work(eh_ctx *c, int64_t n, int64_t nnz) {
   ALLOC(w.Ua, (size_t)n * SP);
   ALLOC(w.Ub, (size_t)n * SP);
   ALLOC(w.P, (size_t)nnz * SP);
+  ALLOC(w.rem, nnz);
   ALLOC(w.la, nnz);
   ALLOC(w.lb, nnz);
   ALLOC(w.lsq, nnz);  // every entry can be queued once per pass
@@ -632,6 +633,7 @@ eh_status eh_create(const eh_config *cfg, eh_ctx **out) {
   p.gamma = cfg->gamma;
   p.cfl = cfg->cfl;
   p.gamma75 = cfg->gamma == 1.4 ? 1 : 0;
+  p.limiter_passes = cfg->limiter_passes;
   p.gm1 = cfg->gamma - 1.0;
   p.z = (cfg->gamma - 1.0) / (2.0 * cfg->gamma);
   p.inv_z = 1.0 / p.z;

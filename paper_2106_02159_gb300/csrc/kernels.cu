@@ -1308,6 +1308,8 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
     }
     return;
   }
+  // slot = the pass (1, 2, ...): pass 1 starts from k_lim1's P_ij, a later
+  // pass from the remainder rem[k] P[k] that the previous one left
   for (int64_t k = k0; k < k1; ++k) {
     if (m.col[k] == i) {
       if (lsym_trace) lsym_trace[k] = 1.0;
@@ -1315,21 +1317,26 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
     }
     const double l = lmin(lin[k], lin[m.tr[k]]);
     if (lsym_trace) lsym_trace[k] = l;
-    // the update with l P. 2D: the remainder (1 - l) P the next search starts
-    // from is stored at once, so the second walk over the row reads it back
-    // instead of gathering the transposed limiter again. 3D: the second walk
-    // forms it (27-entry rows find the first walk's lines of P still in L1,
-    // and storing there in the first walk doubled the kernel's time) from l,
-    // which the first walk parks in the row's own slot of lout (only this row
-    // writes there; the second walk or the queued search overwrites it)
     double *Pk = w.P + k * SP;
+    double P[S];
+    if (slot > 1) {
+      const double r = w.rem[k];
+      if (dbits(r) == 0) continue;  // nothing left of P_ij (rem stays 0)
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const double pk = Pk[s];
-      u[s] += lambda_i * l * pk;
-      if constexpr (DIM == 2) Pk[s] = (1.0 - l) * pk;
+      for (int s = 0; s < S; ++s) {
+        P[s] = r * Pk[s];
+        Pk[s] = P[s];  // this pass's P_ij, for the remainder it leaves
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < S; ++s) P[s] = Pk[s];
     }
-    if constexpr (DIM == 3) lout[k] = l;
+    // the update with l P; the remainder (1 - l) P is left as rem[k] (a
+    // store of (1 - l) P here costs more than forming it where it is read,
+    // and for l = 1 -- most entries -- nothing is read at all)
+#pragma unroll
+    for (int s = 0; s < S; ++s) u[s] += lambda_i * l * P[s];
+    w.rem[k] = 1.0 - l;
   }
   double *Uo = Uout + (int64_t)i * SP;
 #pragma unroll
@@ -1344,19 +1351,15 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
       lout[k] = 1.0;
       continue;
     }
-    double *Pk = w.P + k * SP;
-    double P[S];
-    if constexpr (DIM == 2) {
-#pragma unroll
-      for (int s = 0; s < S; ++s) P[s] = Pk[s];
-    } else {
-      const double l = lout[k];  // parked by the first walk
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
-        P[s] = (1.0 - l) * Pk[s];
-        Pk[s] = P[s];
-      }
+    const double r = w.rem[k];
+    if (dbits(r) == 0) {  // the remainder is 0: every l gives the same state, the largest is 1
+      lout[k] = 1.0;
+      continue;
     }
+    const double *Pk = w.P + k * SP;
+    double P[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) P[s] = r * Pk[s];
     if (line_search_at_one<DIM>(p, u, P, rmin, rmax, phimin5, rf))
       lout[k] = 1.0;
     else if (k - k0 < 64)
@@ -1407,10 +1410,11 @@ __global__ void __launch_bounds__(256) k_ls_deferred(MeshView m, Params p, Work 
     const double *bi = w.bounds + (int64_t)it.x * 4;
     const double phimin = bi[2], phimin2 = phimin * phimin, phimin5 = phimin2 * phimin2 * phimin;
     double u[S], P[S];
+    const double r = slot > 0 ? w.rem[it.y] : 1.0;  // a later pass: the remainder rem P
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       u[s] = ub[(int64_t)it.x * SP + s];
-      P[s] = w.P[(int64_t)it.y * SP + s];
+      P[s] = slot > 0 ? r * w.P[(int64_t)it.y * SP + s] : w.P[(int64_t)it.y * SP + s];
     }
     const LsBracket b = line_search_start<DIM>(p, u, P, bi[0], bi[1], phimin, phimin5);
     if (b.done)
@@ -1432,10 +1436,11 @@ __global__ void __launch_bounds__(256) k_ls_iterate(MeshView m, Params p, Work w
     const LsItem it = w.lsq2[q];
     const double phimin = w.bounds[(int64_t)it.i * 4 + 2];
     double u[S], P[S];
+    const double r = slot > 0 ? w.rem[it.k] : 1.0;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       u[s] = ub[(int64_t)it.i * SP + s];
-      P[s] = w.P[(int64_t)it.k * SP + s];
+      P[s] = slot > 0 ? r * w.P[(int64_t)it.k * SP + s] : w.P[(int64_t)it.k * SP + s];
     }
     const LsBracket b{it.l, it.pl, it.pr, it.rR, false};
     lout[it.k] = line_search_iterate<DIM>(p, u, P, phimin, b);
@@ -1689,8 +1694,15 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
         }
         if (lsym_trace) lsym_trace[k] = ls[q];
         const double *Pk = w.P + k * SP;
+        if (p.limiter_passes >= 2) {  // the remainder rem P that the last k_pass left
+          const double r = w.rem[k];
+          if (dbits(r) == 0) continue;
 #pragma unroll
-        for (int s = 0; s < S; ++s) u[s] += lambda_i * ls[q] * Pk[s];
+          for (int s = 0; s < S; ++s) u[s] += lambda_i * ls[q] * (r * Pk[s]);
+        } else {
+#pragma unroll
+          for (int s = 0; s < S; ++s) u[s] += lambda_i * ls[q] * Pk[s];
+        }
       }
     }
   } else if (lsym_trace) {

@@ -108,6 +108,7 @@ struct Params {
   double inv_z;              // 2 gamma/(gamma-1)
   double kshock;             // (gamma+1)/(2 gamma)
   double inv_gm1;            // 1/(gamma - 1)
+  int limiter_passes;        // 1 + the passes of k_pass (k_final reads rem when >= 2)
 };
 
 struct Work {
@@ -134,6 +135,11 @@ struct Work {
   double *Ua;      // [n][SP]    limited state, ping
   double *Ub;      // [n][SP]    limited state, pong
   double *P;       // [nnz][SP]
+  // rem[k] = 1 - l_ij of the last limiter pass (written by k_pass): that
+  // pass leaves the remainder rem[k] P[k] for the next one, formed where it
+  // is read and never stored (rem = 0: nothing left of P_ij); from the third
+  // pass on, k_pass first writes its own input back to P
+  double *rem;     // [nnz]
   double *la;      // [nnz]      limiter, ping
   double *lb;      // [nnz]      limiter, pong
   unsigned long long *bound_bits;  // [ninst] running minimum of c_cfl m_i / (2 sum_j d_ij) over the
