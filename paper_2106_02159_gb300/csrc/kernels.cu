@@ -1259,6 +1259,7 @@ __device__ __forceinline__ double lmin(double a, double b) {
 // dependent gather (tr[k], then l at tr[k]), and issuing a chunk's gathers
 // together overlaps their latencies instead of paying them one entry at a time.
 constexpr int LCHUNK = 3;  // measured on the 4.0M cylinder: 3 shortens k_final by 7%; 4 and 9 lengthen it
+                           // (one limiter pass; after two or more k_final gathers only where rem != 0)
 __device__ __forceinline__ void sym_limiters(const MeshView &m, const double *__restrict__ lin, int64_t kb, int cnt,
                                              int i, double *ls, bool *diag) {
   int32_t t[LCHUNK], c[LCHUNK];
@@ -1678,7 +1679,25 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
   const double *Ui = Uin + (int64_t)i * SP;
 #pragma unroll
   for (int s = 0; s < S; ++s) u[s] = Ui[s];
-  if (w.rough2[i]) {  // else every P_ij is 0 (see lim1_row) and the update adds nothing
+  if (w.rough2[i] && p.limiter_passes >= 2) {
+    // the remainder rem P that the last k_pass left: where rem = 0 (most
+    // entries) the update adds nothing, and the symmetrised limiter -- a
+    // dependent gather of the transposed one -- is not needed
+    for (int64_t k = k0; k < k1; ++k) {
+      if (m.col[k] == i) {
+        if (lsym_trace) lsym_trace[k] = 1.0;
+        continue;
+      }
+      const double r = w.rem[k];
+      if (dbits(r) == 0 && !lsym_trace) continue;
+      const double l = lmin(lin[k], lin[m.tr[k]]);
+      if (lsym_trace) lsym_trace[k] = l;
+      if (dbits(r) == 0) continue;
+      const double *Pk = w.P + k * SP;
+#pragma unroll
+      for (int s = 0; s < S; ++s) u[s] += lambda_i * l * (r * Pk[s]);
+    }
+  } else if (w.rough2[i]) {  // else every P_ij is 0 (see lim1_row) and the update adds nothing
     for (int64_t kb = k0; kb < k1; kb += LCHUNK) {
       const int cnt = (int)min((int64_t)LCHUNK, k1 - kb);
       double ls[LCHUNK];
@@ -1694,15 +1713,8 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
         }
         if (lsym_trace) lsym_trace[k] = ls[q];
         const double *Pk = w.P + k * SP;
-        if (p.limiter_passes >= 2) {  // the remainder rem P that the last k_pass left
-          const double r = w.rem[k];
-          if (dbits(r) == 0) continue;
 #pragma unroll
-          for (int s = 0; s < S; ++s) u[s] += lambda_i * ls[q] * (r * Pk[s]);
-        } else {
-#pragma unroll
-          for (int s = 0; s < S; ++s) u[s] += lambda_i * ls[q] * Pk[s];
-        }
+        for (int s = 0; s < S; ++s) u[s] += lambda_i * ls[q] * Pk[s];
       }
     }
   } else if (lsym_trace) {
