@@ -449,6 +449,7 @@ eh_status alloc_work(eh_ctx *c, int64_t n, int64_t nnz) {
   ALLOC(w.rough, n);
   ALLOC(w.rough2, n);
   ALLOC(w.steady, n);
+  ALLOC(w.lone, 2 * n);
   ALLOC(w.inc, (size_t)n * SP);
   if (mixed(c)) {
     // FP32 node record, packed w_ij/a_ij/d_ij slots and F^H

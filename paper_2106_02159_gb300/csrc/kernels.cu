@@ -1156,6 +1156,7 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
         for (int s = 0; s < S; ++s) P_trace[k * SP + s] = 0.0;
       }
     }
+    w.lone[i] = 1;
     return;
   }
   const double tau = w.tau_inst[m.inst ? m.inst[i] : 0];
@@ -1198,6 +1199,7 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
   const double tc = tau * (double)(k1 - k0 - 1);
   const double coef = tc * m.inv_mi[i];
   uint64_t defer = 0;  // entries whose line search goes to k_ls_deferred
+  bool long_deferred = false;
   for (int64_t k = k0; k < k1; ++k) {
     const int j = m.col[k];
     double *Pk = w.P + k * SP;
@@ -1226,13 +1228,16 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
 #pragma unroll
       for (int s = 0; s < S; ++s) P_trace[k * SP + s] = P[s];
     }
-    if (line_search_at_one<DIM>(p, ul, P, rmin, rmax, phimin5, rf))
+    if (line_search_at_one<DIM>(p, ul, P, rmin, rmax, phimin5, rf)) {
       w.la[k] = 1.0;
-    else if (k - k0 < 64)
+    } else if (k - k0 < 64) {
       defer |= 1ull << (k - k0);
-    else
+    } else {
       defer_line_searches(w, 0, i, k, 1ull);  // rows longer than 64 entries
+      long_deferred = true;
+    }
   }
+  w.lone[i] = (defer == 0 && !long_deferred) ? 1 : 0;
   defer_line_searches(w, 0, i, k0, defer);
 }
 
@@ -1299,6 +1304,8 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
   const double *Ui = Uin + (int64_t)i * SP;
 #pragma unroll
   for (int s = 0; s < S; ++s) u[s] = Ui[s];
+  const unsigned char *lone_in = w.lone + (int64_t)((slot - 1) & 1) * m.n;
+  unsigned char *lone_out = w.lone + (int64_t)(slot & 1) * m.n;
   if (!w.rough2[i]) {  // every P_ij is 0 (see lim1_row): the state stays, every next search returns 1
     double *Uo = Uout + (int64_t)i * SP;
 #pragma unroll
@@ -1307,16 +1314,20 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
       lout[k] = 1.0;
       if (lsym_trace) lsym_trace[k] = m.col[k] == i ? 1.0 : lmin(lin[k], lin[m.tr[k]]);
     }
+    lone_out[i] = 1;
     return;
   }
+  const bool one_i = lone_in[i] != 0;
   // slot = the pass (1, 2, ...): pass 1 starts from k_lim1's P_ij, a later
   // pass from the remainder rem[k] P[k] that the previous one left
   for (int64_t k = k0; k < k1; ++k) {
-    if (m.col[k] == i) {
+    const int j = m.col[k];
+    if (j == i) {
       if (lsym_trace) lsym_trace[k] = 1.0;
       continue;
     }
-    const double l = lmin(lin[k], lin[m.tr[k]]);
+    // every limiter of rows i and j is 1: so is min(l_ij, l_ji), no gather
+    const double l = (one_i && lone_in[j]) ? 1.0 : lmin(lin[k], lin[m.tr[k]]);
     if (lsym_trace) lsym_trace[k] = l;
     double *Pk = w.P + k * SP;
     double P[S];
@@ -1347,6 +1358,7 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
   const double phimin2 = phimin * phimin, phimin5 = phimin2 * phimin2 * phimin;
   const RowF32 rf = row_f32<DIM>(u, rmin, rmax, phimin5);
   uint64_t defer = 0;
+  bool long_deferred = false;
   for (int64_t k = k0; k < k1; ++k) {
     if (m.col[k] == i) {
       lout[k] = 1.0;
@@ -1361,13 +1373,16 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
     double P[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) P[s] = r * Pk[s];
-    if (line_search_at_one<DIM>(p, u, P, rmin, rmax, phimin5, rf))
+    if (line_search_at_one<DIM>(p, u, P, rmin, rmax, phimin5, rf)) {
       lout[k] = 1.0;
-    else if (k - k0 < 64)
+    } else if (k - k0 < 64) {
       defer |= 1ull << (k - k0);
-    else
+    } else {
       defer_line_searches(w, slot, i, k, 1ull);
+      long_deferred = true;
+    }
   }
+  lone_out[i] = (defer == 0 && !long_deferred) ? 1 : 0;
   defer_line_searches(w, slot, i, k0, defer);
 }
 

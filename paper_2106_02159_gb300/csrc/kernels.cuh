@@ -126,6 +126,11 @@ struct Work {
   // which also has bit 1 joins equal states whose edge values k_visc already
   // stored: it is skipped.
   unsigned char *steady;  // [n]
+  // lone[q * n + i] = 1 when every limiter of row i in a pass is 1 (no entry
+  // of the row went to the queued searches): written by k_lim1 (q = 0) and by
+  // k_pass of pass p (q = p & 1), read by the next pass, which then needs no
+  // gather of the transposed limiter for an entry between two such rows
+  unsigned char *lone;    // [2][n]
   double *w;       // [nnz][SP]  (f(U_j) - f(U_i)) c_ij
   double *d;       // [nnz]      d^L_ij (diagonal: d_ii)
   double *inc;     // [n][SP]    sum_{j != i} d_ij (U_j - U_i) - w_ij
