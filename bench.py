@@ -424,7 +424,9 @@ def roofline_of(prof, mesh, ms_per_step, hbm, hbm_src, precision):
             "note": "the count is the method's for every entry; entries between bit-identical states are "
                     "evaluated by the exact identical-state shortcut (see identical_edge_share), so where that "
                     "share is large a fraction can exceed what the executed arithmetic alone would give -- "
-                    "developed_flow has none of them"}
+                    "developed_flow has none of them; likewise the planned bytes of k_pass and k_final include "
+                    "reads of P_ij that they skip where the limiter is 1 (the remainder (1 - l) P_ij is 0), so "
+                    "their hbm_frac can exceed 1"}
 
 
 def timed_steps(solver, stream, steps):
