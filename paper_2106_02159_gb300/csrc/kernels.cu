@@ -1149,14 +1149,13 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
 #pragma unroll
     for (int s = 0; s < S; ++s) ULi[s] = Ri[s];
     const int64_t k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
-    for (int64_t k = k0; k < k1; ++k) {
-      w.la[k] = 1.0;
-      if (P_trace) {
+    if (P_trace) {
+      for (int64_t k = k0; k < k1; ++k) {
 #pragma unroll
         for (int s = 0; s < S; ++s) P_trace[k * SP + s] = 0.0;
       }
     }
-    w.lone[i] = 1;
+    w.lone[i] = 1;  // every limiter is 1; la is not written (readers check lone first)
     return;
   }
   const double tau = w.tau_inst[m.inst ? m.inst[i] : 0];
@@ -1200,6 +1199,7 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
   const double coef = tc * m.inv_mi[i];
   uint64_t defer = 0;  // entries whose line search goes to k_ls_deferred
   bool long_deferred = false;
+  const bool longrow = k1 - k0 > 64;  // limiters stored as they are known
   for (int64_t k = k0; k < k1; ++k) {
     const int j = m.col[k];
     double *Pk = w.P + k * SP;
@@ -1210,7 +1210,7 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
 #pragma unroll
         for (int s = 0; s < S; ++s) P_trace[k * SP + s] = 0.0;
       }
-      w.la[k] = 1.0;
+      if (longrow) w.la[k] = 1.0;
       continue;
     }
     const double *Rj = w.rec + (int64_t)j * R::SIZE;
@@ -1229,7 +1229,7 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
       for (int s = 0; s < S; ++s) P_trace[k * SP + s] = P[s];
     }
     if (line_search_at_one<DIM>(p, ul, P, rmin, rmax, phimin5, rf)) {
-      w.la[k] = 1.0;
+      if (longrow) w.la[k] = 1.0;
     } else if (k - k0 < 64) {
       defer |= 1ull << (k - k0);
     } else {
@@ -1237,7 +1237,13 @@ __device__ __forceinline__ void lim1_row(const MeshView &m, const Params &p, con
       long_deferred = true;
     }
   }
-  w.lone[i] = (defer == 0 && !long_deferred) ? 1 : 0;
+  const bool lone = defer == 0 && !long_deferred;
+  w.lone[i] = lone ? 1 : 0;
+  // a row with a queued search stores its other limiters (1); a row without
+  // one stores none (every limiter of it is 1, and its lone flag says so)
+  if (!lone && !longrow)
+    for (int64_t k = k0; k < k1; ++k)
+      if (!((defer >> (k - k0)) & 1ull)) w.la[k] = 1.0;
   defer_line_searches(w, 0, i, k0, defer);
 }
 
@@ -1259,14 +1265,16 @@ __device__ __forceinline__ double lmin(double a, double b) {
 }
 
 // The symmetrised limiters l_ij = min(l_k, l_tr[k]) of the cnt <= LCHUNK
-// entries kb, kb + 1, ... of row i (diag[q]: the entry is the diagonal). Every
+// entries kb, kb + 1, ... of row i (diag[q]: the entry is the diagonal); a
+// row whose lone flag is set has every limiter 1 (and none stored). Every
 // load of the chunk is issued before the first use: the transposed value is a
 // dependent gather (tr[k], then l at tr[k]), and issuing a chunk's gathers
 // together overlaps their latencies instead of paying them one entry at a time.
 constexpr int LCHUNK = 3;  // measured on the 4.0M cylinder: 3 shortens k_final by 7%; 4 and 9 lengthen it
                            // (one limiter pass; after two or more k_final gathers only where rem != 0)
-__device__ __forceinline__ void sym_limiters(const MeshView &m, const double *__restrict__ lin, int64_t kb, int cnt,
-                                             int i, double *ls, bool *diag) {
+__device__ __forceinline__ void sym_limiters(const MeshView &m, const double *__restrict__ lin,
+                                             const unsigned char *__restrict__ lone, int64_t kb, int cnt, int i,
+                                             double *ls, bool *diag) {
   int32_t t[LCHUNK], c[LCHUNK];
 #pragma unroll
   for (int q = 0; q < LCHUNK; ++q)
@@ -1274,12 +1282,13 @@ __device__ __forceinline__ void sym_limiters(const MeshView &m, const double *__
       t[q] = m.tr[kb + q];
       c[q] = m.col[kb + q];
     }
+  const bool one_i = lone[i] != 0;
   double a[LCHUNK], b[LCHUNK];
 #pragma unroll
   for (int q = 0; q < LCHUNK; ++q)
     if (q < cnt) {
-      a[q] = lin[kb + q];
-      b[q] = lin[t[q]];
+      a[q] = one_i ? 1.0 : lin[kb + q];
+      b[q] = lone[c[q]] ? 1.0 : lin[t[q]];
     }
 #pragma unroll
   for (int q = 0; q < LCHUNK; ++q)
@@ -1310,11 +1319,13 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
     double *Uo = Uout + (int64_t)i * SP;
 #pragma unroll
     for (int s = 0; s < S; ++s) Uo[s] = u[s];
-    for (int64_t k = k0; k < k1; ++k) {
-      lout[k] = 1.0;
-      if (lsym_trace) lsym_trace[k] = m.col[k] == i ? 1.0 : lmin(lin[k], lin[m.tr[k]]);
+    if (lsym_trace) {
+      for (int64_t k = k0; k < k1; ++k) {
+        const int j = m.col[k];
+        lsym_trace[k] = j == i ? 1.0 : lmin(lone_in[i] ? 1.0 : lin[k], lone_in[j] ? 1.0 : lin[m.tr[k]]);
+      }
     }
-    lone_out[i] = 1;
+    lone_out[i] = 1;  // every next limiter is 1; lout is not written
     return;
   }
   const bool one_i = lone_in[i] != 0;
@@ -1326,8 +1337,9 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
       if (lsym_trace) lsym_trace[k] = 1.0;
       continue;
     }
-    // every limiter of rows i and j is 1: so is min(l_ij, l_ji), no gather
-    const double l = (one_i && lone_in[j]) ? 1.0 : lmin(lin[k], lin[m.tr[k]]);
+    // a row whose limiters are all 1 has none stored: its side is 1, and an
+    // entry between two such rows needs no gather of the transposed limiter
+    const double l = lmin(one_i ? 1.0 : lin[k], lone_in[j] ? 1.0 : lin[m.tr[k]]);
     if (lsym_trace) lsym_trace[k] = l;
     double *Pk = w.P + k * SP;
     double P[S];
@@ -1359,14 +1371,15 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
   const RowF32 rf = row_f32<DIM>(u, rmin, rmax, phimin5);
   uint64_t defer = 0;
   bool long_deferred = false;
+  const bool longrow = k1 - k0 > 64;  // limiters stored as they are known
   for (int64_t k = k0; k < k1; ++k) {
     if (m.col[k] == i) {
-      lout[k] = 1.0;
+      if (longrow) lout[k] = 1.0;
       continue;
     }
     const double r = w.rem[k];
     if (dbits(r) == 0) {  // the remainder is 0: every l gives the same state, the largest is 1
-      lout[k] = 1.0;
+      if (longrow) lout[k] = 1.0;
       continue;
     }
     const double *Pk = w.P + k * SP;
@@ -1374,7 +1387,7 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
 #pragma unroll
     for (int s = 0; s < S; ++s) P[s] = r * Pk[s];
     if (line_search_at_one<DIM>(p, u, P, rmin, rmax, phimin5, rf)) {
-      lout[k] = 1.0;
+      if (longrow) lout[k] = 1.0;
     } else if (k - k0 < 64) {
       defer |= 1ull << (k - k0);
     } else {
@@ -1382,7 +1395,11 @@ __device__ __forceinline__ void pass_row(const MeshView &m, const Params &p, con
       long_deferred = true;
     }
   }
-  lone_out[i] = (defer == 0 && !long_deferred) ? 1 : 0;
+  const bool lone = defer == 0 && !long_deferred;
+  lone_out[i] = lone ? 1 : 0;
+  if (!lone && !longrow)  // as in k_lim1: only a row with a queued search stores its limiters
+    for (int64_t k = k0; k < k1; ++k)
+      if (!((defer >> (k - k0)) & 1ull)) lout[k] = 1.0;
   defer_line_searches(w, slot, i, k0, defer);
 }
 
@@ -1694,6 +1711,7 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
   const double *Ui = Uin + (int64_t)i * SP;
 #pragma unroll
   for (int s = 0; s < S; ++s) u[s] = Ui[s];
+  const unsigned char *lone = w.lone + (int64_t)((p.limiter_passes - 1) & 1) * m.n;  // of the last pass
   if (w.rough2[i] && p.limiter_passes >= 2) {
     // the remainder rem P that the last k_pass left: where rem = 0 (most
     // entries) the update adds nothing, and the symmetrised limiter -- a
@@ -1705,7 +1723,8 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
       }
       const double r = w.rem[k];
       if (dbits(r) == 0 && !lsym_trace) continue;
-      const double l = lmin(lin[k], lin[m.tr[k]]);
+      const int j = m.col[k];
+      const double l = lmin(lone[i] ? 1.0 : lin[k], lone[j] ? 1.0 : lin[m.tr[k]]);
       if (lsym_trace) lsym_trace[k] = l;
       if (dbits(r) == 0) continue;
       const double *Pk = w.P + k * SP;
@@ -1717,7 +1736,7 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
       const int cnt = (int)min((int64_t)LCHUNK, k1 - kb);
       double ls[LCHUNK];
       bool dg[LCHUNK];
-      sym_limiters(m, lin, kb, cnt, i, ls, dg);
+      sym_limiters(m, lin, lone, kb, cnt, i, ls, dg);
 #pragma unroll
       for (int q = 0; q < LCHUNK; ++q) {
         if (q >= cnt) break;
@@ -1733,7 +1752,10 @@ __device__ __forceinline__ void final_row(const MeshView &m, const Params &p, co
       }
     }
   } else if (lsym_trace) {
-    for (int64_t k = k0; k < k1; ++k) lsym_trace[k] = m.col[k] == i ? 1.0 : lmin(lin[k], lin[m.tr[k]]);
+    for (int64_t k = k0; k < k1; ++k) {
+      const int j = m.col[k];
+      lsym_trace[k] = j == i ? 1.0 : lmin(lone[i] ? 1.0 : lin[k], lone[j] ? 1.0 : lin[m.tr[k]]);
+    }
   }
   if (Upre_trace) {
 #pragma unroll
