@@ -366,7 +366,7 @@ def run_reference(args, dist):
 # timed window; k_visc + k_alpha as "visc"); a launch moves about this times
 # nnz. None where a kernel changed after the capture.
 NCU_DRAM_BYTES_PER_ENTRY_2D_FP64 = {
-    "prep": 24.3, "visc": 95.8, "low": 60.9, "lim1": 61.2, "pass": 51.6, "final": 31.3,
+    "prep": 24.3, "visc": 95.0, "low": 61.0, "lim1": 48.7, "pass": 32.4, "final": 18.3,
 }
 NCU_CAPTURE_NOTE = ("ncu launch list of the 4.0M-vertex cylinder at the bench's timed window "
                     "(dram__bytes_read.sum + dram__bytes_write.sum per launch, as bytes per CSR entry x nnz)")
