@@ -610,18 +610,17 @@ eh_status eh_create(const eh_config *cfg, eh_ctx **out) {
   if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) c->nsm = 0;
   if (cfg->dim == 3) {
     // 3D: eh_autotune on a 6.0M-vertex extruded cylinder (after 100 steps
-    // and on a perturbed state, FP64 and mixed): fewer rows in flight keep
-    // each 27-entry row's cache lines of P in L1 between k_pass's two walks
-    // (cap 512 per SM); the other kernels run fastest uncapped (1-2% over
-    // 128 threads per block with caps on k_lim1 and k_final)
+    // and on a perturbed state, FP64 and mixed), with k_pass reading P only
+    // where a limiter is below 1: every kernel uncapped (2-3% over a cap of
+    // 512 rows in flight per SM on k_pass, which kept a 27-entry row's lines
+    // of P in L1 while its second walk still re-read all of them)
     c->tpb[EH_KERNEL_PREP] = 64;
     c->tpb[EH_KERNEL_VISC] = 64;
     c->tpb[EH_KERNEL_LOW] = 64;
-    c->tpb[EH_KERNEL_LIM1] = 256;
-    c->tpb[EH_KERNEL_PASS] = 128;
-    c->tpb[EH_KERNEL_FINAL] = 256;
+    c->tpb[EH_KERNEL_LIM1] = 128;
+    c->tpb[EH_KERNEL_PASS] = 256;
+    c->tpb[EH_KERNEL_FINAL] = 64;
     c->tpb[EH_KERNEL_LSEARCH] = 64;
-    c->rows_per_sm[EH_KERNEL_PASS] = 512;
   } else {
     // 2D: eh_autotune on the 4.0M cylinder (bench window and a perturbed
     // state, FP64 and mixed) picks 64 rows per block and no cap on the rows

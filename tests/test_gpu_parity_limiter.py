@@ -314,9 +314,8 @@ def test_served_requests_match_oracle():
 
 
 def test_three_dimensional_large_box_matches_oracle():
-    """60^3 periodic Q1 hexes: 216,000 rows of 27 entries, so k_pass's
-    grid-stride loop (at most 512 rows in flight per SM) wraps several
-    times; 2 steps, relaxed bounds at 1e-12 per step, strict bounds against
+    """60^3 periodic Q1 hexes: 216,000 rows of 27 entries (well past one
+    wave of 64-256-row blocks on every SM); 2 steps, relaxed bounds at 1e-12 per step, strict bounds against
     the oracle's spread."""
     mesh = M.structured_q1_3d(60, 60, 60, periodic=(True, True, True))
     U0 = W.perturbed_state(mesh, 11, base=dict(rho=1.0, vel=(0.5, -0.2, 0.1), p=1.0), amplitude=0.2)
