@@ -147,7 +147,9 @@ eh_status eh_stage(eh_ctx *ctx, double tau, double *tau_used);
 /* One SSPRK(3,3) step. dt > 0: that step (EH_ERR_CFL if it exceeds the
  * invariant-domain limit of the first stage; the state is then unchanged);
  * dt <= 0: the CFL step of the first stage, reused by stages 2 and 3.
- * dt_used may be NULL (then no synchronisation). */
+ * dt_used may be NULL (then no synchronisation). The step is a replay of the
+ * CUDA graph that eh_run caches (captured on first use) when dt <= 0 or dt is
+ * the one the graph holds; another dt launches the kernels one by one. */
 eh_status eh_step(eh_ctx *ctx, double dt, double *dt_used);
 
 /* nsteps SSPRK(3,3) steps with the same dt rule as eh_step, replayed from a

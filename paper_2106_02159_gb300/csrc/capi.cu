@@ -545,6 +545,26 @@ eh_status reset_status(eh_ctx *c) {
   return EH_OK;
 }
 
+// The cached CUDA graph of one SSPRK(3,3) step with dt (captured again when
+// dt differs from the one it holds).
+eh_status ensure_graph(eh_ctx *c, double dt) {
+  if (c->graph && c->graph_dt == dt) return EH_OK;
+  if (c->graph) {
+    CUDA_TRY(c, cudaGraphExecDestroy(c->graph));
+    c->graph = nullptr;
+  }
+  cudaGraph_t g;
+  CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_step_any(c, dt);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess) return fail(c, EH_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, EH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  c->graph_dt = dt;
+  return EH_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -874,7 +894,15 @@ eh_status eh_step(eh_ctx *c, double dt, double *dt_used) {
   eh_status st = require_ready(c);
   if (st) return st;
   CUDA_TRY(c, cudaSetDevice(c->device));
-  enqueue_step_any(c, dt);
+  // the CFL step, or a prescribed dt the cached graph was captured with, is
+  // one graph replay (as eh_run); another prescribed dt launches the step's
+  // kernels one by one rather than capturing a graph for a single use
+  if (c->profiling || (dt > 0.0 && !(c->graph && c->graph_dt == dt))) {
+    enqueue_step_any(c, dt);
+  } else {
+    if ((st = ensure_graph(c, dt))) return st;
+    CUDA_TRY(c, cudaGraphLaunch(c->graph, c->stream));
+  }
   CUDA_TRY(c, cudaGetLastError());
   c->steps += 1;
   c->last_stage_traced = false;
@@ -898,21 +926,7 @@ eh_status eh_run(eh_ctx *c, int32_t nsteps, double dt) {
     c->last_stage_traced = false;
     return EH_OK;
   }
-  if (!c->graph || c->graph_dt != dt) {
-    if (c->graph) {
-      CUDA_TRY(c, cudaGraphExecDestroy(c->graph));
-      c->graph = nullptr;
-    }
-    cudaGraph_t g;
-    CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_step_any(c, dt);
-    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-    if (e != cudaSuccess) return fail(c, EH_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&c->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return fail(c, EH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    c->graph_dt = dt;
-  }
+  if ((st = ensure_graph(c, dt))) return st;
   for (int32_t k = 0; k < nsteps; ++k) CUDA_TRY(c, cudaGraphLaunch(c->graph, c->stream));
   c->steps += nsteps;
   c->last_stage_traced = false;

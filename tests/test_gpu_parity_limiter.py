@@ -315,8 +315,10 @@ def test_served_requests_match_oracle():
 
 def test_three_dimensional_large_box_matches_oracle():
     """60^3 periodic Q1 hexes: 216,000 rows of 27 entries (well past one
-    wave of 64-256-row blocks on every SM); 2 steps, relaxed bounds at 1e-12 per step, strict bounds against
-    the oracle's spread."""
+    wave of 64-256-row blocks on every SM); 2 steps, relaxed bounds at 1e-12
+    per step, strict bounds against the oracle's spread. The limiter kernels
+    capped at 256 rows in flight per SM (152 x 256 rows per sweep, so their
+    grid-stride loops wrap five times) give the same bits."""
     mesh = M.structured_q1_3d(60, 60, 60, periodic=(True, True, True))
     U0 = W.perturbed_state(mesh, 11, base=dict(rho=1.0, vel=(0.5, -0.2, 0.1), p=1.0), amplitude=0.2)
     steps = 2
@@ -326,8 +328,16 @@ def test_three_dimensional_large_box_matches_oracle():
         s = solver_for(mesh, bound_relaxation=relax)
         s.set_state(U0)
         s.run(steps)
-        err = H.rel_l1(s.get_state(), ref).max()
+        U = s.get_state()
+        err = H.rel_l1(U, ref).max()
         s.close()
+        q = solver_for(mesh, bound_relaxation=relax)
+        for k in ("lim1", "pass", "final"):
+            q.set_launch_shape(k, 64, 256)
+        q.set_state(U0)
+        q.run(steps)
+        assert np.array_equal(q.get_state(), U), relax
+        q.close()
         orf = oracle.Oracle(mesh, bound_relaxation=relax, lib=oracle.load_fma())
         spread = H.oracle_spread(lambda V: orc.run(V, steps)[0], U0, samples=1,
                                  fn_fma=lambda V: orf.run(V, steps)[0])
