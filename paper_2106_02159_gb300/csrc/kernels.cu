@@ -11,6 +11,14 @@
 // k_prep and gathered; |c_ij|, 1/|c_ij|, m_ij/m_j and m_ji/m_i are static
 // per-edge arrays; (f(U_j) - f(U_i)) c_ij is computed once per edge in k_visc
 // and reused by k_low; the limiter directions P_ij are stored.
+//
+// Work that cannot change a result is skipped, exactly: an edge between two
+// bit-identical states takes the closed form of its values; a node record made
+// from the same state bits is kept, and an edge between two kept states that
+// were equal at the previous stage keeps its stored values; a row none of whose
+// neighbours differs has P_ij = 0 and every limiter 1; a limiter pass leaves
+// its remainder (1 - l) P_ij as the factor 1 - l (nothing is read where it is
+// 0); a row whose limiters are all 1 stores none and says so in a flag.
 #include "kernels.cuh"
 
 #include <cooperative_groups.h>
@@ -23,7 +31,7 @@
 namespace eh {
 
 // threads (= rows) per block of the row kernels: chosen per kernel at run time
-// (default 128, see eh_autotune), at most TPB_MAX
+// (eh_create's defaults, eh_autotune, eh_set_launch_shape), at most TPB_MAX
 
 __host__ __device__ inline unsigned nblocks(int64_t n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
 
