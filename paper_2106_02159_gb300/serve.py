@@ -140,7 +140,10 @@ def poisson_trace(count, rate, seed, n_range, t_final, mach_range=(1.5, 4.0), si
     uniform in mach_range, all to ``t_final``. size_grid > 0 snaps each drawn
     vertex count to the nearest of that many log-spaced sizes spanning n_range
     (so that meshes repeat and are built once); workers > 0 builds the distinct
-    meshes in that many processes (spawned: safe after CUDA is initialised)."""
+    meshes in that many processes (spawned: safe after CUDA is initialised; the
+    spawned workers import the caller's main module, so a script that calls
+    this with workers > 0 must do so under ``if __name__ == "__main__":``).
+    Inside a worker process the meshes are built in that process."""
     from . import meshes, workloads
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
@@ -156,8 +159,8 @@ def poisson_trace(count, rate, seed, n_range, t_final, mach_range=(1.5, 4.0), si
         mach = float(rng.uniform(*mach_range))
         specs.append((m, p1, mach))
     keys = sorted({(m, p1) for m, p1, _ in specs}, key=lambda t: -t[0])
-    if workers > 0 and len(keys) > 1:
-        import multiprocessing as mp
+    import multiprocessing as mp
+    if workers > 0 and len(keys) > 1 and mp.parent_process() is None:
         with mp.get_context("spawn").Pool(min(workers, len(keys))) as pool:
             built = dict(zip(keys, pool.map(_build_mesh, keys)))
     else:
