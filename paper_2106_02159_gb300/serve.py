@@ -143,7 +143,8 @@ def poisson_trace(count, rate, seed, n_range, t_final, mach_range=(1.5, 4.0), si
     meshes in that many processes (spawned: safe after CUDA is initialised; the
     spawned workers import the caller's main module, so a script that calls
     this with workers > 0 must do so under ``if __name__ == "__main__":``).
-    Inside a worker process the meshes are built in that process."""
+    Inside a worker process, or when the workers cannot start, the meshes are
+    built in the calling process."""
     from . import meshes, workloads
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
@@ -160,10 +161,16 @@ def poisson_trace(count, rate, seed, n_range, t_final, mach_range=(1.5, 4.0), si
         specs.append((m, p1, mach))
     keys = sorted({(m, p1) for m, p1, _ in specs}, key=lambda t: -t[0])
     import multiprocessing as mp
+    built = None
     if workers > 0 and len(keys) > 1 and mp.parent_process() is None:
-        with mp.get_context("spawn").Pool(min(workers, len(keys))) as pool:
-            built = dict(zip(keys, pool.map(_build_mesh, keys)))
-    else:
+        from concurrent.futures import ProcessPoolExecutor
+        from concurrent.futures.process import BrokenProcessPool
+        try:
+            with ProcessPoolExecutor(min(workers, len(keys)), mp_context=mp.get_context("spawn")) as ex:
+                built = dict(zip(keys, ex.map(_build_mesh, keys)))
+        except BrokenProcessPool:  # a worker could not start (say, a main module that cannot be imported)
+            built = None
+    if built is None:
         built = {key: _build_mesh(key) for key in keys}
     out = []
     for k, (m, p1, mach) in enumerate(specs):

@@ -90,3 +90,16 @@ def test_requests_wait_for_their_arrival(fake_batch):
 
 def test_empty_trace():
     assert serve.SolveServer(1, lib=object()).run([]) == []
+
+
+def test_trace_meshes_built_in_worker_processes_equal_serial():
+    """poisson_trace with workers > 0 builds the distinct meshes in spawned
+    processes; the trace equals the one built in this process."""
+    kw = dict(count=6, rate=1e3, seed=3, n_range=(800, 3000), t_final=0.01, size_grid=3)
+    a = serve.poisson_trace(**kw, workers=0)
+    b = serve.poisson_trace(**kw, workers=2)
+    assert [r.name for r in a] == [r.name for r in b]
+    for x, y in zip(a, b):
+        assert x.arrival == y.arrival and x.t_final == y.t_final
+        assert np.array_equal(x.mesh.row_ptr, y.mesh.row_ptr) and np.array_equal(x.mesh.col, y.mesh.col)
+        assert np.array_equal(x.mesh.cij, y.mesh.cij) and np.array_equal(x.U0, y.U0)
